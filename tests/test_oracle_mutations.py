@@ -1,0 +1,173 @@
+"""Plant plausible mistakes in the oracle (CPU only) and check that the pins
+in test_oracle_pins.py catch every one of them.
+
+Each mutation replaces one oracle function by a subtly wrong copy for the
+duration of one check; the check must then fail.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import dirac
+import test_oracle_pins as pins
+
+
+def _hopping_variant(fwd_proj=-1, bwd_proj=+1, dag=True, fwd_site=0, bc=True):
+    def hop(U, psi, t_bc=-1.0):
+        tb = t_bc if bc else 1.0
+        out = np.zeros_like(psi)
+        for mu in range(4):
+            U_mu = U[..., mu, :, :]
+            if fwd_site:
+                U_mu_f = dirac.shift(U_mu, mu, fwd_site, 2, 1.0)
+            else:
+                U_mu_f = U_mu
+            fwd = dirac._colour(U_mu_f, dirac.shift(psi, mu, +1, 2, tb))
+            out += dirac._spin(dirac.EYE4 + fwd_proj * dirac.GAMMA[mu], fwd)
+            cd = dirac._colour_dag if dag else dirac._colour
+            bwd = dirac.shift(cd(U_mu, psi), mu, -1, 2, tb)
+            out += dirac._spin(dirac.EYE4 + bwd_proj * dirac.GAMMA[mu], bwd)
+        return out
+    return hop
+
+
+def _leaves_variant(kind):
+    orig = dirac.plaquette_leaves
+
+    def leaves(U, mu, nu):
+        Q = orig(U, mu, nu)
+        if kind == "reverse_one_leaf":
+            Um, Un = U[..., mu, :, :], U[..., nu, :, :]
+            sm = lambda A, s: dirac._link_shift(A, mu, s)
+            sn = lambda A, s: dirac._link_shift(A, nu, s)
+            l1 = Um @ sm(Un, +1) @ dirac.dagger(sn(Um, +1)) @ dirac.dagger(Un)
+            return Q - l1 + dirac.dagger(l1)
+        if kind == "three_leaves":
+            Um, Un = U[..., mu, :, :], U[..., nu, :, :]
+            sm = lambda A, s: dirac._link_shift(A, mu, s)
+            sn = lambda A, s: dirac._link_shift(A, nu, s)
+            l1 = Um @ sm(Un, +1) @ dirac.dagger(sn(Um, +1)) @ dirac.dagger(Un)
+            return Q - l1
+        if kind == "double":
+            return 2 * Q
+        raise ValueError(kind)
+    return leaves
+
+
+def _no_trace_removal(U):
+    out = []
+    for mu, nu in dirac.PLANES:
+        Q = dirac.plaquette_leaves(U, mu, nu)
+        out.append((Q - dirac.dagger(Q)) / 8.0)
+    return np.stack(out, axis=-3)
+
+
+def _bad_bicgstab(apply, b, tol=1e-12, maxiter=400, x0=None):
+    # beta without the alpha/omega factor
+    x = np.zeros_like(b)
+    r = b - apply(x)
+    rhat = r.copy()
+    rho = 1.0
+    p = np.zeros_like(b)
+    v = np.zeros_like(b)
+    omega = 1.0
+    for it in range(maxiter):
+        rho_new = dirac.inner(rhat, r)
+        beta = rho_new / rho
+        rho = rho_new
+        p = r + beta * (p - omega * v)
+        v = apply(p)
+        alpha = rho / dirac.inner(rhat, v)
+        s = r - alpha * v
+        t = apply(s)
+        omega = dirac.inner(t, s) / dirac.inner(t, t)
+        x = x + alpha * p + omega * s
+        r = s - omega * t
+    return x, maxiter, np.linalg.norm(b - apply(x)) / np.linalg.norm(b)
+
+
+def _pion_off_by_one(psi, t_src=0):
+    T = psi.shape[0]
+    per_t = np.sum(np.abs(psi) ** 2, axis=(1, 2, 3, 4, 5))
+    return np.array([per_t[(t_src + dt + 1) % T] for dt in range(T)])
+
+
+def _run_pins(names):
+    """Run the named pins; return True if every one passed."""
+    U = pins.unit_links  # noqa: F841  (keeps the module imported)
+    dims = (4, 4, 4, 6)
+    from paper_1405_4524_gb300 import inputs
+    Ur = inputs.make_links(dims, 0.8, 77)
+    rough = (dims, Ur, dirac.field_strength(Ur))
+    ok = True
+    for name in names:
+        fn = getattr(pins, name)
+        try:
+            if name in ("test_gamma5_hermiticity", "test_gauge_covariance",
+                        "test_clover_structure"):
+                fn(rough)
+            elif name == "test_free_field_plane_waves":
+                fn(-1.0)
+            elif name == "test_constant_abelian_background":
+                fn(0, 2, 1)
+                fn(3, 1, 1)
+            elif name == "test_dense_lu_vs_bicgstab":
+                fn((4, 2, 2, 4))
+            else:
+                fn()
+        except AssertionError:
+            ok = False
+        except (FloatingPointError, ZeroDivisionError, np.linalg.LinAlgError):
+            ok = False
+    return ok
+
+
+ALL_OPERATOR_PINS = [
+    "test_free_field_plane_waves",
+    "test_free_field_propagator_closed_form",
+    "test_gamma5_hermiticity",
+    "test_gauge_covariance",
+    "test_clover_structure",
+    "test_constant_abelian_background",
+    "test_dense_lu_vs_bicgstab",
+    "test_schur_formulas_vs_dense",
+]
+
+MUTATIONS = {
+    "backward projector sign": ("hopping", _hopping_variant(bwd_proj=-1)),
+    "forward projector sign": ("hopping", _hopping_variant(fwd_proj=+1)),
+    "both projector signs": ("hopping", _hopping_variant(fwd_proj=+1, bwd_proj=-1)),
+    "backward link not daggered": ("hopping", _hopping_variant(dag=False)),
+    "forward link at x+mu": ("hopping", _hopping_variant(fwd_site=+1)),
+    "no time boundary sign": ("hopping", _hopping_variant(bc=False)),
+    "one clover leaf reversed": ("plaquette_leaves", _leaves_variant("reverse_one_leaf")),
+    "three clover leaves": ("plaquette_leaves", _leaves_variant("three_leaves")),
+    "clover normalisation 1/4": ("plaquette_leaves", _leaves_variant("double")),
+    "trace not removed": ("field_strength", _no_trace_removal),
+}
+
+
+def test_unmutated_oracle_passes_the_pins():
+    assert _run_pins(ALL_OPERATOR_PINS)
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_operator_mutation_is_caught(name, monkeypatch):
+    attr, fn = MUTATIONS[name]
+    monkeypatch.setattr(dirac, attr, fn)
+    with np.errstate(all="ignore"):
+        assert not _run_pins(ALL_OPERATOR_PINS), f"mutation not caught: {name}"
+
+
+def test_bicgstab_mutation_is_caught(monkeypatch):
+    monkeypatch.setattr(dirac, "bicgstab", _bad_bicgstab)
+    with np.errstate(all="ignore"):
+        assert not _run_pins(["test_bicgstab_on_a_random_matrix",
+                              "test_dense_lu_vs_bicgstab"])
+
+
+def test_pion_mutation_is_caught(monkeypatch):
+    monkeypatch.setattr(dirac, "pion_correlator", _pion_off_by_one)
+    import oracle
+    monkeypatch.setattr(oracle, "pion_correlator", _pion_off_by_one)
+    assert not _run_pins(["test_pion_correlator_brute_force"])

@@ -1,0 +1,344 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each check below is chosen so that a plausible mistake in the oracle (a
+dropped term, a wrong sign, a wrong neighbour index, a transposed or
+un-daggered link, a wrong clover normalisation or leaf orientation, a broken
+Krylov step) fails at least one of them:
+
+* Dirac algebra of the gamma basis (Clifford relations, gamma5).
+* Free field (all links 1): the momentum-space closed form of M and of
+  M^{-1}, with antiperiodic time momenta.
+* gamma5-hermiticity  <phi, g5 M g5 chi> = <M phi, chi>.
+* gauge covariance   M[U^g] (g psi) = g M[U] psi.
+* constant abelian background: closed-form clover term.
+* dense LU on tiny lattices for BiCGStab and the even-odd formulas.
+* the pion contraction against brute-force loops and against its exact
+  expectation value from the dense inverse.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import dirac
+from paper_1405_4524_gb300 import inputs
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def unit_links(dims):
+    X, Y, Z, T = dims
+    U = np.zeros((T, Z, Y, X, 4, 3, 3), dtype=np.complex128)
+    U[...] = np.eye(3)
+    return U
+
+
+def random_spinor(dims, rng, n=None):
+    X, Y, Z, T = dims
+    sh = (T, Z, Y, X, 4, 3) if n is None else (n, T, Z, Y, X, 4, 3)
+    return rng.standard_normal(sh) + 1j * rng.standard_normal(sh)
+
+
+def random_su3(shape, rng):
+    g = rng.standard_normal(shape + (3, 3)) + 1j * rng.standard_normal(shape + (3, 3))
+    q, r = np.linalg.qr(g)
+    d = np.diagonal(r, axis1=-2, axis2=-1)
+    q = q * (d / np.abs(d))[..., None, :]
+    det = np.linalg.det(q)
+    return q / (det ** (1.0 / 3.0))[..., None, None]
+
+
+# ---------------------------------------------------------------------------
+# Dirac algebra
+# ---------------------------------------------------------------------------
+
+def test_gamma_clifford_and_gamma5():
+    G = oracle.GAMMA
+    for mu in range(4):
+        assert np.allclose(G[mu], G[mu].conj().T)
+        for nu in range(4):
+            anti = G[mu] @ G[nu] + G[nu] @ G[mu]
+            assert np.allclose(anti, 2.0 * (mu == nu) * np.eye(4))
+    assert np.allclose(oracle.GAMMA5, np.diag([1, 1, -1, -1]))
+    for mu in range(4):
+        assert np.allclose(oracle.GAMMA5 @ G[mu], -G[mu] @ oracle.GAMMA5)
+
+
+def test_sigma_block_diagonal_in_chirality():
+    for mu, nu in oracle.PLANES:
+        s = oracle.sigma(mu, nu)
+        assert np.allclose(s, s.conj().T)
+        assert np.allclose(s[:2, 2:], 0) and np.allclose(s[2:, :2], 0)
+
+
+# ---------------------------------------------------------------------------
+# Free field: closed-form momentum space
+# ---------------------------------------------------------------------------
+
+def free_M_of_p(p, kappa):
+    """M(p) = (1 - 2 k sum cos p) + 2 i k sum g_mu sin p_mu (U = 1)."""
+    a = 1.0 - 2.0 * kappa * np.sum(np.cos(p))
+    return a * np.eye(4) + 2j * kappa * sum(
+        oracle.GAMMA[mu] * np.sin(p[mu]) for mu in range(4))
+
+
+@pytest.mark.parametrize("t_bc", [-1.0, 1.0])
+def test_free_field_plane_waves(t_bc):
+    dims = (4, 6, 4, 8)
+    X, Y, Z, T = dims
+    kappa, csw = 0.13, 1.0
+    U = unit_links(dims)
+    F = oracle.field_strength(U)
+    assert np.allclose(F, 0)
+    rng = np.random.default_rng(5)
+    t, z, y, x = np.meshgrid(np.arange(T), np.arange(Z), np.arange(Y),
+                             np.arange(X), indexing="ij")
+    shift4 = 0.5 if t_bc < 0 else 0.0
+    for n in [(0, 0, 0, 0), (1, 2, 3, 5), (3, 5, 1, 7), (2, 0, 1, 2)]:
+        p = np.array([2 * np.pi * n[0] / X, 2 * np.pi * n[1] / Y,
+                      2 * np.pi * n[2] / Z, 2 * np.pi * (n[3] + shift4) / T])
+        u = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+        phase = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+        psi = phase[..., None, None] * u
+        got = oracle.apply_M(U, F, psi, kappa, csw, t_bc)
+        want = phase[..., None, None] * (free_M_of_p(p, kappa) @ u)
+        assert rel(got, want) < 1e-13
+
+
+def free_propagator_fft(eta, dims, kappa):
+    """psi = M^{-1} eta at U = 1, antiperiodic time, by FFT.
+
+    Momenta p_i = 2 pi k_i / L_i, p_4 = (2 k_4 + 1) pi / T; the half-integer
+    time momentum is carried by the twist exp(-i pi t / T). With
+    a = 1 - 2k sum cos p and s_mu = sin p_mu:
+    M(p)^{-1} = (a - 2 i k g.s) / (a^2 + 4 k^2 s.s).
+    """
+    X, Y, Z, T = dims
+    tw = np.exp(1j * np.pi * np.arange(T) / T)[:, None, None, None, None, None]
+    eh = np.fft.fftn(eta / tw, axes=(0, 1, 2, 3))
+    kt, kz, ky, kx = np.meshgrid(np.arange(T), np.arange(Z), np.arange(Y),
+                                 np.arange(X), indexing="ij")
+    p = [2 * np.pi * kx / X, 2 * np.pi * ky / Y, 2 * np.pi * kz / Z,
+         2 * np.pi * (kt + 0.5) / T]
+    a = 1.0 - 2.0 * kappa * sum(np.cos(q) for q in p)
+    s = [np.sin(q) for q in p]
+    den = a ** 2 + 4 * kappa ** 2 * sum(q ** 2 for q in s)
+    Minv = a[..., None, None] * np.eye(4) - 2j * kappa * sum(
+        oracle.GAMMA[mu] * s[mu][..., None, None] for mu in range(4))
+    Minv = Minv / den[..., None, None]
+    ph = Minv @ eh
+    return np.fft.ifftn(ph, axes=(0, 1, 2, 3)) * tw
+
+
+def test_free_field_propagator_closed_form():
+    dims = (4, 4, 6, 8)
+    kappa = 0.124
+    U = unit_links(dims)
+    rng = np.random.default_rng(7)
+    eta = random_spinor(dims, rng)
+    want = free_propagator_fft(eta, dims, kappa)
+    F = oracle.field_strength(U)
+    # apply_M of the closed-form solution gives back the source
+    assert rel(oracle.apply_M(U, F, want, kappa, 1.0, -1.0), eta) < 1e-13
+    # and the oracle's BiCGStab finds the same solution
+    got, it, res = oracle.solve(U, eta, kappa, 1.0, -1.0, tol=1e-13)
+    assert res <= 1e-13
+    assert rel(got, want) < 1e-11
+
+
+# ---------------------------------------------------------------------------
+# Invariants on random gauge fields (with the clover term)
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def rough_field():
+    dims = (4, 4, 4, 6)
+    U = inputs.make_links(dims, 0.8, 77)
+    return dims, U, oracle.field_strength(U)
+
+
+def test_gamma5_hermiticity(rough_field):
+    dims, U, F = rough_field
+    rng = np.random.default_rng(11)
+    phi, chi = random_spinor(dims, rng), random_spinor(dims, rng)
+    g5 = lambda v: oracle.GAMMA5 @ v
+    for kappa, csw in [(0.12, 1.0), (0.2, 2.5)]:
+        lhs = oracle.inner(phi, g5(oracle.apply_M(U, F, g5(chi), kappa, csw)))
+        rhs = oracle.inner(oracle.apply_M(U, F, phi, kappa, csw), chi)
+        assert abs(lhs - rhs) / abs(rhs) < 1e-13
+
+
+def test_gauge_covariance(rough_field):
+    dims, U, F = rough_field
+    X, Y, Z, T = dims
+    rng = np.random.default_rng(12)
+    g = random_su3((T, Z, Y, X), rng)
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        g_fwd = oracle.shift(g, mu, +1, 2, 1.0)
+        Ug[..., mu, :, :] = g @ U[..., mu, :, :] @ oracle.dagger(g_fwd)
+    Fg = oracle.field_strength(Ug)
+    psi = random_spinor(dims, rng)
+    gpsi = psi @ np.swapaxes(g, -1, -2)  # colour rotation at every site
+    kappa, csw = 0.125, 1.3
+    lhs = oracle.apply_M(Ug, Fg, gpsi, kappa, csw)
+    rhs = oracle.apply_M(U, F, psi, kappa, csw) @ np.swapaxes(g, -1, -2)
+    assert rel(lhs, rhs) < 1e-13
+
+
+def test_clover_structure(rough_field):
+    dims, U, F = rough_field
+    assert np.allclose(np.trace(F, axis1=-2, axis2=-1), 0, atol=1e-14)
+    assert np.allclose(F, -oracle.dagger(F), atol=1e-14)
+    A = oracle.clover_matrices(F, 0.12, 1.0)
+    assert np.allclose(A, oracle.dagger(A), atol=1e-14)
+    assert np.allclose(A[..., :6, 6:], 0, atol=1e-15)
+    assert np.allclose(A[..., 6:, :6], 0, atol=1e-15)
+    # the explicit matrices and the operator form agree
+    rng = np.random.default_rng(3)
+    psi = random_spinor(dims, rng)
+    assert rel(oracle.site_apply(A, psi),
+               oracle.clover_apply(F, psi, 0.12, 1.0)) < 1e-14
+
+
+@pytest.mark.parametrize("mu,nu,n", [(0, 2, 1), (3, 1, 1), (1, 3, 2)])
+def test_constant_abelian_background(mu, nu, n):
+    """U_mu(x) = diag(e^{i th x_nu}, e^{-i th x_nu}, 1), th = 2 pi n / L_nu,
+    all other links 1. Every mu-nu leaf is diag(e^{-i th}, e^{i th}, 1), so
+    Fhat_mu_nu = i diag(-sin th, sin th, 0) and all other planes vanish."""
+    dims = (4, 4, 6, 8)
+    X, Y, Z, T = dims
+    U = unit_links(dims)
+    coord = np.meshgrid(np.arange(T), np.arange(Z), np.arange(Y),
+                        np.arange(X), indexing="ij")[::-1]  # x, y, z, t
+    th = 2 * np.pi * n / dims[nu]
+    phi = th * coord[nu]
+    U[..., mu, 0, 0] = np.exp(1j * phi)
+    U[..., mu, 1, 1] = np.exp(-1j * phi)
+    F = oracle.field_strength(U)
+    f = 1j * np.diag([-np.sin(th), np.sin(th), 0.0])
+    kappa, csw = 0.11, 1.7
+    for p, (a, b) in enumerate(oracle.PLANES):
+        if (a, b) == (mu, nu):
+            want = f
+        elif (a, b) == (nu, mu):
+            want = -f
+        else:
+            want = np.zeros((3, 3))
+        assert np.allclose(F[..., p, :, :], want, atol=1e-14)
+    s = oracle.sigma(mu, nu)
+    A_want = np.eye(12) + 1j * kappa * csw * np.kron(s, f)
+    A = oracle.clover_matrices(F, kappa, csw)
+    assert np.allclose(A, A_want, atol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Dense linear algebra on tiny lattices
+# ---------------------------------------------------------------------------
+
+def dense_M(U, F, kappa, csw, t_bc, dims):
+    X, Y, Z, T = dims
+    n = X * Y * Z * T * 12
+    basis = np.eye(n, dtype=np.complex128).reshape(n, T, Z, Y, X, 4, 3)
+    cols = oracle.apply_M(U, F, basis, kappa, csw, t_bc)
+    return cols.reshape(n, n).T
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 2, 2, 4)])
+def test_dense_lu_vs_bicgstab(dims):
+    U = inputs.make_links(dims, 0.25, 31)
+    F = oracle.field_strength(U)
+    kappa, csw = 0.12, 1.0
+    M = dense_M(U, F, kappa, csw, -1.0, dims)
+    # gamma5-hermiticity at the matrix level: g5 M g5 = M^dag
+    V = np.prod(dims)
+    G5 = np.kron(np.eye(V), np.kron(oracle.GAMMA5, np.eye(3)))
+    assert np.allclose(G5 @ M @ G5, M.conj().T, atol=1e-14)
+    eta = inputs.make_z4(dims, 1, 99)[0]
+    exact = np.linalg.solve(M, eta.reshape(-1)).reshape(eta.shape)
+    got, it, res = oracle.solve(U, eta, kappa, csw, -1.0, tol=1e-13)
+    assert res <= 1e-13
+    assert rel(got, exact) < 1e-12
+
+
+def test_schur_formulas_vs_dense():
+    dims = (4, 2, 2, 4)
+    U = inputs.make_links(dims, 0.5, 41)
+    F = oracle.field_strength(U)
+    kappa, csw = 0.13, 1.0
+    par = oracle.parity_field(dims)
+    A = oracle.clover_matrices(F, kappa, csw)
+    Ainv = np.linalg.inv(A)
+    eta = inputs.make_z4(dims, 1, 7)[0]
+    M = dense_M(U, F, kappa, csw, -1.0, dims)
+    exact = np.linalg.solve(M, eta.reshape(-1)).reshape(eta.shape)
+    # the exact solution's even part solves the Schur system
+    b = oracle.schur_source(U, Ainv, eta, kappa, par)
+    lhs = oracle.schur_apply(U, Ainv, oracle.restrict(exact, par, 0), kappa, par)
+    assert rel(lhs, b) < 1e-13
+    # and the reconstruction gives back the full solution
+    psi = oracle.schur_reconstruct(U, Ainv, eta, oracle.restrict(exact, par, 0),
+                                   kappa, par)
+    assert rel(psi, exact) < 1e-13
+    # BiCGStab on the Schur system, reconstructed
+    xe, it, res = oracle.bicgstab(
+        lambda v: oracle.schur_apply(U, Ainv, v, kappa, par), b, tol=1e-13)
+    psi2 = oracle.schur_reconstruct(U, Ainv, eta, xe, kappa, par)
+    assert rel(psi2, exact) < 1e-12
+
+
+def test_bicgstab_on_a_random_matrix():
+    rng = np.random.default_rng(2)
+    n = 300
+    A = np.eye(n) * 4 + (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x, it, res = oracle.bicgstab(lambda v: A @ v, b, tol=1e-13)
+    assert res <= 1e-13
+    assert rel(x, np.linalg.solve(A, b)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Pion contraction
+# ---------------------------------------------------------------------------
+
+def test_pion_correlator_brute_force():
+    dims = (2, 2, 2, 4)
+    X, Y, Z, T = dims
+    rng = np.random.default_rng(9)
+    psi = random_spinor(dims, rng)
+    for t0 in [0, 3]:
+        C = oracle.pion_correlator(psi, t0)
+        for dt in range(T):
+            acc = 0.0
+            for z in range(Z):
+                for y in range(Y):
+                    for x in range(X):
+                        for s in range(4):
+                            for c in range(3):
+                                v = psi[(t0 + dt) % T, z, y, x, s, c]
+                                acc += v.real ** 2 + v.imag ** 2
+            assert abs(C[dt] - acc) <= 1e-13 * acc
+
+
+def test_pion_stochastic_estimate_matches_exact():
+    """E_eta[C(t)] = sum_{x in t} sum_y tr[S(x,y) S(x,y)^dag] for Z4 eta,
+    where S = M^{-1} comes from the dense LU inverse."""
+    dims = (4, 2, 2, 4)
+    X, Y, Z, T = dims
+    U = inputs.make_links(dims, 0.25, 51)
+    F = oracle.field_strength(U)
+    kappa, csw = 0.12, 1.0
+    M = dense_M(U, F, kappa, csw, -1.0, dims)
+    S = np.linalg.inv(M)
+    per_row = np.sum(np.abs(S) ** 2, axis=1).reshape(T, Z, Y, X, 4, 3)
+    exact = per_row.sum(axis=(1, 2, 3, 4, 5))
+    n = 48
+    eta = inputs.make_z4(dims, n, 500)
+    psi = (S @ eta.reshape(n, -1).T).T.reshape(eta.shape)
+    Cs = np.array([oracle.pion_correlator(psi[k]) for k in range(n)])
+    mean = Cs.mean(axis=0)
+    err = Cs.std(axis=0, ddof=1) / np.sqrt(n)
+    z = np.abs(mean - exact) / err
+    assert np.all(z < 4.0), z
