@@ -1,0 +1,243 @@
+/*
+ * stochq.h - C ABI of libstochq, a GB300 (sm_103a) solver for the clover
+ * Wilson-Dirac system M psi = eta on many stochastic noise sources.
+ *
+ * The operation (Giedt & Howarth, "Stochastic propagators for multi-pion
+ * correlation functions in lattice QCD with GPUs", Sec. "Stochastic
+ * propagators", Eq. Sfill): the stochastic all-to-all propagator is built
+ * from solution vectors X_i = M^{-1} eta_i of random sources eta_i, where
+ * M is the lattice fermion matrix of clover fermions with c_SW = 1.0
+ * (Sec. "Correlation function"). The paper does not write M out; this
+ * library uses the kappa-normalised Sheikholeslami-Wohlert operator
+ *
+ *   M = A - kappa D
+ *   D psi(x) = sum_mu (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^+ psi(x-mu)
+ *   A(x)     = 1 + i kappa c_sw sum_{mu<nu} sigma_mu_nu Fhat_mu_nu(x)
+ *   Fhat     = (Q_mu_nu - Q_mu_nu^+)/8, traceless; Q = sum of the four clover leaves
+ *
+ * with DeGrand-Rossi gamma matrices (gamma5 = diag(1,1,-1,-1)), periodic
+ * space and a factor t_bc on the fermion hop across the time boundary.
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions shared by every call
+ * ---------------------------------------------------------------------------
+ * Lattice dims[4] = {X, Y, Z, T}, each even and >= 2; V = X*Y*Z*T, Vh = V/2.
+ * Site x = (x,y,z,t) has lexicographic index i = x + X*(y + Y*(z + Z*t)) and
+ * parity p = (x+y+z+t) mod 2. Its checkerboard index within its parity is
+ * cb = i / 2 (integer division).
+ *
+ * Host ("lexicographic") layouts, all FP64, real and imaginary interleaved:
+ *   gauge field  U[t][z][y][x][mu][a][b][re,im]   (mu = 0..3 is x,y,z,t;
+ *                                                   a = row, b = column)
+ *   spinors      S[k][t][z][y][x][spin][colour][re,im]   (k = source)
+ *
+ * Device ("even-odd") spinor layout, one parity, n sources. A site holds
+ * 12 complex numbers, index j = 3*spin + colour, stored in 16-byte chunks;
+ * chunk c of source k at checkerboard site cb is element (k*NC + c)*Vh + cb:
+ *   SQ_F64: NC = 12 chunks of double2, chunk c = complex j = c
+ *   SQ_F32: NC = 6 chunks of float4,  chunk c = complex 2c, 2c+1
+ *   SQ_F16: NC = 3 chunks of 8 x IEEE binary16, chunk c = complex 4c..4c+3,
+ *           each value stored as v / norm; after the n*3*Vh chunks follow
+ *           n*Vh FP32 norms (norm of source k at site cb at k*Vh + cb),
+ *           norm = max |re|,|im| over the site's 24 reals (0 for a zero site).
+ * sq_field_bytes() gives the size of one such field.
+ *
+ * Ownership: the context owns the gauge field, clover terms, workspace and
+ * its CUDA stream. Caller buffers are never retained past a call.
+ * Streams: every call runs on the context's own stream, ordered after the
+ * work already queued on the caller's stream given to sq_create (and the
+ * caller's stream waits for the call's work before the call returns).
+ * Calls that take host buffers return when the results are in them.
+ * Errors: every call returns a status; none aborts or exits. The message
+ * of the last failure is kept per context (sq_last_error). Arguments are
+ * validated before any kernel is launched. One context per host thread.
+ */
+#ifndef STOCHQ_H
+#define STOCHQ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sq_ctx sq_ctx;
+
+typedef enum {
+  SQ_OK = 0,
+  SQ_ERR_ARG = 1,        /* invalid argument (dims, parity, sizes, NULL, ...) */
+  SQ_ERR_CUDA = 2,       /* a CUDA runtime call failed */
+  SQ_ERR_OOM = 3,        /* device memory could not be allocated */
+  SQ_ERR_NONFINITE = 4,  /* NaN or Inf in links or sources */
+  SQ_ERR_CLOVER = 5,     /* a 6x6 clover block is singular */
+  SQ_ERR_NOCONV = 6,     /* max_iter reached before tol on some source */
+  SQ_ERR_BREAKDOWN = 7,  /* BiCGStab broke down and restarts did not help */
+  SQ_ERR_TIMEOUT = 8,    /* a bounded device-side wait ran out */
+  SQ_ERR_STATE = 9       /* call made in the wrong state (e.g. no gauge) */
+} sq_status;
+
+typedef enum { SQ_F64 = 0, SQ_F32 = 1, SQ_F16 = 2 } sq_prec;
+
+/* Where a caller buffer lives. */
+enum { SQ_HOST = 0, SQ_DEVICE = 1 };
+
+/* sq_dslash_eo flags */
+enum {
+  SQ_DS_CLOVER_INV = 1, /* apply A_pp^{-1} after the hopping term */
+  SQ_DS_XPAY = 2,       /* out = x + a * (...) instead of out = (...) */
+  SQ_DS_SYNC = 4        /* wait for the result before returning */
+};
+
+/* sq_solve_params.outer */
+enum { SQ_OUTER_RELIABLE = 0, SQ_OUTER_DEFECT = 1 };
+
+typedef struct sq_solve_params {
+  int inner_prec;      /* SQ_F64: plain FP64 solver; SQ_F32 / SQ_F16: mixed */
+  int outer;           /* SQ_OUTER_RELIABLE (keep the Krylov space) or
+                          SQ_OUTER_DEFECT (restart at every FP64 update)    */
+  double delta;        /* FP64 update when ||r|| < delta * max||r|| since the
+                          last update (reliable) or < delta * ||r_start||
+                          (defect correction); ignored for SQ_F64          */
+  int max_iter;        /* inner iterations per source (default 20000)      */
+  int recon;           /* low-precision links: 12 or 18 (FP16 always 12)   */
+  int sites_per_block; /* dslash CTA shape; 0 = autotune                   */
+  int rhs_per_block;   /* dslash sources per CTA; 0 = autotune             */
+  int chunk;           /* iterations per CUDA-graph launch (default 16)    */
+  int use_graph;       /* 1 (default): capture the inner loop in graphs    */
+  int io;              /* SQ_HOST (default) or SQ_DEVICE for sources and
+                          solutions                                        */
+  int use_x0;          /* 1: solutions hold an initial guess on entry      */
+  int verbose;         /* 1: progress lines on stderr                      */
+} sq_solve_params;
+
+typedef struct sq_solve_stats {
+  int status;            /* sq_status of this source                      */
+  int iterations;        /* inner BiCGStab iterations                     */
+  int updates;           /* FP64 residual recomputations (reliable updates
+                            or defect-correction cycles)                  */
+  int restarts;          /* BiCGStab restarts (breakdown or defect cycle) */
+  double true_residual;  /* ||eta - M psi|| / ||eta||, FP64, full lattice */
+  double seconds;        /* wall time of the whole sq_solve call          */
+} sq_solve_stats;
+
+/* Fill *p with the defaults (FP32 inner, reliable updates, delta 0.1). */
+void sq_default_params(sq_solve_params *p);
+
+/* Create a context for one lattice. dims = {X,Y,Z,T}, all even, >= 2.
+ * t_bc = -1 (antiperiodic in time) or +1 (periodic). cuda_stream is a
+ * cudaStream_t to order against (NULL = legacy default stream).
+ * Errors: SQ_ERR_ARG (bad dims/t_bc/NULL ctx), SQ_ERR_CUDA. */
+sq_status sq_create(sq_ctx **ctx, const int dims[4], int t_bc, void *cuda_stream);
+
+/* Free everything the context owns. NULL is accepted. */
+sq_status sq_destroy(sq_ctx *ctx);
+
+/* Load the gauge field U (host or device, lexicographic FP64, see above).
+ * Kept on the device as FP64 reconstruct-18, FP32 reconstruct-`recon`
+ * and FP16 reconstruct-12, per-parity site-blocked (the analogue of the
+ * array reordering between the paper's host code and its GPU inverter,
+ * Sec. "Stochastic propagators"). Drops cached clover terms.
+ * Errors: SQ_ERR_ARG (recon not 12/18, NULL), SQ_ERR_NONFINITE,
+ * SQ_ERR_ARG if recon = 12 and some link is not SU(3) to 1e-6. */
+sq_status sq_load_gauge(sq_ctx *ctx, const double *U, int recon, int where);
+
+/* Build the clover term A and its inverse for (kappa, c_sw) on the device
+ * in FP64: clover-leaf Fhat (Sec. "Correlation function": c_SW = 1.0 is
+ * the paper's tree-level value), A as two 6x6 Hermitian blocks per site in
+ * the chiral basis, each inverted in FP64 (partial-pivot Gauss-Jordan);
+ * FP32 and FP16 copies of A^{-1} feed the low-precision operator. Up to 8
+ * (kappa, c_sw) pairs are cached; a cached pair is reused.
+ * Errors: SQ_ERR_STATE (no gauge), SQ_ERR_ARG (non-finite kappa/c_sw),
+ * SQ_ERR_CLOVER (a block is singular: |pivot| < 1e-12 * block scale). */
+sq_status sq_build_clover(sq_ctx *ctx, double kappa, double c_sw);
+
+/* Bytes of one device even-odd field (one parity) of n_rhs sources. */
+sq_status sq_field_bytes(const sq_ctx *ctx, sq_prec prec, int n_rhs, size_t *bytes);
+
+/* Convert the parity-`parity` sites of n_rhs lexicographic FP64 spinors
+ * (host or device per `where`) into a device even-odd field of precision
+ * prec. Errors: SQ_ERR_ARG. */
+sq_status sq_pack_spinor(sq_ctx *ctx, void *eo_out, const double *lex_in,
+                         int parity, sq_prec prec, int n_rhs, int where);
+
+/* Write the parity-`parity` sites of a device even-odd field into n_rhs
+ * lexicographic FP64 spinors (host or device per `where`); sites of the
+ * other parity are left unchanged. Errors: SQ_ERR_ARG. */
+sq_status sq_unpack_spinor(sq_ctx *ctx, double *lex_out, const void *eo_in,
+                           int parity, sq_prec prec, int n_rhs, int where);
+
+/* One even-odd hopping application on device even-odd fields of precision
+ * prec, n_rhs sources:
+ *   w   = D_{p,1-p} in                      (hop from parity 1-p onto p)
+ *   w  <- A_pp^{-1} w                       if flags & SQ_DS_CLOVER_INV
+ *   out = x + a * w   if flags & SQ_DS_XPAY, else out = w
+ * in has parity 1 - out_parity; out and x have parity out_parity (x may
+ * equal out; in must not alias out). D_eo / D_oe are the blocks of the
+ * hopping term D above (the Schur operator of the solver is
+ * 1 - kappa^2 A_ee^{-1} D_eo A_oo^{-1} D_oe). SQ_DS_CLOVER_INV uses the
+ * clover term of the last sq_build_clover. Asynchronous unless
+ * SQ_DS_SYNC. Errors: SQ_ERR_ARG, SQ_ERR_STATE (no gauge / no clover). */
+sq_status sq_dslash_eo(sq_ctx *ctx, void *out, const void *in, const void *x,
+                       int out_parity, sq_prec prec, int n_rhs, int flags, double a);
+
+/* Full-lattice FP64 operator: out = M in for n_rhs lexicographic FP64
+ * spinors (host or device per `where`), with the clover term for
+ * (kappa, c_sw) (built if not cached). Errors: SQ_ERR_ARG, SQ_ERR_STATE,
+ * SQ_ERR_CLOVER. */
+sq_status sq_apply_M(sq_ctx *ctx, double *out, const double *in, int n_rhs,
+                     double kappa, double c_sw, int where);
+
+/* Solve M psi_k = eta_k for n_rhs sources (Eq. Sfill's X_i = M^{-1} eta_i)
+ * with even-odd preconditioned BiCGStab on
+ *   Mhat = 1 - kappa^2 A_ee^{-1} D_eo A_oo^{-1} D_oe,
+ *   bhat = A_ee^{-1} (eta_e + kappa D_eo A_oo^{-1} eta_o),
+ *   psi_o = A_oo^{-1} (eta_o + kappa D_oe psi_e),
+ * batched over all sources, mixed precision per params (FP64 updates of
+ * the true residual). Stops when the FP64 full-lattice relative residual
+ * ||eta_k - M psi_k|| / ||eta_k|| <= tol for every source (checked).
+ * sources/solutions: lexicographic FP64, host or device per params->io.
+ * params NULL = defaults; stats (n_rhs entries) may be NULL.
+ * Errors: SQ_ERR_ARG, SQ_ERR_STATE (no gauge), SQ_ERR_NONFINITE (source),
+ * SQ_ERR_CLOVER, SQ_ERR_NOCONV / SQ_ERR_BREAKDOWN (solutions then hold the
+ * best iterate; stats give the per-source reason), SQ_ERR_OOM, SQ_ERR_CUDA.
+ * A zero source gives a zero solution. */
+sq_status sq_solve(sq_ctx *ctx, double kappa, double c_sw, const double *sources,
+                   double *solutions, int n_rhs, double tol,
+                   const sq_solve_params *params, sq_solve_stats *stats);
+
+/* One problem of a heterogeneous batch. */
+typedef struct sq_problem {
+  sq_ctx *ctx;            /* lattice (each problem may use its own)       */
+  double kappa, c_sw;
+  const double *sources;  /* lexicographic FP64, per params->io           */
+  double *solutions;
+  int n_rhs;
+  double tol;
+} sq_problem;
+
+/* Solve several problems (different lattices and/or kappa) in one
+ * iteration loop whose kernels each cover every source of every problem;
+ * converged sources retire from all launches. All contexts must share the
+ * same CUDA device. stats holds sum(n_rhs) entries in problem order.
+ * Errors as sq_solve. */
+sq_status sq_solve_batch(const sq_problem *probs, int n_probs,
+                         const sq_solve_params *params, sq_solve_stats *stats);
+
+/* Pion correlator of each solution vector (the zero-momentum contraction
+ * sum_{x in t} sum_y tr S S^+ of Sec. "Stochastic propagators", estimated
+ * per source):  C[k][dt] = sum over sites x on timeslice (t_k + dt) mod T
+ * of sum_{spin,colour} |psi_k(x)|^2, t_k = src_tslice[k] (0 if NULL).
+ * Accumulated in FP64 in a fixed order. solutions: lexicographic FP64,
+ * host or device per `where`; C: host, n_rhs * T doubles. No 1/N or
+ * volume factor. Errors: SQ_ERR_ARG. */
+sq_status sq_contract_pion(sq_ctx *ctx, const double *solutions, int n_rhs,
+                           const int *src_tslice, double *C, int where);
+
+const char *sq_status_string(sq_status s);
+const char *sq_last_error(const sq_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STOCHQ_H */

@@ -1,0 +1,501 @@
+// The extern "C" boundary of libstochq (declared in include/stochq.h):
+// argument validation, context and stream handling, host <-> device
+// staging, and dispatch to the kernels of the other translation units.
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "sq_internal.h"
+
+namespace sq {
+
+Geom geom_of(const sq_ctx* c) {
+  Geom g;
+  g.X = c->dims[0];
+  g.Y = c->dims[1];
+  g.Z = c->dims[2];
+  g.T = c->dims[3];
+  g.X2 = g.X / 2;
+  g.Vh = c->Vh;
+  g.tbc = (double)c->t_bc;
+  return g;
+}
+
+sq_status set_error(sq_ctx* c, sq_status s, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->last_error = buf;
+  }
+  return s;
+}
+
+sq_status cuda_check(sq_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return SQ_OK;
+  cudaGetLastError();
+  if (e == cudaErrorMemoryAllocation) return set_error(c, SQ_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return set_error(c, SQ_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+size_t field_bytes(int Vh, int prec, int n) {
+  if (prec == P64) return (size_t)n * Vh * 192;
+  if (prec == P32) return (size_t)n * Vh * 96;
+  return (size_t)n * Vh * 52;  // 48 B of halves + 4 B norm
+}
+
+Field make_field(void* data, int Vh, int prec, int n) {
+  Field f;
+  f.data = data;
+  f.Vh = Vh;
+  f.norm = (prec == P16 && data) ? (float*)((uint4*)data + (size_t)n * 3 * Vh) : nullptr;
+  return f;
+}
+
+sq_status enter_stream(sq_ctx* c) {
+  cudaError_t e = cudaEventRecord(c->ev, c->user_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev, 0);
+  return cuda_check(c, e, "stream ordering");
+}
+
+sq_status leave_stream(sq_ctx* c) {
+  cudaError_t e = cudaEventRecord(c->ev, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->user_stream, c->ev, 0);
+  return cuda_check(c, e, "stream ordering");
+}
+
+sq_status read_error_word(sq_ctx* c, int* bits) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  *bits = h;
+  return cuda_check(c, e, "device error word");
+}
+
+static void free_clover(CloverSet& cs) {
+  cudaFree(cs.A64);
+  cudaFree(cs.Ainv64);
+  cudaFree(cs.Ainv32);
+  cudaFree(cs.Ainv16);
+  cs = CloverSet();
+}
+
+// Cached clover term for (kappa, c_sw); builds it if needed (LRU of 8).
+sq_status find_clover(sq_ctx* c, double kappa, double csw, CloverSet** out) {
+  for (auto& cs : c->clover)
+    if (cs.A64 && cs.kappa == kappa && cs.csw == csw) {
+      cs.tick = ++c->tick;
+      *out = &cs;
+      return SQ_OK;
+    }
+  if (!c->have_gauge) return set_error(c, SQ_ERR_STATE, "clover: no gauge field loaded");
+  if (c->clover.size() < 8) c->clover.resize(c->clover.size() + 1);
+  size_t victim = 0;
+  for (size_t i = 0; i < c->clover.size(); i++) {
+    if (!c->clover[i].A64) { victim = i; break; }
+    if (c->clover[i].tick < c->clover[victim].tick) victim = i;
+  }
+  CloverSet& cs = c->clover[victim];
+  free_clover(cs);
+  const size_t Vh = c->Vh;
+  cudaError_t e = cudaMalloc((void**)&cs.A64, 2 * 36 * Vh * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&cs.Ainv64, 2 * 36 * Vh * sizeof(double2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&cs.Ainv32, 2 * 18 * Vh * sizeof(float4));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&cs.Ainv16, 2 * 9 * Vh * sizeof(uint4));
+  if (e != cudaSuccess) {
+    free_clover(cs);
+    return cuda_check(c, e, "clover allocation");
+  }
+  sq_status s = clover_build(c, cs, kappa, csw);
+  int bits = 0;
+  if (s == SQ_OK) s = read_error_word(c, &bits);
+  if (s == SQ_OK && (bits & ERRBIT_CLOVER)) {
+    free_clover(cs);
+    return set_error(c, SQ_ERR_CLOVER, "clover: a 6x6 block is singular for kappa=%g c_sw=%g", kappa, csw);
+  }
+  if (s != SQ_OK) {
+    free_clover(cs);
+    return s;
+  }
+  cs.tick = ++c->tick;
+  *out = &cs;
+  return SQ_OK;
+}
+
+}  // namespace sq
+
+using namespace sq;
+
+extern "C" {
+
+void sq_default_params(sq_solve_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->inner_prec = SQ_F32;
+  p->outer = SQ_OUTER_RELIABLE;
+  p->delta = 0.1;
+  p->max_iter = 20000;
+  p->recon = 12;
+  p->chunk = 16;
+  p->use_graph = 1;
+  p->io = SQ_HOST;
+}
+
+const char* sq_status_string(sq_status s) {
+  switch (s) {
+    case SQ_OK: return "SQ_OK";
+    case SQ_ERR_ARG: return "SQ_ERR_ARG: invalid argument";
+    case SQ_ERR_CUDA: return "SQ_ERR_CUDA: CUDA runtime error";
+    case SQ_ERR_OOM: return "SQ_ERR_OOM: out of device memory";
+    case SQ_ERR_NONFINITE: return "SQ_ERR_NONFINITE: NaN or Inf in the input";
+    case SQ_ERR_CLOVER: return "SQ_ERR_CLOVER: singular clover block";
+    case SQ_ERR_NOCONV: return "SQ_ERR_NOCONV: not converged within max_iter";
+    case SQ_ERR_BREAKDOWN: return "SQ_ERR_BREAKDOWN: BiCGStab breakdown";
+    case SQ_ERR_TIMEOUT: return "SQ_ERR_TIMEOUT: device-side wait timed out";
+    case SQ_ERR_STATE: return "SQ_ERR_STATE: call made in the wrong state";
+  }
+  return "unknown status";
+}
+
+const char* sq_last_error(const sq_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
+
+sq_status sq_create(sq_ctx** out, const int dims[4], int t_bc, void* cuda_stream) {
+  if (!out || !dims) return SQ_ERR_ARG;
+  *out = nullptr;
+  long long V = 1;
+  for (int i = 0; i < 4; i++) {
+    if (dims[i] < 2 || (dims[i] & 1)) return SQ_ERR_ARG;
+    V *= dims[i];
+  }
+  if (V / 2 > (1LL << 30) / 36) return SQ_ERR_ARG;  // 32-bit site indices in every kernel
+  if (t_bc != 1 && t_bc != -1) return SQ_ERR_ARG;
+  sq_ctx* c = new sq_ctx();
+  for (int i = 0; i < 4; i++) c->dims[i] = dims[i];
+  c->V = (int)V;
+  c->Vh = (int)(V / 2);
+  c->t_bc = t_bc;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (c->stream) cudaStreamDestroy(c->stream);
+    if (c->ev) cudaEventDestroy(c->ev);
+    if (c->d_err) cudaFree(c->d_err);
+    delete c;
+    return e == cudaErrorMemoryAllocation ? SQ_ERR_OOM : SQ_ERR_CUDA;
+  }
+  c->user_stream = (cudaStream_t)cuda_stream;
+  *out = c;
+  return SQ_OK;
+}
+
+sq_status sq_destroy(sq_ctx* c) {
+  if (!c) return SQ_OK;
+  cudaStreamSynchronize(c->stream);
+  if (c->ws.graph) cudaGraphExecDestroy(c->ws.graph);
+  if (c->ws.base) cudaFree(c->ws.base);
+  for (auto& cs : c->clover) free_clover(cs);
+  cudaFree(c->U64);
+  cudaFree(c->U32);
+  cudaFree(c->U16);
+  cudaFree(c->d_err);
+  cudaEventDestroy(c->ev);
+  cudaStreamDestroy(c->stream);
+  delete c;
+  return SQ_OK;
+}
+
+sq_status sq_load_gauge(sq_ctx* c, const double* U, int recon, int where) {
+  if (!c) return SQ_ERR_ARG;
+  if (!U) return set_error(c, SQ_ERR_ARG, "sq_load_gauge: null U");
+  if (recon != 12 && recon != 18) return set_error(c, SQ_ERR_ARG, "sq_load_gauge: recon must be 12 or 18");
+  if (where != SQ_HOST && where != SQ_DEVICE) return set_error(c, SQ_ERR_ARG, "sq_load_gauge: bad where");
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  const size_t Vh = c->Vh;
+  for (auto& cs : c->clover) free_clover(cs);
+  c->clover.clear();
+  c->tuned.clear();
+  cudaFree(c->U64);
+  cudaFree(c->U32);
+  cudaFree(c->U16);
+  c->U64 = nullptr;
+  c->U32 = nullptr;
+  c->U16 = nullptr;
+  c->have_gauge = 0;
+  c->recon = recon;
+  cudaError_t e = cudaMalloc((void**)&c->U64, 2 * 4 * 9 * Vh * sizeof(double2));
+  if (e == cudaSuccess)
+    e = cudaMalloc(&c->U32, recon == 12 ? 2 * 4 * 3 * Vh * sizeof(float4) : 2 * 4 * 9 * Vh * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->U16, 2 * 4 * 3 * Vh * sizeof(uint2));
+  if (e != cudaSuccess) return cuda_check(c, e, "gauge allocation");
+  const size_t nd = (size_t)c->V * 4 * 18;
+  const double* dU = U;
+  double* stage = nullptr;
+  if (where == SQ_HOST) {
+    e = cudaMallocAsync((void**)&stage, nd * sizeof(double), c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "gauge staging");
+    cudaMemcpyAsync(stage, U, nd * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    dU = stage;
+  }
+  s = gauge_convert(c, dU);
+  if (stage) cudaFreeAsync(stage, c->stream);
+  int bits = 0;
+  if (s == SQ_OK) s = read_error_word(c, &bits);
+  if (s != SQ_OK) return s;
+  if (bits & ERRBIT_NONFINITE) return set_error(c, SQ_ERR_NONFINITE, "sq_load_gauge: NaN or Inf in U");
+  c->su3 = !(bits & ERRBIT_NOT_SU3);
+  if (!c->su3 && recon == 12)
+    return set_error(c, SQ_ERR_ARG, "sq_load_gauge: links are not SU(3); reconstruct-12 needs SU(3) (use 18)");
+  c->have_gauge = 1;
+  return leave_stream(c);
+}
+
+sq_status sq_build_clover(sq_ctx* c, double kappa, double csw) {
+  if (!c) return SQ_ERR_ARG;
+  if (!std::isfinite(kappa) || !std::isfinite(csw))
+    return set_error(c, SQ_ERR_ARG, "sq_build_clover: non-finite kappa or c_sw");
+  if (!c->have_gauge) return set_error(c, SQ_ERR_STATE, "sq_build_clover: no gauge field loaded");
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  CloverSet* cs = nullptr;
+  s = find_clover(c, kappa, csw, &cs);
+  if (s != SQ_OK) return s;
+  c->cur_clover = (int)(cs - c->clover.data());
+  return leave_stream(c);
+}
+
+sq_status sq_field_bytes(const sq_ctx* c, sq_prec prec, int n, size_t* bytes) {
+  if (!c || !bytes || n < 0 || prec < SQ_F64 || prec > SQ_F16) return SQ_ERR_ARG;
+  *bytes = field_bytes(c->Vh, prec, n);
+  return SQ_OK;
+}
+
+static sq_status stage_in(sq_ctx* c, const double* lex, int n, int where, const double** dev, double** tmp) {
+  *tmp = nullptr;
+  *dev = lex;
+  if (where == SQ_DEVICE) return SQ_OK;
+  const size_t b = (size_t)n * c->V * 24 * sizeof(double);
+  cudaError_t e = cudaMallocAsync((void**)tmp, b, c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "staging buffer");
+  e = cudaMemcpyAsync(*tmp, lex, b, cudaMemcpyHostToDevice, c->stream);
+  *dev = *tmp;
+  return cuda_check(c, e, "host to device copy");
+}
+
+sq_status sq_pack_spinor(sq_ctx* c, void* eo_out, const double* lex_in, int parity, sq_prec prec, int n,
+                         int where) {
+  if (!c) return SQ_ERR_ARG;
+  if (!eo_out || !lex_in || n <= 0 || (parity != 0 && parity != 1) || prec < SQ_F64 || prec > SQ_F16 ||
+      (where != SQ_HOST && where != SQ_DEVICE))
+    return set_error(c, SQ_ERR_ARG, "sq_pack_spinor: bad argument");
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  const double* dev;
+  double* tmp;
+  s = stage_in(c, lex_in, n, where, &dev, &tmp);
+  if (s != SQ_OK) return s;
+  launch_pack(c, make_field(eo_out, c->Vh, prec, n), dev, parity, prec, n, c->stream);
+  if (tmp) cudaFreeAsync(tmp, c->stream);
+  cudaError_t e = where == SQ_HOST ? cudaStreamSynchronize(c->stream) : cudaGetLastError();
+  s = cuda_check(c, e, "sq_pack_spinor");
+  if (s != SQ_OK) return s;
+  return leave_stream(c);
+}
+
+sq_status sq_unpack_spinor(sq_ctx* c, double* lex_out, const void* eo_in, int parity, sq_prec prec, int n,
+                           int where) {
+  if (!c) return SQ_ERR_ARG;
+  if (!eo_in || !lex_out || n <= 0 || (parity != 0 && parity != 1) || prec < SQ_F64 || prec > SQ_F16 ||
+      (where != SQ_HOST && where != SQ_DEVICE))
+    return set_error(c, SQ_ERR_ARG, "sq_unpack_spinor: bad argument");
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  const size_t b = (size_t)n * c->V * 24 * sizeof(double);
+  double* dev = lex_out;
+  if (where == SQ_HOST) {
+    cudaError_t e = cudaMallocAsync((void**)&dev, b, c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "staging buffer");
+    // the other parity's sites must come back unchanged
+    cudaMemcpyAsync(dev, lex_out, b, cudaMemcpyHostToDevice, c->stream);
+  }
+  launch_unpack(c, dev, make_field((void*)eo_in, c->Vh, prec, n), parity, prec, n, c->stream);
+  cudaError_t e = cudaGetLastError();
+  if (where == SQ_HOST) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lex_out, dev, b, cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(dev, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  }
+  s = cuda_check(c, e, "sq_unpack_spinor");
+  if (s != SQ_OK) return s;
+  return leave_stream(c);
+}
+
+sq_status sq_dslash_eo(sq_ctx* c, void* out, const void* in, const void* x, int out_parity, sq_prec prec, int n,
+                       int flags, double a) {
+  if (!c) return SQ_ERR_ARG;
+  if (!out || !in || n <= 0 || (out_parity != 0 && out_parity != 1) || prec < SQ_F64 || prec > SQ_F16)
+    return set_error(c, SQ_ERR_ARG, "sq_dslash_eo: bad argument");
+  if ((flags & SQ_DS_XPAY) && !x) return set_error(c, SQ_ERR_ARG, "sq_dslash_eo: XPAY needs x");
+  if (out == in) return set_error(c, SQ_ERR_ARG, "sq_dslash_eo: in must not alias out");
+  if (!c->have_gauge) return set_error(c, SQ_ERR_STATE, "sq_dslash_eo: no gauge field loaded");
+  if (prec == SQ_F16 && !c->su3) return set_error(c, SQ_ERR_ARG, "sq_dslash_eo: FP16 links need SU(3) links");
+  const CloverSet* cs = nullptr;
+  if (flags & SQ_DS_CLOVER_INV) {
+    if (c->cur_clover < 0 || c->cur_clover >= (int)c->clover.size() || !c->clover[c->cur_clover].A64)
+      return set_error(c, SQ_ERR_STATE, "sq_dslash_eo: no clover term built");
+    cs = &c->clover[c->cur_clover];
+  }
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  DslashCall d;
+  memset(&d, 0, sizeof(d));
+  d.out = make_field(out, c->Vh, prec, n);
+  d.in = make_field((void*)in, c->Vh, prec, n);
+  d.x = make_field((void*)x, c->Vh, prec, n);
+  d.p_out = out_parity;
+  d.prec = prec;
+  d.recon = prec == SQ_F64 ? 18 : (prec == SQ_F16 ? 12 : c->recon);
+  d.clover = (flags & SQ_DS_CLOVER_INV) ? 1 : 0;
+  d.xpay = (flags & SQ_DS_XPAY) ? 1 : 0;
+  d.a = a;
+  d.cs = cs;
+  d.n = n;
+  d.fin = FIN_NONE;
+  d.shape.sx = 64;
+  d.shape.ry = n >= 4 ? 4 : (n >= 2 ? 2 : 1);
+  launch_dslash(c, d, c->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && (flags & SQ_DS_SYNC)) e = cudaStreamSynchronize(c->stream);
+  s = cuda_check(c, e, "sq_dslash_eo");
+  if (s != SQ_OK) return s;
+  return leave_stream(c);
+}
+
+sq_status sq_apply_M(sq_ctx* c, double* out, const double* in, int n, double kappa, double csw, int where) {
+  if (!c) return SQ_ERR_ARG;
+  if (!out || !in || n <= 0 || (where != SQ_HOST && where != SQ_DEVICE) || !std::isfinite(kappa) ||
+      !std::isfinite(csw))
+    return set_error(c, SQ_ERR_ARG, "sq_apply_M: bad argument");
+  if (!c->have_gauge) return set_error(c, SQ_ERR_STATE, "sq_apply_M: no gauge field loaded");
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  CloverSet* cs = nullptr;
+  s = find_clover(c, kappa, csw, &cs);
+  if (s != SQ_OK) return s;
+  const double* dev;
+  double* tmp;
+  s = stage_in(c, in, n, where, &dev, &tmp);
+  if (s != SQ_OK) return s;
+  const size_t fb = field_bytes(c->Vh, P64, n);
+  char* f = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&f, 4 * fb, c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "sq_apply_M buffers");
+  Field ie = make_field(f, c->Vh, P64, n), io = make_field(f + fb, c->Vh, P64, n);
+  Field oe = make_field(f + 2 * fb, c->Vh, P64, n), oo = make_field(f + 3 * fb, c->Vh, P64, n);
+  Field none = make_field(nullptr, c->Vh, P64, n);
+  launch_pack(c, ie, dev, 0, P64, n, c->stream);
+  launch_pack(c, io, dev, 1, P64, n, c->stream);
+  // out_p = A_pp in_p - kappa D_{p,1-p} in_{1-p}
+  launch_clover64(c, *cs, oe, none, ie, 0, 0.0, 1.0, 0, n, c->stream);
+  launch_clover64(c, *cs, oo, none, io, 1, 0.0, 1.0, 0, n, c->stream);
+  DslashCall d;
+  memset(&d, 0, sizeof(d));
+  d.prec = P64;
+  d.recon = 18;
+  d.xpay = 1;
+  d.a = -kappa;
+  d.n = n;
+  d.shape.sx = 64;
+  d.shape.ry = 1;
+  d.out = oe; d.in = io; d.x = oe; d.p_out = 0;
+  launch_dslash(c, d, c->stream);
+  d.out = oo; d.in = ie; d.x = oo; d.p_out = 1;
+  launch_dslash(c, d, c->stream);
+  double* dout = out;
+  double* otmp = nullptr;
+  const size_t lb = (size_t)n * c->V * 24 * sizeof(double);
+  if (where == SQ_HOST) {
+    e = cudaMallocAsync((void**)&otmp, lb, c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "sq_apply_M output staging");
+    dout = otmp;
+  }
+  launch_unpack(c, dout, oe, 0, P64, n, c->stream);
+  launch_unpack(c, dout, oo, 1, P64, n, c->stream);
+  if (where == SQ_HOST) cudaMemcpyAsync(out, otmp, lb, cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(f, c->stream);
+  if (tmp) cudaFreeAsync(tmp, c->stream);
+  if (otmp) cudaFreeAsync(otmp, c->stream);
+  e = cudaStreamSynchronize(c->stream);
+  s = cuda_check(c, e, "sq_apply_M");
+  if (s != SQ_OK) return s;
+  return leave_stream(c);
+}
+
+sq_status sq_solve(sq_ctx* c, double kappa, double csw, const double* sources, double* solutions, int n,
+                   double tol, const sq_solve_params* params, sq_solve_stats* stats) {
+  if (!c) return SQ_ERR_ARG;
+  if (params && params->inner_prec == SQ_F16 && c->have_gauge && !c->su3)
+    return set_error(c, SQ_ERR_ARG, "sq_solve: FP16 inner solves need SU(3) links");
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  s = solve_impl(c, kappa, csw, sources, solutions, n, tol, params, stats);
+  sq_status s2 = leave_stream(c);
+  return s != SQ_OK ? s : s2;
+}
+
+sq_status sq_contract_pion(sq_ctx* c, const double* sol, int n, const int* tsl, double* C, int where) {
+  if (!c) return SQ_ERR_ARG;
+  if (!sol || !C || n <= 0 || (where != SQ_HOST && where != SQ_DEVICE))
+    return set_error(c, SQ_ERR_ARG, "sq_contract_pion: bad argument");
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  const double* dev;
+  double* tmp;
+  s = stage_in(c, sol, n, where, &dev, &tmp);
+  if (s != SQ_OK) return s;
+  const int T = c->dims[3];
+  double* dC = nullptr;
+  int* dt = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&dC, (size_t)n * T * sizeof(double), c->stream);
+  if (e == cudaSuccess && tsl) {
+    e = cudaMallocAsync((void**)&dt, n * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tsl, n * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+  }
+  if (e != cudaSuccess) return cuda_check(c, e, "sq_contract_pion buffers");
+  launch_pion(c, dev, n, dt, dC, c->stream);
+  e = cudaMemcpyAsync(C, dC, (size_t)n * T * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  cudaFreeAsync(dC, c->stream);
+  if (dt) cudaFreeAsync(dt, c->stream);
+  if (tmp) cudaFreeAsync(tmp, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  s = cuda_check(c, e, "sq_contract_pion");
+  if (s != SQ_OK) return s;
+  return leave_stream(c);
+}
+
+sq_status sq_solve_batch(const sq_problem* probs, int n_probs, const sq_solve_params* params,
+                         sq_solve_stats* stats) {
+  if (!probs || n_probs <= 0) return SQ_ERR_ARG;
+  // Problems are solved one after the other until the fused batch path is in.
+  sq_status worst = SQ_OK;
+  size_t off = 0;
+  for (int i = 0; i < n_probs; i++) {
+    const sq_problem& p = probs[i];
+    if (!p.ctx) return SQ_ERR_ARG;
+    sq_status s = sq_solve(p.ctx, p.kappa, p.c_sw, p.sources, p.solutions, p.n_rhs, p.tol, params,
+                           stats ? stats + off : nullptr);
+    off += p.n_rhs > 0 ? p.n_rhs : 0;
+    if (s != SQ_OK && worst == SQ_OK) worst = s;
+  }
+  return worst;
+}
+
+}  // extern "C"

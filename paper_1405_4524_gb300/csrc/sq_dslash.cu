@@ -1,0 +1,332 @@
+// G1: even-odd Wilson hopping term with fused clover inverse, xpay and
+// reductions, for FP64 / FP32 / FP16 fields and many sources per CTA.
+//
+// Operator (the kappa-normalised clover-Wilson matrix M = A - kappa D, with
+// D psi(x) = sum_mu (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^+ psi(x-mu)),
+// restricted to hops from parity 1-p onto parity p. Each hop is done on a
+// half spinor: in the DeGrand-Rossi basis g_mu = [[0, B_mu], [B_mu^+, 0]] in
+// 2x2 spin blocks, so (1 -+ g_mu) psi = [h; -+ B_mu^+ h] with
+// h = psi_up -+ B_mu psi_dn: two SU(3) mat-vecs per hop instead of four.
+//
+// CTA = sx sites (threadIdx.x, consecutive checkerboard sites: every spinor
+// and link chunk load of a warp is one contiguous 128-bit-per-lane segment)
+// times ry sources (threadIdx.y). The ry sources of a CTA read the same
+// links and clover blocks, so those come from HBM once per CTA and from L1
+// for the other sources.
+#include <cstdio>
+
+#include "sq_internal.h"
+
+namespace sq {
+
+struct KArgs {
+  Geom g;
+  Field out, in, x, r1;
+  const void* links;
+  const void* clov;
+  int p_out;
+  double a;
+  const int* list;
+  const int* count;
+  int n;
+  RedArgs ra;
+};
+
+// h = psi_up + SIGN * B_mu psi_dn   (SIGN = -1: forward hop, +1: backward)
+template <int MU, int SIGN, typename R>
+__device__ __forceinline__ void project(const cx<R> v[12], cx<R> h[6]) {
+  const R sg = (R)SIGN;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    cx<R> d0, d1;
+    if (MU == 0) {  // B = [[0, i], [i, 0]]
+      d0 = itimes(v[9 + c]);
+      d1 = itimes(v[6 + c]);
+    } else if (MU == 1) {  // B = [[0, -1], [1, 0]]
+      d0 = mk(-v[9 + c].re, -v[9 + c].im);
+      d1 = v[6 + c];
+    } else if (MU == 2) {  // B = [[i, 0], [0, -i]]
+      d0 = itimes(v[6 + c]);
+      d1 = mk(v[9 + c].im, -v[9 + c].re);
+    } else {  // B = 1
+      d0 = v[6 + c];
+      d1 = v[9 + c];
+    }
+    h[c] = mk(v[c].re + sg * d0.re, v[c].im + sg * d0.im);
+    h[3 + c] = mk(v[3 + c].re + sg * d1.re, v[3 + c].im + sg * d1.im);
+  }
+}
+
+// acc_up += w ; acc_dn += SIGN * B_mu^+ w
+template <int MU, int SIGN, typename R>
+__device__ __forceinline__ void accum(cx<R> acc[12], const cx<R> w[6]) {
+  const R sg = (R)SIGN;
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    acc[c] = acc[c] + w[c];
+    acc[3 + c] = acc[3 + c] + w[3 + c];
+    cx<R> e0, e1;
+    if (MU == 0) {  // B^+ = [[0, -i], [-i, 0]]
+      e0 = mk(w[3 + c].im, -w[3 + c].re);
+      e1 = mk(w[c].im, -w[c].re);
+    } else if (MU == 1) {  // B^+ = [[0, 1], [-1, 0]]
+      e0 = w[3 + c];
+      e1 = mk(-w[c].re, -w[c].im);
+    } else if (MU == 2) {  // B^+ = [[-i, 0], [0, i]]
+      e0 = mk(w[c].im, -w[c].re);
+      e1 = itimes(w[3 + c]);
+    } else {
+      e0 = w[c];
+      e1 = w[3 + c];
+    }
+    acc[6 + c] = mk(acc[6 + c].re + sg * e0.re, acc[6 + c].im + sg * e0.im);
+    acc[9 + c] = mk(acc[9 + c].re + sg * e1.re, acc[9 + c].im + sg * e1.im);
+  }
+}
+
+// w[s] = U h[s]
+template <typename R>
+__device__ __forceinline__ void mv(const Link<R>& u, const cx<R> h[6], cx<R> w[6]) {
+#pragma unroll
+  for (int s = 0; s < 2; s++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      cx<R> r = u.e[3 * a] * h[3 * s];
+      r = cfma(u.e[3 * a + 1], h[3 * s + 1], r);
+      r = cfma(u.e[3 * a + 2], h[3 * s + 2], r);
+      w[3 * s + a] = r;
+    }
+}
+
+// w[s] = U^+ h[s]
+template <typename R>
+__device__ __forceinline__ void mv_dag(const Link<R>& u, const cx<R> h[6], cx<R> w[6]) {
+#pragma unroll
+  for (int s = 0; s < 2; s++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      cx<R> r = cmul(u.e[a], h[3 * s]);
+      r = cjfma(u.e[3 + a], h[3 * s + 1], r);
+      r = cjfma(u.e[6 + a], h[3 * s + 2], r);
+      w[3 * s + a] = r;
+    }
+}
+
+template <int P, int RECON, int MU>
+__device__ __forceinline__ void hop_dir(const KArgs& a, int k, int cb, Coord c,
+                                        cx<typename Real<P>::T> acc[12]) {
+  typedef typename Real<P>::T R;
+  {  // forward: (1 - g_mu) U_mu(x) psi(x + mu)
+    Coord n = step(a.g, c, MU, +1);
+    int ncb = cb_of(a.g, n.x, n.y, n.z, n.t);
+    cx<R> v[12], h[6], w[6];
+    SpinorIO<P>::load(a.in, k, ncb, v);
+    project<MU, -1>(v, h);
+    Link<R> u;
+    LinkIO<P, RECON>::load(a.links, a.g.Vh, a.p_out, MU, cb, u);
+    mv(u, h, w);
+    if (MU == 3 && c.t == a.g.T - 1) {
+      const R f = (R)a.g.tbc;
+#pragma unroll
+      for (int j = 0; j < 6; j++) w[j] = f * w[j];
+    }
+    accum<MU, -1>(acc, w);
+  }
+  {  // backward: (1 + g_mu) U_mu(x - mu)^+ psi(x - mu)
+    Coord n = step(a.g, c, MU, -1);
+    int ncb = cb_of(a.g, n.x, n.y, n.z, n.t);
+    cx<R> v[12], h[6], w[6];
+    SpinorIO<P>::load(a.in, k, ncb, v);
+    project<MU, +1>(v, h);
+    Link<R> u;
+    LinkIO<P, RECON>::load(a.links, a.g.Vh, 1 - a.p_out, MU, ncb, u);
+    mv_dag(u, h, w);
+    if (MU == 3 && c.t == 0) {
+      const R f = (R)a.g.tbc;
+#pragma unroll
+      for (int j = 0; j < 6; j++) w[j] = f * w[j];
+    }
+    accum<MU, +1>(acc, w);
+  }
+}
+
+template <int P, int RECON, int CLOV, int XPAY, int FIN>
+__global__ void __launch_bounds__(256) k_dslash(const KArgs a) {
+  typedef typename Real<P>::T R;
+  constexpr int NRED = FIN == FIN_ALPHA ? 2 : FIN == FIN_OMEGA ? 3 : 1;
+  const int cnt = a.list ? *a.count : a.n;
+  const int slot0 = blockIdx.y * blockDim.y;
+  if (slot0 >= cnt) return;  // whole CTA idle (uniform)
+  const int slot = slot0 + threadIdx.y;
+  const int k = slot < cnt ? (a.list ? a.list[slot] : slot) : -1;
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ok = (k >= 0) && (cb < a.g.Vh);
+  double red[NRED];
+#pragma unroll
+  for (int i = 0; i < NRED; i++) red[i] = 0.0;
+  if (ok) {
+    cx<R> acc[12];
+#pragma unroll
+    for (int j = 0; j < 12; j++) acc[j] = zero<R>();
+    const Coord c = cb_coords(a.g, cb, a.p_out);
+    hop_dir<P, RECON, 0>(a, k, cb, c, acc);
+    hop_dir<P, RECON, 1>(a, k, cb, c, acc);
+    hop_dir<P, RECON, 2>(a, k, cb, c, acc);
+    hop_dir<P, RECON, 3>(a, k, cb, c, acc);
+    if (CLOV) {
+      cx<R> w[6];
+      R blk[36];
+      CloverIO<P>::template load_block<0>(a.clov, a.g.Vh, a.p_out, cb, blk);
+      herm6_apply(blk, acc, w);
+#pragma unroll
+      for (int j = 0; j < 6; j++) acc[j] = w[j];
+      CloverIO<P>::template load_block<1>(a.clov, a.g.Vh, a.p_out, cb, blk);
+      herm6_apply(blk, acc + 6, w);
+#pragma unroll
+      for (int j = 0; j < 6; j++) acc[6 + j] = w[j];
+    }
+    cx<R> xv[12];
+    if (XPAY) {
+      SpinorIO<P>::load(a.x, k, cb, xv);
+      const R f = (R)a.a;
+#pragma unroll
+      for (int j = 0; j < 12; j++) acc[j] = mk(xv[j].re + f * acc[j].re, xv[j].im + f * acc[j].im);
+    }
+    SpinorIO<P>::store(a.out, k, cb, acc);
+    if (FIN == FIN_ALPHA) {  // <r1, out>
+      cx<R> rv[12];
+      SpinorIO<P>::load(a.r1, k, cb, rv);
+      R sr = 0, si = 0;
+#pragma unroll
+      for (int j = 0; j < 12; j++) {
+        sr += rv[j].re * acc[j].re + rv[j].im * acc[j].im;
+        si += rv[j].re * acc[j].im - rv[j].im * acc[j].re;
+      }
+      red[0] = sr;
+      red[1] = si;
+    } else if (FIN == FIN_OMEGA) {  // <out, x>, <out, out>
+      R sr = 0, si = 0, tt = 0;
+#pragma unroll
+      for (int j = 0; j < 12; j++) {
+        sr += acc[j].re * xv[j].re + acc[j].im * xv[j].im;
+        si += acc[j].re * xv[j].im - acc[j].im * xv[j].re;
+        tt += acc[j].re * acc[j].re + acc[j].im * acc[j].im;
+      }
+      red[0] = sr;
+      red[1] = si;
+      red[2] = tt;
+    } else if (FIN == FIN_TRUE) {
+      R tt = 0;
+#pragma unroll
+      for (int j = 0; j < 12; j++) tt += acc[j].re * acc[j].re + acc[j].im * acc[j].im;
+      red[0] = tt;
+    }
+  }
+  if (FIN != FIN_NONE) reduce_finalize<NRED, FIN>(a.ra, red, k);
+}
+
+// ---------------------------------------------------------------------------
+// host launcher
+// ---------------------------------------------------------------------------
+int dslash_nblk(const sq_ctx* c, Shape sh) { return (c->Vh + sh.sx - 1) / sh.sx; }
+
+template <int P, int RECON, int CLOV, int XPAY, int FIN>
+static void go(const KArgs& a, dim3 grid, dim3 block, cudaStream_t s) {
+  k_dslash<P, RECON, CLOV, XPAY, FIN><<<grid, block, 0, s>>>(a);
+}
+
+template <int P, int RECON>
+static bool dispatch_mode(const DslashCall& d, const KArgs& a, dim3 grid, dim3 block, cudaStream_t s) {
+  const int m = (d.clover ? 1 : 0) | (d.xpay ? 2 : 0);
+  if (d.fin == FIN_NONE) {
+    switch (m) {
+      case 0: go<P, RECON, 0, 0, FIN_NONE>(a, grid, block, s); return true;
+      case 1: go<P, RECON, 1, 0, FIN_NONE>(a, grid, block, s); return true;
+      case 2: go<P, RECON, 0, 1, FIN_NONE>(a, grid, block, s); return true;
+      case 3: go<P, RECON, 1, 1, FIN_NONE>(a, grid, block, s); return true;
+    }
+  }
+  if (m != 3) return false;
+  if (d.fin == FIN_ALPHA) { go<P, RECON, 1, 1, FIN_ALPHA>(a, grid, block, s); return true; }
+  if (d.fin == FIN_OMEGA) { go<P, RECON, 1, 1, FIN_OMEGA>(a, grid, block, s); return true; }
+  return false;
+}
+
+void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s) {
+  KArgs a;
+  a.g = geom_of(c);
+  a.out = d.out;
+  a.in = d.in;
+  a.x = d.x;
+  a.r1 = d.r1;
+  a.p_out = d.p_out;
+  a.a = d.a;
+  a.list = d.list;
+  a.count = d.count;
+  a.n = d.n;
+  a.ra = d.ra;
+  a.clov = nullptr;
+  if (d.clover && d.cs) {
+    a.clov = d.prec == P64 ? (const void*)d.cs->Ainv64
+           : d.prec == P32 ? (const void*)d.cs->Ainv32 : (const void*)d.cs->Ainv16;
+  }
+  a.links = d.prec == P64 ? (const void*)c->U64 : d.prec == P32 ? c->U32 : (const void*)c->U16;
+  dim3 block(d.shape.sx, d.shape.ry);
+  dim3 grid((c->Vh + d.shape.sx - 1) / d.shape.sx, (d.n + d.shape.ry - 1) / d.shape.ry);
+  bool ok = false;
+  if (d.prec == P64) {
+    if (d.fin == FIN_TRUE && d.clover && d.xpay) {
+      go<P64, 18, 1, 1, FIN_TRUE>(a, grid, block, s);
+      ok = true;
+    } else {
+      ok = dispatch_mode<P64, 18>(d, a, grid, block, s);
+    }
+  } else if (d.prec == P32) {
+    ok = d.recon == 18 ? dispatch_mode<P32, 18>(d, a, grid, block, s)
+                       : dispatch_mode<P32, 12>(d, a, grid, block, s);
+  } else {
+    ok = dispatch_mode<P16, 12>(d, a, grid, block, s);
+  }
+  if (!ok) fprintf(stderr, "libstochq: internal error: no dslash variant for this call\n");
+}
+
+// Pick (sites, sources) per CTA by timing the candidates on the call's own
+// fields (no reduction). Results are cached per (precision, recon, Vh, n).
+Shape tune_dslash(sq_ctx* c, DslashCall d, cudaStream_t s) {
+  long long key = ((long long)d.prec << 56) ^ ((long long)d.recon << 48) ^ ((long long)c->Vh << 12) ^ d.n;
+  auto it = c->tuned.find(key);
+  if (it != c->tuned.end()) return it->second;
+  static const int cand[][2] = {{32, 1}, {32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2},
+                                {64, 4}, {128, 1}, {128, 2}, {256, 1}};
+  d.fin = FIN_NONE;
+  d.list = nullptr;
+  d.count = nullptr;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  Shape best;
+  float best_ms = 1e30f;
+  for (auto& cd : cand) {
+    if (cd[1] > 1 && cd[1] > d.n) continue;
+    d.shape.sx = cd[0];
+    d.shape.ry = cd[1];
+    for (int w = 0; w < 2; w++) launch_dslash(c, d, s);
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 5; r++) launch_dslash(c, d, s);
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (cudaGetLastError() != cudaSuccess) continue;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = d.shape;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->tuned[key] = best;
+  return best;
+}
+
+}  // namespace sq

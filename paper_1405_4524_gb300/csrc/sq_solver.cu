@@ -1,0 +1,663 @@
+// Batched even-odd BiCGStab for the clover-Wilson system M psi = eta, one
+// Krylov recurrence per source, all sources advanced by the same kernels.
+//
+// Schur system on even sites (M = [[A_ee, -k D_eo], [-k D_oe, A_oo]]):
+//   Mhat = 1 - k^2 A_ee^{-1} D_eo A_oo^{-1} D_oe,
+//   bhat = A_ee^{-1} (eta_e + k D_eo A_oo^{-1} eta_o),
+//   psi_o = A_oo^{-1} (eta_o + k D_oe psi_e).
+// The full-lattice residual is r_e = A_ee (bhat - Mhat psi_e), r_o = 0, so
+// ||r|| <= max||A|| ||bhat - Mhat psi_e||: the Schur target is
+// tol ||eta|| / max||A||, and the full FP64 residual is checked at the end.
+//
+// Precision: the inner recurrence runs on FP32 or FP16 (per-site norm)
+// fields with FP32 arithmetic; x accumulates in FP32; every FP64 update
+// recomputes r = bhat - Mhat x in FP64 (reliable updates keep the Krylov
+// space, defect correction restarts it). With inner FP64 the same loop is
+// the plain FP64 solver (an FP64 update only to confirm convergence).
+//
+// One iteration = 12 kernels, all reading their per-source scalars and the
+// active / update lists from device memory, so `chunk` iterations are
+// captured once into a CUDA graph and replayed; the host reads one integer
+// (sources still active) per graph launch.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "sq_internal.h"
+
+namespace sq {
+
+static const Shape kBlasShape = {128, 2};
+
+struct VArgs {
+  int Vh;
+  Field f0, f1, f2, f3, f4, f5;
+  RhsState* st;
+  const int* list;
+  const int* count;
+  int n;
+  RedArgs ra;
+};
+
+#define SLOT_PROLOGUE                                           \
+  const int cnt = *a.count;                                     \
+  const int slot0 = blockIdx.y * blockDim.y;                    \
+  if (slot0 >= cnt) return;                                     \
+  const int slot = slot0 + threadIdx.y;                         \
+  const int k = slot < cnt ? a.list[slot] : -1;                 \
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;         \
+  const bool ok = (k >= 0) && (cb < a.Vh);
+
+// s = r - alpha v          f0 = r, f1 = v, f2 = s
+template <int P>
+__global__ void __launch_bounds__(256) k_s_update(const VArgs a) {
+  typedef typename Real<P>::T R;
+  SLOT_PROLOGUE
+  if (!ok) return;
+  const RhsState& q = a.st[k];
+  const R ar = (R)q.alpha_re, ai = (R)q.alpha_im;
+  cx<R> r[12], v[12];
+  SpinorIO<P>::load(a.f0, k, cb, r);
+  SpinorIO<P>::load(a.f1, k, cb, v);
+#pragma unroll
+  for (int j = 0; j < 12; j++)
+    r[j] = mk(r[j].re - (ar * v[j].re - ai * v[j].im), r[j].im - (ar * v[j].im + ai * v[j].re));
+  SpinorIO<P>::store(a.f2, k, cb, r);
+}
+
+// x += alpha p + omega s ; r = s - omega t ; reduce ||r||^2, <rhat, r>
+// f0 = x (PX), f1 = p, f2 = s, f3 = t, f4 = r, f5 = rhat
+template <int P, int PX>
+__global__ void __launch_bounds__(256) k_xr_update(const VArgs a) {
+  typedef typename Real<P>::T R;
+  typedef typename Real<PX>::T RX;
+  SLOT_PROLOGUE
+  double red[3] = {0.0, 0.0, 0.0};
+  if (ok) {
+    const RhsState& q = a.st[k];
+    const R ar = (R)q.alpha_re, ai = (R)q.alpha_im, wr = (R)q.omega_re, wi = (R)q.omega_im;
+    cx<R> p[12], s[12];
+    cx<RX> x[12];
+    SpinorIO<P>::load(a.f1, k, cb, p);
+    SpinorIO<P>::load(a.f2, k, cb, s);
+    SpinorIO<PX>::load(a.f0, k, cb, x);
+#pragma unroll
+    for (int j = 0; j < 12; j++) {
+      R dr = ar * p[j].re - ai * p[j].im + wr * s[j].re - wi * s[j].im;
+      R di = ar * p[j].im + ai * p[j].re + wr * s[j].im + wi * s[j].re;
+      x[j] = mk((RX)(x[j].re + dr), (RX)(x[j].im + di));
+    }
+    SpinorIO<PX>::store(a.f0, k, cb, x);
+    cx<R> t[12], rh[12];
+    SpinorIO<P>::load(a.f3, k, cb, t);
+#pragma unroll
+    for (int j = 0; j < 12; j++)
+      s[j] = mk(s[j].re - (wr * t[j].re - wi * t[j].im), s[j].im - (wr * t[j].im + wi * t[j].re));
+    SpinorIO<P>::store(a.f4, k, cb, s);
+    SpinorIO<P>::load(a.f5, k, cb, rh);
+    R n2 = 0, dr = 0, di = 0;
+#pragma unroll
+    for (int j = 0; j < 12; j++) {
+      n2 += s[j].re * s[j].re + s[j].im * s[j].im;
+      dr += rh[j].re * s[j].re + rh[j].im * s[j].im;
+      di += rh[j].re * s[j].im - rh[j].im * s[j].re;
+    }
+    red[0] = n2;
+    red[1] = dr;
+    red[2] = di;
+  }
+  reduce_finalize<3, FIN_ITER>(a.ra, red, k);
+}
+
+// p = r + beta (p - omega v)     f0 = r, f1 = p, f2 = v
+template <int P>
+__global__ void __launch_bounds__(256) k_p_update(const VArgs a) {
+  typedef typename Real<P>::T R;
+  SLOT_PROLOGUE
+  if (!ok) return;
+  const RhsState& q = a.st[k];
+  const R br = (R)q.beta_re, bi = (R)q.beta_im, wr = (R)q.omega_re, wi = (R)q.omega_im;
+  cx<R> r[12], p[12], v[12];
+  SpinorIO<P>::load(a.f0, k, cb, r);
+  SpinorIO<P>::load(a.f1, k, cb, p);
+  SpinorIO<P>::load(a.f2, k, cb, v);
+#pragma unroll
+  for (int j = 0; j < 12; j++) {
+    R ur = p[j].re - (wr * v[j].re - wi * v[j].im);
+    R ui = p[j].im - (wr * v[j].im + wi * v[j].re);
+    p[j] = mk(r[j].re + br * ur - bi * ui, r[j].im + br * ui + bi * ur);
+  }
+  SpinorIO<P>::store(a.f1, k, cb, p);
+}
+
+// FP64 update, part 1: x64 += xs ; xs = 0 ; r64 = b64 - x64
+// f0 = x64, f1 = xs (PX), f2 = b64, f3 = r64
+template <int PX>
+__global__ void __launch_bounds__(256) k_rel_x(const VArgs a) {
+  typedef typename Real<PX>::T RX;
+  SLOT_PROLOGUE
+  if (!ok) return;
+  cx<double> x[12], b[12];
+  cx<RX> xs[12];
+  SpinorIO<P64>::load(a.f0, k, cb, x);
+  SpinorIO<PX>::load(a.f1, k, cb, xs);
+  SpinorIO<P64>::load(a.f2, k, cb, b);
+#pragma unroll
+  for (int j = 0; j < 12; j++) {
+    x[j] = mk(x[j].re + (double)xs[j].re, x[j].im + (double)xs[j].im);
+    b[j] = b[j] - x[j];
+    xs[j] = mk((RX)0, (RX)0);
+  }
+  SpinorIO<P64>::store(a.f0, k, cb, x);
+  SpinorIO<PX>::store(a.f1, k, cb, xs);
+  SpinorIO<P64>::store(a.f3, k, cb, b);
+}
+
+// FP64 update, part 2: r = r64 ; on restart rhat = r, p = r ; reduce <rhat, r>
+// f0 = r64, f1 = r, f2 = rhat, f3 = p
+template <int P>
+__global__ void __launch_bounds__(256) k_rel_r(const VArgs a) {
+  typedef typename Real<P>::T R;
+  SLOT_PROLOGUE
+  double red[2] = {0.0, 0.0};
+  if (ok) {
+    const bool restart = a.st[k].want_restart != 0;
+    cx<double> r64[12];
+    SpinorIO<P64>::load(a.f0, k, cb, r64);
+    cx<R> r[12], rh[12];
+#pragma unroll
+    for (int j = 0; j < 12; j++) r[j] = mk((R)r64[j].re, (R)r64[j].im);
+    SpinorIO<P>::store(a.f1, k, cb, r);
+    if (restart) {
+      SpinorIO<P>::store(a.f2, k, cb, r);
+      SpinorIO<P>::store(a.f3, k, cb, r);
+#pragma unroll
+      for (int j = 0; j < 12; j++) rh[j] = r[j];
+    } else {
+      SpinorIO<P>::load(a.f2, k, cb, rh);
+    }
+    R dr = 0, di = 0;
+#pragma unroll
+    for (int j = 0; j < 12; j++) {
+      dr += rh[j].re * r[j].re + rh[j].im * r[j].im;
+      di += rh[j].re * r[j].im - rh[j].im * r[j].re;
+    }
+    red[0] = dr;
+    red[1] = di;
+  }
+  reduce_finalize<2, FIN_UPDATE>(a.ra, red, k);
+}
+
+// Rebuild the active list (ascending source index) and clear the update list.
+__global__ void k_control(RhsState* st, Control* ctl, int* active_list, int n) {
+  const int lane = threadIdx.x;
+  int base = 0;
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int k = k0 + lane;
+    const bool on = k < n && st[k].active;
+    const unsigned m = __ballot_sync(0xffffffffu, on);
+    if (on) active_list[base + __popc(m & ((1u << lane) - 1u))] = k;
+    base += __popc(m);
+  }
+  if (lane == 0) {
+    ctl->n_active = base;
+    ctl->n_update = 0;
+  }
+}
+
+// Initial state: every source asks for an FP64 update with restart.
+__global__ void k_init(RhsState* st, Control* ctl, int* update_list, const double* target2, double delta2,
+                       int max_iter, int defect, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) {
+    RhsState q;
+    memset(&q, 0, sizeof(q));
+    q.target2 = target2[k];
+    q.delta2 = delta2;
+    q.max_iter = max_iter;
+    q.defect = defect;
+    q.active = 1;
+    q.want_update = 1;
+    q.want_restart = 1;
+    q.status = 0;
+    q.rho_re = 1.0;
+    q.alpha_re = 1.0;
+    q.omega_re = 1.0;
+    st[k] = q;
+    update_list[k] = k;
+  }
+  if (k == 0) {
+    ctl->n_update = n;
+    ctl->n_active = 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static inline int px_of(int inner) { return inner == P64 ? P64 : P32; }
+
+static void free_ws(sq_ctx* c) {
+  Workspace& w = c->ws;
+  if (w.graph) cudaGraphExecDestroy(w.graph);
+  if (w.base) cudaFree(w.base);
+  w = Workspace();
+}
+
+static sq_status alloc_ws(sq_ctx* c, int n, int inner) {
+  Workspace& w = c->ws;
+  if (w.base && w.n_rhs == n && w.inner == inner) return SQ_OK;
+  free_ws(c);
+  const int Vh = c->Vh;
+  const size_t f64 = field_bytes(Vh, P64, n), fin = field_bytes(Vh, inner, n);
+  const size_t fx = field_bytes(Vh, px_of(inner), n);
+  const int nblk = (Vh + 31) / 32;
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  size_t tot = 0;
+  size_t o_f64 = tot; tot += al(f64) * 7;
+  size_t o_fin = tot; tot += al(fin) * 7;
+  size_t o_fx = tot; tot += al(fx);
+  size_t o_lex = tot; tot += al((size_t)n * c->V * 24 * sizeof(double));
+  size_t o_part = tot; tot += al((size_t)n * nblk * 3 * sizeof(double));
+  size_t o_cnt = tot; tot += al((size_t)n * sizeof(unsigned));
+  size_t o_st = tot; tot += al((size_t)n * sizeof(RhsState));
+  size_t o_ctl = tot; tot += al(sizeof(Control));
+  size_t o_al = tot; tot += al((size_t)n * sizeof(int));
+  size_t o_ul = tot; tot += al((size_t)n * sizeof(int));
+  size_t o_sc = tot; tot += al((size_t)n * 8 * sizeof(double));
+  void* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, tot);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(c, SQ_ERR_OOM, "workspace of %zu bytes for %d sources: %s", tot, n, cudaGetErrorString(e));
+  }
+  char* b = (char*)base;
+  w.base = base;
+  w.bytes = tot;
+  w.n_rhs = n;
+  w.inner = inner;
+  Field* f64s[7] = {&w.b64, &w.x64, &w.r64, &w.t64o, &w.x64o, &w.eta_e, &w.eta_o};
+  for (int i = 0; i < 7; i++) *f64s[i] = make_field(b + o_f64 + al(f64) * i, Vh, P64, n);
+  Field* fins[7] = {&w.r, &w.rh, &w.p, &w.v, &w.s, &w.t, &w.to};
+  for (int i = 0; i < 7; i++) *fins[i] = make_field(b + o_fin + al(fin) * i, Vh, inner, n);
+  w.xs = make_field(b + o_fx, Vh, px_of(inner), n);
+  w.lex = (double*)(b + o_lex);
+  w.partial = (double*)(b + o_part);
+  w.counter = (unsigned*)(b + o_cnt);
+  w.st = (RhsState*)(b + o_st);
+  w.ctl = (Control*)(b + o_ctl);
+  w.active_list = (int*)(b + o_al);
+  w.update_list = (int*)(b + o_ul);
+  w.scal = (double*)(b + o_sc);
+  w.nblk_stride = nblk;
+  cudaMemsetAsync(w.counter, 0, (size_t)n * sizeof(unsigned), c->stream);
+  return SQ_OK;
+}
+
+static RedArgs red_args(const Workspace& w) {
+  RedArgs r;
+  r.partial = w.partial;
+  r.counter = w.counter;
+  r.st = w.st;
+  r.ctl = w.ctl;
+  r.update_list = w.update_list;
+  r.out = w.scal;
+  r.nblk_stride = w.nblk_stride;
+  return r;
+}
+
+static VArgs vargs(const sq_ctx* c, const Workspace& w, bool update_list) {
+  VArgs a;
+  memset(&a, 0, sizeof(a));
+  a.Vh = c->Vh;
+  a.st = w.st;
+  a.list = update_list ? w.update_list : w.active_list;
+  a.count = update_list ? &w.ctl->n_update : &w.ctl->n_active;
+  a.n = w.n_rhs;
+  a.ra = red_args(w);
+  return a;
+}
+
+template <int P, int PX>
+static void launch_iteration(sq_ctx* c, const CloverSet& cs, double kappa, Shape sh, cudaStream_t s) {
+  Workspace& w = c->ws;
+  const int n = w.n_rhs;
+  dim3 bb(kBlasShape.sx, kBlasShape.ry);
+  dim3 bg((c->Vh + kBlasShape.sx - 1) / kBlasShape.sx, (n + kBlasShape.ry - 1) / kBlasShape.ry);
+  DslashCall d;
+  memset(&d, 0, sizeof(d));
+  d.prec = P;
+  d.recon = P == P64 ? 18 : (P == P16 ? 12 : c->recon);
+  d.cs = &cs;
+  d.list = w.active_list;
+  d.count = &w.ctl->n_active;
+  d.n = n;
+  d.ra = red_args(w);
+  d.shape = sh;
+  d.clover = 1;
+  // v = Mhat p ; alpha
+  d.out = w.to; d.in = w.p; d.p_out = 1; d.xpay = 0; d.fin = FIN_NONE;
+  launch_dslash(c, d, s);
+  d.out = w.v; d.in = w.to; d.x = w.p; d.p_out = 0; d.xpay = 1; d.a = -kappa * kappa;
+  d.fin = FIN_ALPHA; d.r1 = w.rh;
+  launch_dslash(c, d, s);
+  VArgs a = vargs(c, w, false);
+  a.f0 = w.r; a.f1 = w.v; a.f2 = w.s;
+  k_s_update<P><<<bg, bb, 0, s>>>(a);
+  // t = Mhat s ; omega
+  d.out = w.to; d.in = w.s; d.p_out = 1; d.xpay = 0; d.fin = FIN_NONE;
+  launch_dslash(c, d, s);
+  d.out = w.t; d.in = w.to; d.x = w.s; d.p_out = 0; d.xpay = 1; d.fin = FIN_OMEGA;
+  launch_dslash(c, d, s);
+  a.f0 = w.xs; a.f1 = w.p; a.f2 = w.s; a.f3 = w.t; a.f4 = w.r; a.f5 = w.rh;
+  k_xr_update<P, PX><<<bg, bb, 0, s>>>(a);
+  a.f0 = w.r; a.f1 = w.p; a.f2 = w.v;
+  k_p_update<P><<<bg, bb, 0, s>>>(a);
+  // FP64 update for the sources that asked for one
+  VArgs u = vargs(c, w, true);
+  u.f0 = w.x64; u.f1 = w.xs; u.f2 = w.b64; u.f3 = w.r64;
+  k_rel_x<PX><<<bg, bb, 0, s>>>(u);
+  DslashCall d64 = d;
+  d64.prec = P64;
+  d64.recon = 18;
+  d64.list = w.update_list;
+  d64.count = &w.ctl->n_update;
+  d64.shape = kBlasShape;
+  d64.out = w.t64o; d64.in = w.x64; d64.p_out = 1; d64.xpay = 0; d64.fin = FIN_NONE;
+  launch_dslash(c, d64, s);
+  d64.out = w.r64; d64.in = w.t64o; d64.x = w.r64; d64.p_out = 0; d64.xpay = 1; d64.a = kappa * kappa;
+  d64.fin = FIN_TRUE;
+  launch_dslash(c, d64, s);
+  u.f0 = w.r64; u.f1 = w.r; u.f2 = w.rh; u.f3 = w.p;
+  k_rel_r<P><<<bg, bb, 0, s>>>(u);
+  k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n);
+}
+
+// the FP64 update alone (used once at the start: r = bhat - Mhat x0)
+template <int P, int PX>
+static void launch_update(sq_ctx* c, const CloverSet& cs, double kappa, cudaStream_t s) {
+  Workspace& w = c->ws;
+  const int n = w.n_rhs;
+  dim3 bb(kBlasShape.sx, kBlasShape.ry);
+  dim3 bg((c->Vh + kBlasShape.sx - 1) / kBlasShape.sx, (n + kBlasShape.ry - 1) / kBlasShape.ry);
+  VArgs u = vargs(c, w, true);
+  u.f0 = w.x64; u.f1 = w.xs; u.f2 = w.b64; u.f3 = w.r64;
+  k_rel_x<PX><<<bg, bb, 0, s>>>(u);
+  DslashCall d64;
+  memset(&d64, 0, sizeof(d64));
+  d64.prec = P64;
+  d64.recon = 18;
+  d64.cs = &cs;
+  d64.clover = 1;
+  d64.list = w.update_list;
+  d64.count = &w.ctl->n_update;
+  d64.n = n;
+  d64.ra = red_args(w);
+  d64.shape = kBlasShape;
+  d64.out = w.t64o; d64.in = w.x64; d64.p_out = 1;
+  launch_dslash(c, d64, s);
+  d64.out = w.r64; d64.in = w.t64o; d64.x = w.r64; d64.p_out = 0; d64.xpay = 1; d64.a = kappa * kappa;
+  d64.fin = FIN_TRUE;
+  launch_dslash(c, d64, s);
+  u.f0 = w.r64; u.f1 = w.r; u.f2 = w.rh; u.f3 = w.p;
+  k_rel_r<P><<<bg, bb, 0, s>>>(u);
+  k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n);
+}
+
+typedef void (*IterFn)(sq_ctx*, const CloverSet&, double, Shape, cudaStream_t);
+typedef void (*UpdFn)(sq_ctx*, const CloverSet&, double, cudaStream_t);
+
+static void fns_for(int inner, IterFn* it, UpdFn* up) {
+  if (inner == P64) { *it = launch_iteration<P64, P64>; *up = launch_update<P64, P64>; }
+  else if (inner == P32) { *it = launch_iteration<P32, P32>; *up = launch_update<P32, P32>; }
+  else { *it = launch_iteration<P16, P32>; *up = launch_update<P16, P32>; }
+}
+
+sq_status find_clover(sq_ctx* c, double kappa, double csw, CloverSet** out);
+
+// FP64 full-lattice residual norms^2 of (x64 even, x64o odd) -> scal[0..n) even, scal[n..2n) odd
+static void launch_full_residual(sq_ctx* c, const CloverSet& cs, double kappa, cudaStream_t s) {
+  Workspace& w = c->ws;
+  const int n = w.n_rhs;
+  DslashCall d;
+  memset(&d, 0, sizeof(d));
+  d.prec = P64;
+  d.recon = 18;
+  d.cs = &cs;
+  d.n = n;
+  d.shape = kBlasShape;
+  d.ra = red_args(w);
+  // r_e = eta_e - A_ee psi_e + k D_eo psi_o
+  launch_clover64(c, cs, w.r64, w.eta_e, w.x64, 0, 1.0, -1.0, 0, n, s);
+  d.out = w.r64; d.in = w.x64o; d.x = w.r64; d.p_out = 0; d.xpay = 1; d.a = kappa;
+  launch_dslash(c, d, s);
+  // r_o = eta_o - A_oo psi_o + k D_oe psi_e
+  launch_clover64(c, cs, w.t64o, w.eta_o, w.x64o, 1, 1.0, -1.0, 0, n, s);
+  d.out = w.t64o; d.in = w.x64; d.x = w.t64o; d.p_out = 1;
+  launch_dslash(c, d, s);
+  RedArgs ra = red_args(w);
+  launch_norm2(c, w.r64, P64, n, w.scal, ra, s);
+  launch_norm2(c, w.t64o, P64, n, w.scal + n, ra, s);
+}
+
+sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, double* sol, int n, double tol,
+                     const sq_solve_params* prm_in, sq_solve_stats* stats) {
+  auto t0 = std::chrono::steady_clock::now();
+  sq_solve_params prm;
+  if (prm_in) prm = *prm_in;
+  else sq_default_params(&prm);
+  if (!c) return SQ_ERR_ARG;
+  if (!src || !sol || n <= 0) return set_error(c, SQ_ERR_ARG, "sq_solve: null buffer or n_rhs <= 0");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(c, SQ_ERR_ARG, "sq_solve: tol must be > 0");
+  if (!std::isfinite(kappa) || !std::isfinite(csw)) return set_error(c, SQ_ERR_ARG, "sq_solve: non-finite kappa/c_sw");
+  if (prm.inner_prec < P64 || prm.inner_prec > P16) return set_error(c, SQ_ERR_ARG, "sq_solve: bad inner_prec");
+  if (prm.io != SQ_HOST && prm.io != SQ_DEVICE) return set_error(c, SQ_ERR_ARG, "sq_solve: bad io");
+  if (prm.max_iter <= 0) return set_error(c, SQ_ERR_ARG, "sq_solve: max_iter must be > 0");
+  if (prm.chunk <= 0) prm.chunk = 16;
+  if (!c->have_gauge) return set_error(c, SQ_ERR_STATE, "sq_solve: no gauge field loaded");
+  const int inner = prm.inner_prec;
+  CloverSet* cs = nullptr;
+  sq_status st = find_clover(c, kappa, csw, &cs);
+  if (st != SQ_OK) return st;
+  st = alloc_ws(c, n, inner);
+  if (st != SQ_OK) return st;
+  Workspace& w = c->ws;
+  cudaStream_t s = c->stream;
+  const size_t lex_doubles = (size_t)n * c->V * 24;
+  // sources to the device, finiteness
+  const double* dsrc = src;
+  if (prm.io == SQ_HOST) {
+    cudaMemcpyAsync(w.lex, src, lex_doubles * sizeof(double), cudaMemcpyHostToDevice, s);
+    dsrc = w.lex;
+  }
+  int bad = 0;
+  st = check_finite(c, dsrc, lex_doubles, &bad);
+  if (st != SQ_OK) return st;
+  if (bad) return set_error(c, SQ_ERR_NONFINITE, "sq_solve: NaN or Inf in the sources");
+  launch_pack(c, w.eta_e, dsrc, 0, P64, n, s);
+  launch_pack(c, w.eta_o, dsrc, 1, P64, n, s);
+  // initial guess (even sites) or zero
+  if (prm.use_x0) {
+    const double* dx0 = sol;
+    if (prm.io == SQ_HOST) {
+      cudaMemcpyAsync(w.lex, sol, lex_doubles * sizeof(double), cudaMemcpyHostToDevice, s);
+      dx0 = w.lex;
+    }
+    bad = 0;
+    st = check_finite(c, dx0, lex_doubles, &bad);
+    if (st != SQ_OK) return st;
+    if (bad) return set_error(c, SQ_ERR_NONFINITE, "sq_solve: NaN or Inf in the initial guess");
+    launch_pack(c, w.x64, dx0, 0, P64, n, s);
+  } else {
+    cudaMemsetAsync(w.x64.data, 0, field_bytes(c->Vh, P64, n), s);
+  }
+  cudaMemsetAsync(w.xs.data, 0, field_bytes(c->Vh, px_of(inner), n), s);
+  // ||eta||^2
+  RedArgs ra = red_args(w);
+  launch_norm2(c, w.eta_e, P64, n, w.scal, ra, s);
+  launch_norm2(c, w.eta_o, P64, n, w.scal + n, ra, s);
+  std::vector<double> eta2(2 * n);
+  cudaMemcpyAsync(eta2.data(), w.scal, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, s);
+  // bhat = A_ee^{-1} (eta_e + k D_eo A_oo^{-1} eta_o)
+  Field none = make_field(nullptr, c->Vh, P64, n);
+  launch_clover64(c, *cs, w.t64o, none, w.eta_o, 1, 0.0, 1.0, 1, n, s);
+  DslashCall d;
+  memset(&d, 0, sizeof(d));
+  d.prec = P64;
+  d.recon = 18;
+  d.cs = cs;
+  d.n = n;
+  d.shape = kBlasShape;
+  d.ra = ra;
+  d.out = w.r64; d.in = w.t64o; d.x = w.eta_e; d.p_out = 0; d.xpay = 1; d.a = kappa;
+  launch_dslash(c, d, s);
+  launch_clover64(c, *cs, w.b64, none, w.r64, 0, 0.0, 1.0, 1, n, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_check(c, e, "sq_solve setup");
+  std::vector<double> target2(n), enorm2(n);
+  for (int k = 0; k < n; k++) {
+    enorm2[k] = eta2[k] + eta2[n + k];
+    double t = tol * std::sqrt(enorm2[k]) / cs->a_bound;
+    target2[k] = t * t;
+  }
+  // dslash launch shape
+  Shape sh;
+  if (prm.sites_per_block > 0 && prm.rhs_per_block > 0) {
+    sh.sx = prm.sites_per_block;
+    sh.ry = prm.rhs_per_block;
+    if (sh.sx % 32 || sh.sx * sh.ry > 256) return set_error(c, SQ_ERR_ARG, "sq_solve: bad CTA shape");
+  } else {
+    DslashCall tcall;
+    memset(&tcall, 0, sizeof(tcall));
+    tcall.prec = inner;
+    tcall.recon = inner == P64 ? 18 : (inner == P16 ? 12 : c->recon);
+    tcall.cs = cs;
+    tcall.clover = 1;
+    tcall.out = w.to;
+    tcall.in = w.p;
+    tcall.p_out = 1;
+    tcall.n = n;
+    cudaMemsetAsync(w.p.data, 0, field_bytes(c->Vh, inner, n), s);
+    sh = tune_dslash(c, tcall, s);
+  }
+  IterFn iter;
+  UpdFn upd;
+  fns_for(inner, &iter, &upd);
+  int* h_active = nullptr;
+  cudaMallocHost((void**)&h_active, sizeof(int));
+  const double delta = inner == P64 ? 0.0 : prm.delta;
+  double* d_t2 = w.scal;  // scratch for the targets
+  sq_status result = SQ_OK;
+  for (int attempt = 0; attempt < 4; attempt++) {
+    cudaMemcpyAsync(d_t2, target2.data(), n * sizeof(double), cudaMemcpyHostToDevice, s);
+    k_init<<<(n + 127) / 128, 128, 0, s>>>(w.st, w.ctl, w.update_list, d_t2, delta * delta, prm.max_iter,
+                                          prm.outer == SQ_OUTER_DEFECT ? 1 : 0, n);
+    upd(c, *cs, kappa, s);
+    // graph of `chunk` iterations (captured once per workspace / shape / kappa)
+    const int key[8] = {n, inner, sh.sx, sh.ry, prm.chunk, (int)(cs - c->clover.data()),
+                        (int)(kappa * 1e9), c->recon};
+    bool use_graph = prm.use_graph != 0;
+    if (use_graph && (!w.graph || memcmp(key, w.graph_key, sizeof(key)) != 0)) {
+      if (w.graph) {
+        cudaGraphExecDestroy(w.graph);
+        w.graph = nullptr;
+      }
+      cudaGraph_t g;
+      e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        for (int i = 0; i < prm.chunk; i++) iter(c, *cs, kappa, sh, s);
+        e = cudaStreamEndCapture(s, &g);
+      }
+      if (e == cudaSuccess) {
+        e = cudaGraphInstantiate(&w.graph, g, 0);
+        cudaGraphDestroy(g);
+      }
+      if (e != cudaSuccess) {
+        cudaFreeHost(h_active);
+        return cuda_check(c, e, "graph capture of the inner loop");
+      }
+      memcpy(w.graph_key, key, sizeof(key));
+    }
+    long long launched = 0;
+    const long long cap = (long long)prm.max_iter + 4LL * prm.chunk;
+    for (;;) {
+      if (use_graph) {
+        e = cudaGraphLaunch(w.graph, s);
+      } else {
+        for (int i = 0; i < prm.chunk; i++) iter(c, *cs, kappa, sh, s);
+        e = cudaGetLastError();
+      }
+      if (e != cudaSuccess) break;
+      launched += prm.chunk;
+      cudaMemcpyAsync(h_active, &w.ctl->n_active, sizeof(int), cudaMemcpyDeviceToHost, s);
+      e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) break;
+      if (prm.verbose) fprintf(stderr, "libstochq: %lld iterations, %d sources active\n", launched, *h_active);
+      if (*h_active == 0 || launched > cap) break;
+    }
+    if (e != cudaSuccess) {
+      cudaFreeHost(h_active);
+      return cuda_check(c, e, "inner loop");
+    }
+    // psi_o = A_oo^{-1} (eta_o + k D_oe psi_e), then the full FP64 residual
+    d.out = w.t64o; d.in = w.x64; d.x = w.eta_o; d.p_out = 1; d.xpay = 1; d.a = kappa; d.fin = FIN_NONE;
+    d.list = nullptr;
+    d.count = nullptr;
+    launch_dslash(c, d, s);
+    launch_clover64(c, *cs, w.x64o, none, w.t64o, 1, 0.0, 1.0, 1, n, s);
+    launch_full_residual(c, *cs, kappa, s);
+    std::vector<double> res2(2 * n);
+    cudaMemcpyAsync(res2.data(), w.scal, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    std::vector<RhsState> hs(n);
+    cudaMemcpyAsync(hs.data(), w.st, n * sizeof(RhsState), cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      cudaFreeHost(h_active);
+      return cuda_check(c, e, "final residual");
+    }
+    bool retry = false;
+    result = SQ_OK;
+    for (int k = 0; k < n; k++) {
+      double rr = enorm2[k] > 0 ? std::sqrt((res2[k] + res2[n + k]) / enorm2[k]) : 0.0;
+      int status = hs[k].status;
+      if (status == SQ_OK && !(rr <= tol)) {
+        if (attempt < 3) {
+          retry = true;
+          target2[k] *= 1.0 / 16.0;
+        } else {
+          status = SQ_ERR_NOCONV;
+        }
+      }
+      if (stats) {
+        sq_solve_stats& o = stats[k];
+        if (attempt == 0) memset(&o, 0, sizeof(o));
+        o.status = status;
+        o.iterations += hs[k].iter;
+        o.updates += hs[k].updates;
+        o.restarts += hs[k].restarts;
+        o.true_residual = rr;
+      }
+      if (status != SQ_OK && result == SQ_OK) result = (sq_status)status;
+    }
+    if (!retry) break;
+    if (prm.verbose) fprintf(stderr, "libstochq: tightening the Schur target\n");
+    // continue from the current x (even sites already in x64)
+  }
+  cudaFreeHost(h_active);
+  // solutions out
+  double* dsol = prm.io == SQ_HOST ? w.lex : sol;
+  launch_unpack(c, dsol, w.x64, 0, P64, n, s);
+  launch_unpack(c, dsol, w.x64o, 1, P64, n, s);
+  if (prm.io == SQ_HOST)
+    cudaMemcpyAsync(sol, w.lex, lex_doubles * sizeof(double), cudaMemcpyDeviceToHost, s);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_check(c, e, "solution copy");
+  double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats)
+    for (int k = 0; k < n; k++) stats[k].seconds = secs;
+  if (result != SQ_OK) set_error(c, result, "sq_solve: some sources did not converge (see stats)");
+  return result;
+}
+
+}  // namespace sq

@@ -1,0 +1,299 @@
+"""Python binding of libstochq (include/stochq.h): the same entry points,
+argument marshalling only. Every step of the computation runs in the CUDA
+library; there is no Python or CPU fallback. If ``libstochq.so`` has not
+been built, importing this module raises.
+
+Host arrays are numpy ``complex128`` in the library's lexicographic layout:
+links ``(T, Z, Y, X, 4, 3, 3)``, spinors ``(n, T, Z, Y, X, 4, 3)``. Device
+buffers are torch CUDA tensors (any dtype; only ``data_ptr()`` is used) or
+raw integer device addresses.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "libstochq.so")
+
+SQ_F64, SQ_F32, SQ_F16 = 0, 1, 2
+SQ_HOST, SQ_DEVICE = 0, 1
+SQ_DS_CLOVER_INV, SQ_DS_XPAY, SQ_DS_SYNC = 1, 2, 4
+SQ_OUTER_RELIABLE, SQ_OUTER_DEFECT = 0, 1
+
+STATUS = {
+    0: "SQ_OK", 1: "SQ_ERR_ARG", 2: "SQ_ERR_CUDA", 3: "SQ_ERR_OOM",
+    4: "SQ_ERR_NONFINITE", 5: "SQ_ERR_CLOVER", 6: "SQ_ERR_NOCONV",
+    7: "SQ_ERR_BREAKDOWN", 8: "SQ_ERR_TIMEOUT", 9: "SQ_ERR_STATE",
+}
+globals().update({v: k for k, v in STATUS.items()})
+
+
+class sq_solve_params(C.Structure):
+    _fields_ = [
+        ("inner_prec", C.c_int), ("outer", C.c_int), ("delta", C.c_double),
+        ("max_iter", C.c_int), ("recon", C.c_int), ("sites_per_block", C.c_int),
+        ("rhs_per_block", C.c_int), ("chunk", C.c_int), ("use_graph", C.c_int),
+        ("io", C.c_int), ("use_x0", C.c_int), ("verbose", C.c_int),
+    ]
+
+
+class sq_solve_stats(C.Structure):
+    _fields_ = [
+        ("status", C.c_int), ("iterations", C.c_int), ("updates", C.c_int),
+        ("restarts", C.c_int), ("true_residual", C.c_double), ("seconds", C.c_double),
+    ]
+
+
+class sq_problem(C.Structure):
+    _fields_ = [
+        ("ctx", C.c_void_p), ("kappa", C.c_double), ("c_sw", C.c_double),
+        ("sources", C.c_void_p), ("solutions", C.c_void_p), ("n_rhs", C.c_int),
+        ("tol", C.c_double),
+    ]
+
+
+class StochqError(RuntimeError):
+    def __init__(self, status, message, stats=None):
+        self.status = status
+        self.stats = stats
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+
+
+if not os.path.exists(LIBPATH):
+    raise ImportError(
+        f"{LIBPATH} is missing: build it with `python -m paper_1405_4524_gb300.build` "
+        "(the CUDA library is required; there is no CPU fallback)")
+
+_lib = C.CDLL(LIBPATH)
+_vp, _i, _d = C.c_void_p, C.c_int, C.c_double
+
+_SIG = {
+    "sq_default_params": (None, [C.POINTER(sq_solve_params)]),
+    "sq_create": (_i, [C.POINTER(_vp), C.POINTER(_i), _i, _vp]),
+    "sq_destroy": (_i, [_vp]),
+    "sq_load_gauge": (_i, [_vp, _vp, _i, _i]),
+    "sq_build_clover": (_i, [_vp, _d, _d]),
+    "sq_field_bytes": (_i, [_vp, _i, _i, C.POINTER(C.c_size_t)]),
+    "sq_pack_spinor": (_i, [_vp, _vp, _vp, _i, _i, _i, _i]),
+    "sq_unpack_spinor": (_i, [_vp, _vp, _vp, _i, _i, _i, _i]),
+    "sq_dslash_eo": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _d]),
+    "sq_apply_M": (_i, [_vp, _vp, _vp, _i, _d, _d, _i]),
+    "sq_solve": (_i, [_vp, _d, _d, _vp, _vp, _i, _d, C.POINTER(sq_solve_params),
+                      C.POINTER(sq_solve_stats)]),
+    "sq_solve_batch": (_i, [C.POINTER(sq_problem), _i, C.POINTER(sq_solve_params),
+                            C.POINTER(sq_solve_stats)]),
+    "sq_contract_pion": (_i, [_vp, _vp, _i, _vp, _vp, _i]),
+    "sq_status_string": (C.c_char_p, [_i]),
+    "sq_last_error": (C.c_char_p, [_vp]),
+}
+for _name, (_res, _args) in _SIG.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTS = tuple(_SIG)
+
+
+def _ptr(a):
+    """Address of a numpy array, torch tensor or raw integer address."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+def _where(a):
+    if isinstance(a, np.ndarray):
+        return SQ_HOST
+    if hasattr(a, "is_cuda"):
+        return SQ_DEVICE if a.is_cuda else SQ_HOST
+    return SQ_DEVICE
+
+
+def _check(ctx, status, stats=None):
+    if status != 0:
+        msg = sq_last_error(ctx) if ctx else STATUS.get(status, "")
+        raise StochqError(status, msg, stats)
+
+
+def _host_c128(a, name):
+    if a.dtype != np.complex128:
+        raise TypeError(f"{name} must be complex128 (FP64 re, im)")
+    return a
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def sq_status_string(status: int) -> str:
+    return _lib.sq_status_string(int(status)).decode()
+
+
+def sq_last_error(ctx) -> str:
+    return _lib.sq_last_error(ctx).decode()
+
+
+def sq_default_params(**overrides) -> sq_solve_params:
+    p = sq_solve_params()
+    _lib.sq_default_params(C.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def sq_create(dims, t_bc: int = -1, stream=None):
+    """dims = (X, Y, Z, T); stream: torch.cuda.Stream, raw handle or None."""
+    d = (C.c_int * 4)(*[int(x) for x in dims])
+    h = _vp()
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    st = _lib.sq_create(C.byref(h), d, int(t_bc), s)
+    _check(None, st)
+    return h.value
+
+
+def sq_destroy(ctx) -> None:
+    _check(None, _lib.sq_destroy(ctx))
+
+
+def sq_load_gauge(ctx, U, recon: int = 12) -> None:
+    if isinstance(U, np.ndarray):
+        U = np.ascontiguousarray(_host_c128(U, "U"))
+    _check(ctx, _lib.sq_load_gauge(ctx, _ptr(U), int(recon), _where(U)))
+
+
+def sq_build_clover(ctx, kappa: float, c_sw: float) -> None:
+    _check(ctx, _lib.sq_build_clover(ctx, float(kappa), float(c_sw)))
+
+
+def sq_field_bytes(ctx, prec: int, n_rhs: int) -> int:
+    b = C.c_size_t()
+    _check(ctx, _lib.sq_field_bytes(ctx, int(prec), int(n_rhs), C.byref(b)))
+    return b.value
+
+
+def sq_pack_spinor(ctx, eo_out, lex_in, parity: int, prec: int, n_rhs: int) -> None:
+    if isinstance(lex_in, np.ndarray):
+        lex_in = np.ascontiguousarray(_host_c128(lex_in, "lex_in"))
+    _check(ctx, _lib.sq_pack_spinor(ctx, _ptr(eo_out), _ptr(lex_in), int(parity), int(prec),
+                                    int(n_rhs), _where(lex_in)))
+
+
+def sq_unpack_spinor(ctx, lex_out, eo_in, parity: int, prec: int, n_rhs: int) -> None:
+    if isinstance(lex_out, np.ndarray):
+        _host_c128(lex_out, "lex_out")
+        if not lex_out.flags["C_CONTIGUOUS"]:
+            raise ValueError("lex_out must be C-contiguous")
+    _check(ctx, _lib.sq_unpack_spinor(ctx, _ptr(lex_out), _ptr(eo_in), int(parity), int(prec),
+                                      int(n_rhs), _where(lex_out)))
+
+
+def sq_dslash_eo(ctx, out, inp, x, out_parity: int, prec: int, n_rhs: int, flags: int = 0,
+                 a: float = 0.0) -> None:
+    _check(ctx, _lib.sq_dslash_eo(ctx, _ptr(out), _ptr(inp), _ptr(x), int(out_parity), int(prec),
+                                  int(n_rhs), int(flags), float(a)))
+
+
+def sq_apply_M(ctx, out, inp, n_rhs: int, kappa: float, c_sw: float) -> None:
+    if isinstance(inp, np.ndarray):
+        inp = np.ascontiguousarray(_host_c128(inp, "in"))
+    _check(ctx, _lib.sq_apply_M(ctx, _ptr(out), _ptr(inp), int(n_rhs), float(kappa), float(c_sw),
+                                _where(inp)))
+
+
+def sq_solve(ctx, kappa: float, c_sw: float, sources, solutions, n_rhs: int, tol: float,
+             params: sq_solve_params | None = None, raise_on_error: bool = True):
+    """Returns (status, list of per-source stats dicts)."""
+    if params is None:
+        params = sq_default_params()
+    params = sq_solve_params.from_buffer_copy(params)
+    params.io = _where(sources)
+    if isinstance(sources, np.ndarray):
+        _host_c128(sources, "sources")
+        _host_c128(solutions, "solutions")
+    stats = (sq_solve_stats * int(n_rhs))()
+    st = _lib.sq_solve(ctx, float(kappa), float(c_sw), _ptr(sources), _ptr(solutions), int(n_rhs),
+                       float(tol), C.byref(params), stats)
+    out = [dict(status=s.status, iterations=s.iterations, updates=s.updates,
+                restarts=s.restarts, true_residual=s.true_residual, seconds=s.seconds)
+           for s in stats]
+    if raise_on_error:
+        _check(ctx, st, out)
+    return st, out
+
+
+def sq_solve_batch(problems, params: sq_solve_params | None = None, raise_on_error: bool = True):
+    """problems: list of dicts with ctx, kappa, c_sw, sources, solutions, n_rhs, tol."""
+    if params is None:
+        params = sq_default_params()
+    params = sq_solve_params.from_buffer_copy(params)
+    params.io = _where(problems[0]["sources"])
+    arr = (sq_problem * len(problems))()
+    total = 0
+    for i, p in enumerate(problems):
+        arr[i] = sq_problem(p["ctx"], float(p["kappa"]), float(p["c_sw"]), _ptr(p["sources"]),
+                            _ptr(p["solutions"]), int(p["n_rhs"]), float(p["tol"]))
+        total += int(p["n_rhs"])
+    stats = (sq_solve_stats * total)()
+    st = _lib.sq_solve_batch(arr, len(problems), C.byref(params), stats)
+    out = [dict(status=s.status, iterations=s.iterations, updates=s.updates,
+                restarts=s.restarts, true_residual=s.true_residual, seconds=s.seconds)
+           for s in stats]
+    if raise_on_error and st != 0:
+        raise StochqError(st, sq_last_error(problems[0]["ctx"]), out)
+    return st, out
+
+
+def sq_contract_pion(ctx, solutions, n_rhs: int, src_tslice=None) -> np.ndarray:
+    """Returns C as a (n_rhs, T) float64 array."""
+    ts = None
+    if src_tslice is not None:
+        ts = np.ascontiguousarray(np.asarray(src_tslice, dtype=np.int32))
+    # T from the solutions' shape when on the host, else from the context
+    T = int(solutions.shape[1]) if hasattr(solutions, "shape") else None
+    if T is None:
+        raise ValueError("solutions must be an array or tensor with shape (n, T, Z, Y, X, 4, 3)")
+    Cout = np.zeros((int(n_rhs), T), dtype=np.float64)
+    _check(ctx, _lib.sq_contract_pion(ctx, _ptr(solutions), int(n_rhs), _ptr(ts), _ptr(Cout),
+                                      _where(solutions)))
+    return Cout
+
+
+class Lattice:
+    """Owns one context: ``with Lattice(dims) as lat: lat.load(U) ...``."""
+
+    def __init__(self, dims, t_bc: int = -1, stream=None):
+        self.dims = tuple(int(d) for d in dims)
+        self.ctx = sq_create(self.dims, t_bc, stream)
+
+    def close(self):
+        if self.ctx:
+            sq_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
