@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark: noise-source solves per second at a true relative residual of
+1e-10, and the HBM bandwidth of the clover dslash, on one GB300 per rank.
+
+One step = the whole hot path on one batch of synthetic input: gauge-field
+layout conversion (sq_load_gauge), FP64 clover build and inversion
+(sq_build_clover), the batched mixed-precision even-odd BiCGStab solve of
+all sources (sq_solve: FP32 dslash, FP64 reliable updates), and the pion
+contraction (sq_contract_pion). Workload: 16^3 x 32 lattice, antiperiodic
+time, eps = 0.25 SU(3) links, c_sw = 1.0, kappa = 0.120, 16 Z4 sources.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun each rank solves its own sources (weak scaling, replicas:
+the solve has no exchange step); value = all ranks' sources / max time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "clover dslash HBM GB/s; noise-source solves/sec at 1e-10 rel. residual vs FP64"
+WORKLOAD = "16x16x16x32"
+TOL = 1e-10
+UNIT = "sources/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="stochq", choices=["stochq", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--inner", default="f32", choices=["f16", "f32", "f64"])
+    p.add_argument("--delta", type=float, default=0.0, help="<= 0: library default")
+    p.add_argument("--extras", type=int, default=1, help="FP64/FP16 comparison solves")
+    p.add_argument("--e2e", type=int, default=1, help="end-to-end host-buffer measurement")
+    p.add_argument("--cpu", type=int, default=1, help="CPU oracle baseline")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for f in ["sq_dslash.cu", "sq_device.cuh", "sq_solver_dev.cuh"]:
+        h.update(open(os.path.join(ROOT, "paper_1405_4524_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class, workload):
+    """DRAM bytes per launch of the kernel from the committed ncu summary,
+    or None if there is none or the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", f"ncu_{kernel_class}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha") != source_sha():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampler during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = str(index)
+        self.p = None
+        self.path = os.path.join("/tmp", f"sq_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or parts[0] != self.index:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        loaded = [x for x in sm if x > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(workload, seconds_budget=12.0):
+    """The FP64 oracle as it stands, on one source of the same workload: time
+    whole BiCGStab iterations for about `seconds_budget` seconds and scale by
+    the iteration count the oracle needs for 1e-10 (tests/golden)."""
+    import oracle
+    from paper_1405_4524_gb300 import inputs
+
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")))[workload]
+    spec, U, eta = inputs.workload(workload, n_rhs=1)
+    F = oracle.field_strength(U)
+    apply = lambda v: oracle.apply_M(U, F, v, spec["kappa"], spec["csw"], -1.0)
+    t0 = time.perf_counter()
+    apply(eta[0])
+    t_apply = time.perf_counter() - t0
+    # bicgstab(maxiter=m) costs 2m operator applications plus one for the
+    # initial and one for the final residual: m + 1 iteration equivalents
+    m = int(max(1, min(40, seconds_budget / (2.0 * t_apply) - 1)))
+    t0 = time.perf_counter()
+    oracle.bicgstab(apply, eta[0], tol=1e-300, maxiter=m)
+    el = time.perf_counter() - t0
+    per_it = el / (m + 1)
+    it = m
+    value = 1.0 / (per_it * gold["iterations"])
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"1 source of {workload}: {it} oracle BiCGStab iterations ({el:.1f} s, "
+                       f"counted as {it + 1} with the initial and final residual), scaled to the "
+                       f"{gold['iterations']} iterations the oracle needs for 1e-10 "
+                       f"(tests/golden/oracle_iterations.json)")}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    budget = max(2.0, 150.0 / max(1, steps + warm))
+    for _ in range(warm):
+        cpu_baseline(args.workload, seconds_budget=budget / 2)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(steps):
+        last = cpu_baseline(args.workload, seconds_budget=budget)
+        vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    value = statistics.median(vals)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warm, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "n_sources": 1, "tol": TOL,
+                       "solver": "oracle: unpreconditioned FP64 BiCGStab (numpy)"},
+            "cpu_baseline": dict(last, value=value),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import torch
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_1405_4524_gb300 import inputs, stochq as sq
+
+    spec = inputs.WORKLOADS[args.workload]
+    dims, n = spec["dims"], spec["n_rhs"]
+    kappa, csw = spec["kappa"], spec["csw"]
+    U = inputs.make_links(dims, spec["eps"], spec["link_seed"])
+    T = dims[3]
+    ts = [k % T for k in range(n)] if spec["diluted"] else None
+    eta = inputs.make_z4(dims, n, spec["src_seed"] + 100000 * rank, ts)
+    inner = {"f64": sq.SQ_F64, "f32": sq.SQ_F32, "f16": sq.SQ_F16}[args.inner]
+
+    stream = torch.cuda.Stream()
+    ctx = sq.sq_create(dims, -1, stream)
+    U_dev = torch.from_numpy(U).cuda()
+    eta_dev = torch.from_numpy(eta).cuda()
+    sol_dev = torch.zeros_like(eta_dev)
+    pinned = [torch.from_numpy(U).pin_memory(), torch.from_numpy(eta).pin_memory(),
+              torch.zeros(eta.shape, dtype=torch.complex128).pin_memory()]
+    U_pin, eta_pin, sol_pin = (t.numpy() for t in pinned)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    prm = sq.sq_default_params(inner_prec=inner, delta=args.delta, profile=1)
+    prm_e2e = sq.sq_default_params(inner_prec=inner, delta=args.delta)
+
+    last = {}
+
+    def step_device():
+        sq.sq_load_gauge(ctx, U_dev, 12)
+        sq.sq_build_clover(ctx, kappa, csw)
+        _, st = sq.sq_solve(ctx, kappa, csw, eta_dev, sol_dev, n, TOL, prm)
+        last["stats"] = st
+        last["C"] = sq.sq_contract_pion(ctx, sol_dev, n, ts)
+
+    def step_e2e():
+        sq.sq_load_gauge(ctx, U_pin, 12)
+        sq.sq_build_clover(ctx, kappa, csw)
+        _, st = sq.sq_solve(ctx, kappa, csw, eta_pin, sol_pin, n, TOL, prm_e2e)
+        last["stats_e2e"] = st
+        last["C_e2e"] = sq.sq_contract_pion(ctx, sol_pin, n, ts)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(step, k, prof=False):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k)]
+        agg = {}
+        barrier()
+        torch.cuda.synchronize()
+        l0 = sq.sq_kernel_launches(ctx)
+        w0 = time.perf_counter()
+        for i in range(k):
+            with torch.cuda.stream(stream):
+                flush.zero_()  # L2 flush between timed steps (outside the events)
+            ev[i][0].record(stream)
+            torch.cuda.nvtx.range_push("timed_step")
+            step()
+            torch.cuda.nvtx.range_pop()
+            ev[i][1].record(stream)
+            if prof:
+                for row in sq.sq_get_profile(ctx):
+                    a = agg.setdefault(row["name"], {"launches": 0, "ms": 0.0, "bytes": 0.0, "flops": 0.0})
+                    for f in ("launches", "ms", "bytes", "flops"):
+                        a[f] += row[f]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+        barrier()
+        launches = sq.sq_kernel_launches(ctx) - l0
+        ms = sum(a.elapsed_time(b) for a, b in ev) / k
+        if world > 1:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, wall, launches, agg
+
+    for _ in range(max(3, args.warmup)):
+        step_device()
+    clocks = Clocks(local)
+    clocks.start()
+    ms, wall, launches, agg = timed(step_device, args.steps, prof=True)
+    clk = clocks.stop()
+    stats = last["stats"]
+    assert all(s["status"] == 0 and s["true_residual"] <= TOL for s in stats), stats
+    value = n * world / (ms / 1000.0)
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = None
+    if args.e2e:
+        for _ in range(2):
+            step_e2e()
+        ms_e2e, _, _, _ = timed(step_e2e, max(2, args.steps // 2))
+        assert all(s["status"] == 0 and s["true_residual"] <= TOL for s in last["stats_e2e"])
+        h2d = U.nbytes + eta.nbytes + eta.nbytes  # links, sources, solutions re-read by the contraction
+        d2h = eta.nbytes + n * T * 8  # solutions, correlator
+        e2e = {"value": round(n * world / (ms_e2e / 1000.0), 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms_e2e, 3)}
+
+    # dominant kernel: the dslash class with the largest device time
+    dsl = {k: v for k, v in agg.items() if k.startswith("dslash")}
+    top = max(dsl, key=lambda k: dsl[k]["ms"])
+    d = dsl[top]
+    hbm, how = peaks()
+    achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
+    traffic = ncu_traffic(f"{top}_{args.inner}", args.workload)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": traffic,
+                "kernel": f"{top} ({args.inner}, recon-12, {n} sources per launch)",
+                "bytes_per_launch": d["bytes"] / max(1, d["launches"]),
+                "us_per_launch": 1000.0 * d["ms"] / max(1, d["launches"]),
+                "peak_kind": f"{how} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
+    tot_ms = sum(v["ms"] for v in agg.values())
+    breakdown = {k: {"share": round(v["ms"] / tot_ms, 4),
+                     "GB/s": round(v["bytes"] / max(v["ms"], 1e-9) / 1e6, 1),
+                     "us_per_launch": round(1000.0 * v["ms"] / max(1, v["launches"]), 2)}
+                 for k, v in agg.items()}
+
+    extras = {}
+    if args.extras and rank == 0:
+        # the plain FP64 even-odd GPU solver and the FP16-inner solver on the same workload
+        for name, p in [("fp64_solver", sq.sq_default_params(inner_prec=sq.SQ_F64)),
+                        ("fp16_inner_solver", sq.sq_default_params(inner_prec=sq.SQ_F16, delta=args.delta))]:
+            sol2 = torch.zeros_like(eta_dev)
+            try:
+                sq.sq_solve(ctx, kappa, csw, eta_dev, sol2, n, TOL, p)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, st2 = sq.sq_solve(ctx, kappa, csw, eta_dev, sol2, n, TOL, p)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                extras[name] = {"sources_per_s": round(n / dt, 2),
+                                "iterations": int(np.mean([s["iterations"] for s in st2])),
+                                "fp64_updates": int(np.mean([s["updates"] for s in st2])),
+                                "max_true_residual": max(s["true_residual"] for s in st2)}
+            except sq.StochqError as e:
+                extras[name] = {"error": str(e)}
+            del sol2
+        if "sources_per_s" in extras["fp64_solver"]:
+            extras["speedup_vs_fp64_solver"] = round(value / world / extras["fp64_solver"]["sources_per_s"], 2)
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "f16": "f16", "f64": "f64"}[args.inner], "data": "synthetic",
+        "config": {"workload": args.workload, "lattice": "x".join(map(str, dims)), "t_bc": "antiperiodic",
+                   "kappa": kappa, "c_sw": csw, "link_eps": spec["eps"], "sources_per_gpu": n,
+                   "noise": "Z4" + (" time-diluted" if spec["diluted"] else ""), "tol": TOL,
+                   "solver": f"even-odd BiCGStab, {args.inner} inner, FP64 reliable updates (delta={args.delta or 'auto'})",
+                   "step": "load_gauge + build_clover + solve + contract_pion",
+                   "l2": "256 MB flush between timed steps; working set > L2",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": e2e,
+        "roofline": roofline,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "iterations": int(np.mean([s["iterations"] for s in stats])),
+        "fp64_updates": int(np.mean([s["updates"] for s in stats])),
+        "max_true_residual": max(s["true_residual"] for s in stats),
+        "kernel_breakdown": breakdown,
+        "extras": extras,
+    }
+    if rank == 0 and world == 1 and args.cpu:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    sq.sq_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -97,7 +97,9 @@ typedef struct sq_solve_params {
                           SQ_OUTER_DEFECT (restart at every FP64 update)    */
   double delta;        /* FP64 update when ||r|| < delta * max||r|| since the
                           last update (reliable) or < delta * ||r_start||
-                          (defect correction); ignored for SQ_F64          */
+                          (defect correction); <= 0 picks the default for
+                          the inner precision (FP32 1e-4, FP16 3e-3);
+                          ignored for SQ_F64                               */
   int max_iter;        /* inner iterations per source (default 20000)      */
   int recon;           /* low-precision links: 12 or 18 (FP16 always 12)   */
   int sites_per_block; /* dslash CTA shape; 0 = autotune                   */
@@ -108,6 +110,9 @@ typedef struct sq_solve_params {
                           solutions                                        */
   int use_x0;          /* 1: solutions hold an initial guess on entry      */
   int verbose;         /* 1: progress lines on stderr                      */
+  int profile;         /* 1: time every kernel of the inner loop with CUDA
+                          events on the context's stream (event nodes in
+                          the captured graph); read with sq_get_profile    */
 } sq_solve_params;
 
 typedef struct sq_solve_stats {
@@ -120,7 +125,7 @@ typedef struct sq_solve_stats {
   double seconds;        /* wall time of the whole sq_solve call          */
 } sq_solve_stats;
 
-/* Fill *p with the defaults (FP32 inner, reliable updates, delta 0.1). */
+/* Fill *p with the defaults (FP32 inner, reliable updates, automatic delta). */
 void sq_default_params(sq_solve_params *p);
 
 /* Create a context for one lattice. dims = {X,Y,Z,T}, all even, >= 2.
@@ -232,6 +237,29 @@ sq_status sq_solve_batch(const sq_problem *probs, int n_probs,
  * volume factor. Errors: SQ_ERR_ARG. */
 sq_status sq_contract_pion(sq_ctx *ctx, const double *solutions, int n_rhs,
                            const int *src_tslice, double *C, int where);
+
+/* Per kernel class of the solver's inner loop (profiling). */
+typedef struct sq_kernel_stat {
+  char name[48];       /* kernel class, e.g. "dslash_clover"              */
+  long long launches;  /* launches timed                                  */
+  double ms;           /* summed device time between the class's events   */
+  double bytes;        /* summed algorithmic bytes: each datum of a launch
+                          counted once (links and clover blocks once per
+                          launch, spinors once per active source)         */
+  double flops;        /* summed algorithmic flops (1320 per site and
+                          source for the hopping term, 504 for a clover
+                          block pair, BLAS-1 by its arithmetic)           */
+} sq_kernel_stat;
+
+/* Totals of the last sq_solve that ran with params->profile = 1, one entry
+ * per kernel class (13). out may be NULL to query *n only; otherwise up to
+ * max entries are written. Errors: SQ_ERR_ARG, SQ_ERR_STATE (no profiled
+ * solve yet). */
+sq_status sq_get_profile(const sq_ctx *ctx, sq_kernel_stat *out, int max, int *n);
+
+/* Number of kernels this context has launched so far (kernel nodes of
+ * replayed CUDA graphs included). */
+sq_status sq_kernel_launches(const sq_ctx *ctx, long long *n);
 
 const char *sq_status_string(sq_status s);
 const char *sq_last_error(const sq_ctx *ctx);

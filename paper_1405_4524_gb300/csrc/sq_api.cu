@@ -85,27 +85,36 @@ static void free_clover(CloverSet& cs) {
 }
 
 // Cached clover term for (kappa, c_sw); builds it if needed (LRU of 8).
+// Buffers are reused in place (stable device addresses for captured graphs).
 sq_status find_clover(sq_ctx* c, double kappa, double csw, CloverSet** out) {
   for (auto& cs : c->clover)
-    if (cs.A64 && cs.kappa == kappa && cs.csw == csw) {
+    if (cs.valid && cs.kappa == kappa && cs.csw == csw) {
       cs.tick = ++c->tick;
       *out = &cs;
       return SQ_OK;
     }
   if (!c->have_gauge) return set_error(c, SQ_ERR_STATE, "clover: no gauge field loaded");
-  if (c->clover.size() < 8) c->clover.resize(c->clover.size() + 1);
-  size_t victim = 0;
-  for (size_t i = 0; i < c->clover.size(); i++) {
-    if (!c->clover[i].A64) { victim = i; break; }
-    if (c->clover[i].tick < c->clover[victim].tick) victim = i;
+  int slot = -1;
+  for (size_t i = 0; i < c->clover.size(); i++)
+    if (!c->clover[i].valid) { slot = (int)i; break; }
+  if (slot < 0 && c->clover.size() < 8) {
+    c->clover.reserve(8);
+    c->clover.resize(c->clover.size() + 1);
+    slot = (int)c->clover.size() - 1;
   }
-  CloverSet& cs = c->clover[victim];
-  free_clover(cs);
+  if (slot < 0) {
+    slot = 0;
+    for (size_t i = 1; i < c->clover.size(); i++)
+      if (c->clover[i].tick < c->clover[slot].tick) slot = (int)i;
+  }
+  CloverSet& cs = c->clover[slot];
+  cs.valid = 0;
   const size_t Vh = c->Vh;
-  cudaError_t e = cudaMalloc((void**)&cs.A64, 2 * 36 * Vh * sizeof(double2));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&cs.Ainv64, 2 * 36 * Vh * sizeof(double2));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&cs.Ainv32, 2 * 18 * Vh * sizeof(float4));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&cs.Ainv16, 2 * 9 * Vh * sizeof(uint4));
+  cudaError_t e = cudaSuccess;
+  if (!cs.A64) e = cudaMalloc((void**)&cs.A64, 2 * 36 * Vh * sizeof(double2));
+  if (e == cudaSuccess && !cs.Ainv64) e = cudaMalloc((void**)&cs.Ainv64, 2 * 36 * Vh * sizeof(double2));
+  if (e == cudaSuccess && !cs.Ainv32) e = cudaMalloc((void**)&cs.Ainv32, 2 * 18 * Vh * sizeof(float4));
+  if (e == cudaSuccess && !cs.Ainv16) e = cudaMalloc((void**)&cs.Ainv16, 2 * 9 * Vh * sizeof(uint4));
   if (e != cudaSuccess) {
     free_clover(cs);
     return cuda_check(c, e, "clover allocation");
@@ -113,14 +122,10 @@ sq_status find_clover(sq_ctx* c, double kappa, double csw, CloverSet** out) {
   sq_status s = clover_build(c, cs, kappa, csw);
   int bits = 0;
   if (s == SQ_OK) s = read_error_word(c, &bits);
-  if (s == SQ_OK && (bits & ERRBIT_CLOVER)) {
-    free_clover(cs);
+  if (s == SQ_OK && (bits & ERRBIT_CLOVER))
     return set_error(c, SQ_ERR_CLOVER, "clover: a 6x6 block is singular for kappa=%g c_sw=%g", kappa, csw);
-  }
-  if (s != SQ_OK) {
-    free_clover(cs);
-    return s;
-  }
+  if (s != SQ_OK) return s;
+  cs.valid = 1;
   cs.tick = ++c->tick;
   *out = &cs;
   return SQ_OK;
@@ -137,7 +142,7 @@ void sq_default_params(sq_solve_params* p) {
   memset(p, 0, sizeof(*p));
   p->inner_prec = SQ_F32;
   p->outer = SQ_OUTER_RELIABLE;
-  p->delta = 0.1;
+  p->delta = 0.0;  // automatic per inner precision
   p->max_iter = 20000;
   p->recon = 12;
   p->chunk = 16;
@@ -199,8 +204,7 @@ sq_status sq_create(sq_ctx** out, const int dims[4], int t_bc, void* cuda_stream
 sq_status sq_destroy(sq_ctx* c) {
   if (!c) return SQ_OK;
   cudaStreamSynchronize(c->stream);
-  if (c->ws.graph) cudaGraphExecDestroy(c->ws.graph);
-  if (c->ws.base) cudaFree(c->ws.base);
+  release_workspace(c);
   for (auto& cs : c->clover) free_clover(cs);
   cudaFree(c->U64);
   cudaFree(c->U32);
@@ -220,21 +224,19 @@ sq_status sq_load_gauge(sq_ctx* c, const double* U, int recon, int where) {
   sq_status s = enter_stream(c);
   if (s != SQ_OK) return s;
   const size_t Vh = c->Vh;
-  for (auto& cs : c->clover) free_clover(cs);
-  c->clover.clear();
-  c->tuned.clear();
-  cudaFree(c->U64);
-  cudaFree(c->U32);
-  cudaFree(c->U16);
-  c->U64 = nullptr;
-  c->U32 = nullptr;
-  c->U16 = nullptr;
+  // keep the device buffers (stable addresses); cached clover terms go stale
+  for (auto& cs : c->clover) cs.valid = 0;
   c->have_gauge = 0;
+  cudaError_t e = cudaSuccess;
+  if (c->U32 && recon != c->recon) {
+    cudaFree(c->U32);
+    c->U32 = nullptr;
+  }
   c->recon = recon;
-  cudaError_t e = cudaMalloc((void**)&c->U64, 2 * 4 * 9 * Vh * sizeof(double2));
-  if (e == cudaSuccess)
+  if (!c->U64) e = cudaMalloc((void**)&c->U64, 2 * 4 * 9 * Vh * sizeof(double2));
+  if (e == cudaSuccess && !c->U32)
     e = cudaMalloc(&c->U32, recon == 12 ? 2 * 4 * 3 * Vh * sizeof(float4) : 2 * 4 * 9 * Vh * sizeof(float2));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->U16, 2 * 4 * 3 * Vh * sizeof(uint2));
+  if (e == cudaSuccess && !c->U16) e = cudaMalloc((void**)&c->U16, 2 * 4 * 3 * Vh * sizeof(uint2));
   if (e != cudaSuccess) return cuda_check(c, e, "gauge allocation");
   const size_t nd = (size_t)c->V * 4 * 18;
   const double* dU = U;
@@ -246,6 +248,7 @@ sq_status sq_load_gauge(sq_ctx* c, const double* U, int recon, int where) {
     dU = stage;
   }
   s = gauge_convert(c, dU);
+  c->launches += 1;
   if (stage) cudaFreeAsync(stage, c->stream);
   int bits = 0;
   if (s == SQ_OK) s = read_error_word(c, &bits);
@@ -349,7 +352,7 @@ sq_status sq_dslash_eo(sq_ctx* c, void* out, const void* in, const void* x, int 
   if (prec == SQ_F16 && !c->su3) return set_error(c, SQ_ERR_ARG, "sq_dslash_eo: FP16 links need SU(3) links");
   const CloverSet* cs = nullptr;
   if (flags & SQ_DS_CLOVER_INV) {
-    if (c->cur_clover < 0 || c->cur_clover >= (int)c->clover.size() || !c->clover[c->cur_clover].A64)
+    if (c->cur_clover < 0 || c->cur_clover >= (int)c->clover.size() || !c->clover[c->cur_clover].valid)
       return set_error(c, SQ_ERR_STATE, "sq_dslash_eo: no clover term built");
     cs = &c->clover[c->cur_clover];
   }
@@ -369,9 +372,23 @@ sq_status sq_dslash_eo(sq_ctx* c, void* out, const void* in, const void* x, int 
   d.cs = cs;
   d.n = n;
   d.fin = FIN_NONE;
-  d.shape.sx = 64;
-  d.shape.ry = n >= 4 ? 4 : (n >= 2 ? 2 : 1);
+  {
+    // autotuned shape, tuned once per (precision, recon, n) into scratch
+    // output so that an in-place xpay (x == out) is never applied twice
+    void* scratch = nullptr;
+    long long key = ((long long)d.prec << 56) ^ ((long long)d.recon << 48) ^ ((long long)c->Vh << 12) ^ n;
+    if (c->tuned.find(key) == c->tuned.end()) {
+      cudaError_t e = cudaMallocAsync(&scratch, field_bytes(c->Vh, prec, n), c->stream);
+      if (e != cudaSuccess) return cuda_check(c, e, "sq_dslash_eo tuning buffer");
+      DslashCall t = d;
+      t.out = make_field(scratch, c->Vh, prec, n);
+      tune_dslash(c, t, c->stream);
+      cudaFreeAsync(scratch, c->stream);
+    }
+    d.shape = tune_dslash(c, d, c->stream);
+  }
   launch_dslash(c, d, c->stream);
+  c->launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && (flags & SQ_DS_SYNC)) e = cudaStreamSynchronize(c->stream);
   s = cuda_check(c, e, "sq_dslash_eo");
@@ -471,6 +488,7 @@ sq_status sq_contract_pion(sq_ctx* c, const double* sol, int n, const int* tsl, 
   }
   if (e != cudaSuccess) return cuda_check(c, e, "sq_contract_pion buffers");
   launch_pion(c, dev, n, dt, dC, c->stream);
+  c->launches += 1;
   e = cudaMemcpyAsync(C, dC, (size_t)n * T * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   cudaFreeAsync(dC, c->stream);
   if (dt) cudaFreeAsync(dt, c->stream);
@@ -479,6 +497,34 @@ sq_status sq_contract_pion(sq_ctx* c, const double* sol, int n, const int* tsl, 
   s = cuda_check(c, e, "sq_contract_pion");
   if (s != SQ_OK) return s;
   return leave_stream(c);
+}
+
+sq_status sq_get_profile(const sq_ctx* c, sq_kernel_stat* out, int max, int* n) {
+  static const char* names[KC_N] = {
+      "dslash_clover",         "dslash_clover_xpay_alpha", "blas_s_update",
+      "dslash_clover",         "dslash_clover_xpay_omega", "blas_xr_update_norms",
+      "blas_p_update",         "plan_fp64_updates",        "fp64_update_x",
+      "fp64_dslash_clover",    "fp64_dslash_xpay_norm",    "fp64_update_r",
+      "control"};
+  if (!c || !n || max < 0) return SQ_ERR_ARG;
+  if (!c->prof_valid) return SQ_ERR_STATE;
+  *n = KC_N;
+  if (!out) return SQ_OK;
+  for (int k = 0; k < KC_N && k < max; k++) {
+    memset(&out[k], 0, sizeof(out[k]));
+    snprintf(out[k].name, sizeof(out[k].name), "%s", names[k]);
+    out[k].launches = c->prof[k].launches;
+    out[k].ms = c->prof[k].ms;
+    out[k].bytes = c->prof[k].bytes;
+    out[k].flops = c->prof[k].flops;
+  }
+  return SQ_OK;
+}
+
+sq_status sq_kernel_launches(const sq_ctx* c, long long* n) {
+  if (!c || !n) return SQ_ERR_ARG;
+  *n = c->launches;
+  return SQ_OK;
 }
 
 sq_status sq_solve_batch(const sq_problem* probs, int n_probs, const sq_solve_params* params,

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) k_norm2(int Vh, Field f, int n, RedArgs r
     for (int j = 0; j < 12; j++) t += (double)a[j].re * a[j].re + (double)a[j].im * a[j].im;
     v[0] = t;
   }
-  reduce_finalize<1, FIN_STORE>(ra, v, k);
+  reduce_finalize<1, FIN_STORE>(ra, v, k, (int)gridDim.x, (int)blockIdx.x);
 }
 
 void launch_norm2(const sq_ctx* c, Field f, int prec, int n, double* out, RedArgs ra, cudaStream_t s) {

@@ -29,8 +29,17 @@ struct KArgs {
   const int* list;
   const int* count;
   int n;
+  int nsb, nrb;  // site blocks, source blocks of the flattened grid
+  int order;     // 0: source blocks fastest (a site tile's links are shared
+                 //    through L2 by its source blocks); 1: site blocks fastest
   RedArgs ra;
 };
+
+// Register budget: __launch_bounds__(256, SQ_DSLASH_MINB) caps registers at
+// 65536 / (256 * SQ_DSLASH_MINB) per thread (2: 128, 3: 85, 4: 64).
+#ifndef SQ_DSLASH_MINB
+#define SQ_DSLASH_MINB 2
+#endif
 
 // h = psi_up + SIGN * B_mu psi_dn   (SIGN = -1: forward hop, +1: backward)
 template <int MU, int SIGN, typename R>
@@ -151,15 +160,23 @@ __device__ __forceinline__ void hop_dir(const KArgs& a, int k, int cb, Coord c,
 }
 
 template <int P, int RECON, int CLOV, int XPAY, int FIN>
-__global__ void __launch_bounds__(256) k_dslash(const KArgs a) {
+__global__ void __launch_bounds__(256, SQ_DSLASH_MINB) k_dslash(const KArgs a) {
   typedef typename Real<P>::T R;
   constexpr int NRED = FIN == FIN_ALPHA ? 2 : FIN == FIN_OMEGA ? 3 : 1;
+  int sb, rb;
+  if (a.order == 0) {
+    sb = blockIdx.x / a.nrb;
+    rb = blockIdx.x - sb * a.nrb;
+  } else {
+    rb = blockIdx.x / a.nsb;
+    sb = blockIdx.x - rb * a.nsb;
+  }
   const int cnt = a.list ? *a.count : a.n;
-  const int slot0 = blockIdx.y * blockDim.y;
+  const int slot0 = rb * blockDim.y;
   if (slot0 >= cnt) return;  // whole CTA idle (uniform)
   const int slot = slot0 + threadIdx.y;
   const int k = slot < cnt ? (a.list ? a.list[slot] : slot) : -1;
-  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cb = sb * blockDim.x + threadIdx.x;
   const bool ok = (k >= 0) && (cb < a.g.Vh);
   double red[NRED];
 #pragma unroll
@@ -222,7 +239,7 @@ __global__ void __launch_bounds__(256) k_dslash(const KArgs a) {
       red[0] = tt;
     }
   }
-  if (FIN != FIN_NONE) reduce_finalize<NRED, FIN>(a.ra, red, k);
+  if (FIN != FIN_NONE) reduce_finalize<NRED, FIN>(a.ra, red, k, a.nsb, sb);
 }
 
 // ---------------------------------------------------------------------------
@@ -272,7 +289,10 @@ void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s) {
   }
   a.links = d.prec == P64 ? (const void*)c->U64 : d.prec == P32 ? c->U32 : (const void*)c->U16;
   dim3 block(d.shape.sx, d.shape.ry);
-  dim3 grid((c->Vh + d.shape.sx - 1) / d.shape.sx, (d.n + d.shape.ry - 1) / d.shape.ry);
+  a.nsb = (c->Vh + d.shape.sx - 1) / d.shape.sx;
+  a.nrb = (d.n + d.shape.ry - 1) / d.shape.ry;
+  a.order = d.shape.order;
+  dim3 grid((unsigned)a.nsb * (unsigned)a.nrb);
   bool ok = false;
   if (d.prec == P64) {
     if (d.fin == FIN_TRUE && d.clover && d.xpay) {
@@ -296,8 +316,8 @@ Shape tune_dslash(sq_ctx* c, DslashCall d, cudaStream_t s) {
   long long key = ((long long)d.prec << 56) ^ ((long long)d.recon << 48) ^ ((long long)c->Vh << 12) ^ d.n;
   auto it = c->tuned.find(key);
   if (it != c->tuned.end()) return it->second;
-  static const int cand[][2] = {{32, 1}, {32, 2}, {32, 4}, {32, 8}, {64, 1}, {64, 2},
-                                {64, 4}, {128, 1}, {128, 2}, {256, 1}};
+  static const int cand[][3] = {{32, 1, 0}, {32, 2, 0}, {32, 4, 0}, {32, 8, 0}, {64, 1, 0}, {64, 2, 0},
+                                {64, 4, 0}, {128, 1, 0}, {128, 2, 0}, {256, 1, 0}, {64, 2, 1}, {32, 4, 1}};
   d.fin = FIN_NONE;
   d.list = nullptr;
   d.count = nullptr;
@@ -310,6 +330,7 @@ Shape tune_dslash(sq_ctx* c, DslashCall d, cudaStream_t s) {
     if (cd[1] > 1 && cd[1] > d.n) continue;
     d.shape.sx = cd[0];
     d.shape.ry = cd[1];
+    d.shape.order = cd[2];
     for (int w = 0; w < 2; w++) launch_dslash(c, d, s);
     cudaEventRecord(e0, s);
     for (int r = 0; r < 5; r++) launch_dslash(c, d, s);

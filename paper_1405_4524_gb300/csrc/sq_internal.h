@@ -23,12 +23,14 @@ struct CloverSet {
   float4* Ainv32 = nullptr;   // [2][18][Vh]
   uint4* Ainv16 = nullptr;    // [2][9][Vh]
   double a_bound = 1.0;       // max over sites of a Gershgorin bound on ||A||_2
+  int valid = 0;              // built for the current gauge field
   unsigned long long tick = 0;
 };
 
 // Dslash launch shape: sites per CTA (x) and sources per CTA (y).
 struct Shape {
   int sx = 64, ry = 2;
+  int order = 0;  // 0: source blocks fastest in the flattened grid
 };
 
 struct Workspace {
@@ -53,10 +55,36 @@ struct Workspace {
   int* update_list = nullptr;
   double* scal = nullptr;       // n_rhs * 4 doubles of scratch results
   int nblk_stride = 0;
-  // cached graph of `chunk` iterations
+  // cached graph of `chunk` iterations, keyed by everything baked into it
   cudaGraphExec_t graph = nullptr;
-  int graph_chunk = 0;
-  int graph_key[8] = {0};
+  std::vector<unsigned long long> graph_key;
+  // profiling: one event before each iteration and after each of its kernels
+  std::vector<cudaEvent_t> pev;
+  int* hist = nullptr;  // [2][chunk]: sources active / updated per iteration
+  int hist_chunk = 0;
+};
+
+// Kernel classes of one solver iteration (profiling), in launch order.
+enum KClass {
+  KC_DSLASH_CLOVER = 0,    // tmp_o = A_oo^{-1} D_oe p   (and of s)
+  KC_DSLASH_XPAY_ALPHA,    // v = p - k^2 A_ee^{-1} D_eo tmp_o ; <rhat, v>
+  KC_S_UPDATE,             // s = r - alpha v
+  KC_DSLASH_CLOVER_2,      // second tmp_o (same kernel as class 0)
+  KC_DSLASH_XPAY_OMEGA,    // t = s - k^2 ... ; <t, s>, <t, t>
+  KC_XR_UPDATE,            // x += alpha p + omega s ; r = s - omega t ; norms
+  KC_P_UPDATE,             // p = r + beta (p - omega v)
+  KC_PLAN,                 // FP64 update list (grouped across sources)
+  KC_REL_X,                // FP64 update: x64 += xs ; r64 = b - x64
+  KC_REL_DSLASH1,          // FP64 tmp = A^{-1} D x64
+  KC_REL_DSLASH2,          // FP64 r64 += k^2 A^{-1} D tmp ; ||r64||^2
+  KC_REL_R,                // r = r64 ; <rhat, r>
+  KC_CONTROL,              // active list
+  KC_N
+};
+
+struct KStat {
+  long long launches = 0;
+  double ms = 0, bytes = 0, flops = 0;
 };
 
 }  // namespace sq
@@ -85,6 +113,10 @@ struct sq_ctx {
   sq::Workspace ws;
   std::map<long long, sq::Shape> tuned;
   std::string last_error;
+  long long launches = 0;          // kernels launched (graph nodes included)
+  int prof_valid = 0;
+  int prof_inner = 0;
+  sq::KStat prof[sq::KC_N];        // per-class totals of the last profiled solve
 };
 
 namespace sq {
@@ -137,6 +169,8 @@ Shape tune_dslash(sq_ctx* c, DslashCall d, cudaStream_t s);
 // ---- solver (sq_solver.cu)
 sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, double* sol, int n,
                      double tol, const sq_solve_params* prm, sq_solve_stats* stats);
+
+void release_workspace(sq_ctx* c);
 
 // ---- contraction (sq_contract.cu)
 void launch_pion(const sq_ctx* c, const double* lex, int n, const int* tsl, double* C, cudaStream_t s);

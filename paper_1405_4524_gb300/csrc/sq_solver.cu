@@ -28,7 +28,9 @@
 
 namespace sq {
 
-static const Shape kBlasShape = {128, 2};
+static const Shape kBlasShape = {128, 2, 0};
+// FP64 dslash: ~146 registers per thread; 64-thread CTAs keep 7 per SM resident
+static const Shape k64Shape = {64, 1, 0};
 
 struct VArgs {
   int Vh;
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(256) k_xr_update(const VArgs a) {
     red[1] = dr;
     red[2] = di;
   }
-  reduce_finalize<3, FIN_ITER>(a.ra, red, k);
+  reduce_finalize<3, FIN_ITER>(a.ra, red, k, (int)gridDim.x, (int)blockIdx.x);
 }
 
 // p = r + beta (p - omega v)     f0 = r, f1 = p, f2 = v
@@ -186,12 +188,34 @@ __global__ void __launch_bounds__(256) k_rel_r(const VArgs a) {
     red[0] = dr;
     red[1] = di;
   }
-  reduce_finalize<2, FIN_UPDATE>(a.ra, red, k);
+  reduce_finalize<2, FIN_UPDATE>(a.ra, red, k, (int)gridDim.x, (int)blockIdx.x);
+}
+
+// ||r64||^2 into the sources' true residual (initial update with x = 0,
+// where r64 = bhat exactly and no FP64 operator is needed).  f0 = r64
+__global__ void __launch_bounds__(256) k_true_norm(const VArgs a) {
+  SLOT_PROLOGUE
+  double red[1] = {0.0};
+  if (ok) {
+    cx<double> r[12];
+    SpinorIO<P64>::load(a.f0, k, cb, r);
+    double t = 0;
+#pragma unroll
+    for (int j = 0; j < 12; j++) t += r[j].re * r[j].re + r[j].im * r[j].im;
+    red[0] = t;
+  }
+  reduce_finalize<1, FIN_TRUE>(a.ra, red, k, (int)gridDim.x, (int)blockIdx.x);
 }
 
 // Rebuild the active list (ascending source index) and clear the update list.
-__global__ void k_control(RhsState* st, Control* ctl, int* active_list, int n) {
+// hist (optional) records the list lengths this iteration ran with.
+__global__ void k_control(RhsState* st, Control* ctl, int* active_list, int n, int* hist, int it, int chunk) {
   const int lane = threadIdx.x;
+  if (hist && lane == 0) {
+    hist[it] = ctl->n_active;
+    hist[chunk + it] = ctl->n_update;
+  }
+  __syncwarp();
   int base = 0;
   for (int k0 = 0; k0 < n; k0 += 32) {
     const int k = k0 + lane;
@@ -204,6 +228,42 @@ __global__ void k_control(RhsState* st, Control* ctl, int* active_list, int n) {
     ctl->n_active = base;
     ctl->n_update = 0;
   }
+}
+
+// Plan the FP64 updates of this iteration for all sources at once. A source
+// is updated when it asked for it, or - if any source asked - when its
+// iterated residual is already below sqrt(delta) of its maximum (halfway to
+// its own trigger on a log scale): the updates of sources that converge at
+// similar rates then share FP64 launches instead of each running an almost
+// empty one. The list is in ascending source order (deterministic).
+__global__ void k_plan(RhsState* st, Control* ctl, int* update_list, int n) {
+  const int lane = threadIdx.x;
+  bool any = false;
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int k = k0 + lane;
+    const bool w = k < n && st[k].active && st[k].want_update;
+    any = __any_sync(0xffffffffu, w) || any;
+  }
+  int base = 0;
+  if (any) {
+    for (int k0 = 0; k0 < n; k0 += 32) {
+      const int k = k0 + lane;
+      bool on = false;
+      if (k < n && st[k].active) {
+        RhsState& q = st[k];
+        const double ref = q.defect ? q.rstart2 : q.maxr2;
+        on = q.want_update || q.rnorm2 < sqrt(q.delta2) * ref;
+        if (on) {
+          q.want_update = 1;
+          if (q.defect) q.want_restart = 1;
+        }
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, on);
+      if (on) update_list[base + __popc(m & ((1u << lane) - 1u))] = k;
+      base += __popc(m);
+    }
+  }
+  if (lane == 0) ctl->n_update = base;
 }
 
 // Initial state: every source asks for an FP64 update with restart.
@@ -233,6 +293,7 @@ __global__ void k_init(RhsState* st, Control* ctl, int* update_list, const doubl
   }
 }
 
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -241,9 +302,13 @@ static inline int px_of(int inner) { return inner == P64 ? P64 : P32; }
 static void free_ws(sq_ctx* c) {
   Workspace& w = c->ws;
   if (w.graph) cudaGraphExecDestroy(w.graph);
+  for (auto e : w.pev) cudaEventDestroy(e);
+  if (w.hist) cudaFree(w.hist);
   if (w.base) cudaFree(w.base);
   w = Workspace();
 }
+
+void release_workspace(sq_ctx* c) { free_ws(c); }
 
 static sq_status alloc_ws(sq_ctx* c, int n, int inner) {
   Workspace& w = c->ws;
@@ -319,8 +384,23 @@ static VArgs vargs(const sq_ctx* c, const Workspace& w, bool update_list) {
   return a;
 }
 
+// Event marks between the kernels of one iteration (profiling only). Inside
+// a stream capture the records become event-record graph nodes.
+struct Marks {
+  cudaEvent_t* ev = nullptr;  // KC_N + 1 events for this iteration
+  bool capture = false;
+  int i = 0;
+  void mark(cudaStream_t s) {
+    if (!ev) return;
+    if (capture) cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
+    else cudaEventRecord(ev[i], s);
+    i++;
+  }
+};
+
 template <int P, int PX>
-static void launch_iteration(sq_ctx* c, const CloverSet& cs, double kappa, Shape sh, cudaStream_t s) {
+static void launch_iteration(sq_ctx* c, const CloverSet& cs, double kappa, Shape sh, cudaStream_t s, Marks m,
+                             int it, int chunk) {
   Workspace& w = c->ws;
   const int n = w.n_rhs;
   dim3 bb(kBlasShape.sx, kBlasShape.ry);
@@ -336,47 +416,63 @@ static void launch_iteration(sq_ctx* c, const CloverSet& cs, double kappa, Shape
   d.ra = red_args(w);
   d.shape = sh;
   d.clover = 1;
+  m.mark(s);
   // v = Mhat p ; alpha
   d.out = w.to; d.in = w.p; d.p_out = 1; d.xpay = 0; d.fin = FIN_NONE;
   launch_dslash(c, d, s);
+  m.mark(s);
   d.out = w.v; d.in = w.to; d.x = w.p; d.p_out = 0; d.xpay = 1; d.a = -kappa * kappa;
   d.fin = FIN_ALPHA; d.r1 = w.rh;
   launch_dslash(c, d, s);
+  m.mark(s);
   VArgs a = vargs(c, w, false);
   a.f0 = w.r; a.f1 = w.v; a.f2 = w.s;
   k_s_update<P><<<bg, bb, 0, s>>>(a);
+  m.mark(s);
   // t = Mhat s ; omega
   d.out = w.to; d.in = w.s; d.p_out = 1; d.xpay = 0; d.fin = FIN_NONE;
   launch_dslash(c, d, s);
+  m.mark(s);
   d.out = w.t; d.in = w.to; d.x = w.s; d.p_out = 0; d.xpay = 1; d.fin = FIN_OMEGA;
   launch_dslash(c, d, s);
+  m.mark(s);
   a.f0 = w.xs; a.f1 = w.p; a.f2 = w.s; a.f3 = w.t; a.f4 = w.r; a.f5 = w.rh;
   k_xr_update<P, PX><<<bg, bb, 0, s>>>(a);
+  m.mark(s);
   a.f0 = w.r; a.f1 = w.p; a.f2 = w.v;
   k_p_update<P><<<bg, bb, 0, s>>>(a);
+  m.mark(s);
+  k_plan<<<1, 32, 0, s>>>(w.st, w.ctl, w.update_list, n);
+  m.mark(s);
   // FP64 update for the sources that asked for one
   VArgs u = vargs(c, w, true);
   u.f0 = w.x64; u.f1 = w.xs; u.f2 = w.b64; u.f3 = w.r64;
   k_rel_x<PX><<<bg, bb, 0, s>>>(u);
+  m.mark(s);
   DslashCall d64 = d;
   d64.prec = P64;
   d64.recon = 18;
   d64.list = w.update_list;
   d64.count = &w.ctl->n_update;
-  d64.shape = kBlasShape;
+  d64.shape = k64Shape;
   d64.out = w.t64o; d64.in = w.x64; d64.p_out = 1; d64.xpay = 0; d64.fin = FIN_NONE;
   launch_dslash(c, d64, s);
+  m.mark(s);
   d64.out = w.r64; d64.in = w.t64o; d64.x = w.r64; d64.p_out = 0; d64.xpay = 1; d64.a = kappa * kappa;
   d64.fin = FIN_TRUE;
   launch_dslash(c, d64, s);
+  m.mark(s);
   u.f0 = w.r64; u.f1 = w.r; u.f2 = w.rh; u.f3 = w.p;
   k_rel_r<P><<<bg, bb, 0, s>>>(u);
-  k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n);
+  m.mark(s);
+  k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n, m.ev ? w.hist : nullptr, it, chunk);
+  m.mark(s);
 }
 
-// the FP64 update alone (used once at the start: r = bhat - Mhat x0)
+// the FP64 update alone (used once at the start: r = bhat - Mhat x0; with
+// x0 = 0 the residual is bhat itself and no operator is applied)
 template <int P, int PX>
-static void launch_update(sq_ctx* c, const CloverSet& cs, double kappa, cudaStream_t s) {
+static void launch_update(sq_ctx* c, const CloverSet& cs, double kappa, cudaStream_t s, bool zero_x) {
   Workspace& w = c->ws;
   const int n = w.n_rhs;
   dim3 bb(kBlasShape.sx, kBlasShape.ry);
@@ -384,6 +480,15 @@ static void launch_update(sq_ctx* c, const CloverSet& cs, double kappa, cudaStre
   VArgs u = vargs(c, w, true);
   u.f0 = w.x64; u.f1 = w.xs; u.f2 = w.b64; u.f3 = w.r64;
   k_rel_x<PX><<<bg, bb, 0, s>>>(u);
+  if (zero_x) {
+    u.f0 = w.r64;
+    k_true_norm<<<bg, bb, 0, s>>>(u);
+    u.f0 = w.r64; u.f1 = w.r; u.f2 = w.rh; u.f3 = w.p;
+    k_rel_r<P><<<bg, bb, 0, s>>>(u);
+    k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n, nullptr, 0, 0);
+    c->launches += 4;
+    return;
+  }
   DslashCall d64;
   memset(&d64, 0, sizeof(d64));
   d64.prec = P64;
@@ -394,7 +499,7 @@ static void launch_update(sq_ctx* c, const CloverSet& cs, double kappa, cudaStre
   d64.count = &w.ctl->n_update;
   d64.n = n;
   d64.ra = red_args(w);
-  d64.shape = kBlasShape;
+  d64.shape = k64Shape;
   d64.out = w.t64o; d64.in = w.x64; d64.p_out = 1;
   launch_dslash(c, d64, s);
   d64.out = w.r64; d64.in = w.t64o; d64.x = w.r64; d64.p_out = 0; d64.xpay = 1; d64.a = kappa * kappa;
@@ -402,11 +507,12 @@ static void launch_update(sq_ctx* c, const CloverSet& cs, double kappa, cudaStre
   launch_dslash(c, d64, s);
   u.f0 = w.r64; u.f1 = w.r; u.f2 = w.rh; u.f3 = w.p;
   k_rel_r<P><<<bg, bb, 0, s>>>(u);
-  k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n);
+  k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n, nullptr, 0, 0);
+  c->launches += 6;
 }
 
-typedef void (*IterFn)(sq_ctx*, const CloverSet&, double, Shape, cudaStream_t);
-typedef void (*UpdFn)(sq_ctx*, const CloverSet&, double, cudaStream_t);
+typedef void (*IterFn)(sq_ctx*, const CloverSet&, double, Shape, cudaStream_t, Marks, int, int);
+typedef void (*UpdFn)(sq_ctx*, const CloverSet&, double, cudaStream_t, bool);
 
 static void fns_for(int inner, IterFn* it, UpdFn* up) {
   if (inner == P64) { *it = launch_iteration<P64, P64>; *up = launch_update<P64, P64>; }
@@ -415,6 +521,47 @@ static void fns_for(int inner, IterFn* it, UpdFn* up) {
 }
 
 sq_status find_clover(sq_ctx* c, double kappa, double csw, CloverSet** out);
+
+// Algorithmic bytes and flops of one launch of class `kc` with na active
+// and nu updating sources: every datum counted once, links and clover blocks
+// once per launch (they are shared by the sources of a CTA).
+struct Cost {
+  double bytes, flops;
+};
+static Cost class_cost(int kc, int inner, int recon, double Vh, double na, double nu) {
+  const double S = inner == P64 ? 192 : inner == P32 ? 96 : 52;  // spinor site
+  const double SX = inner == P64 ? 192 : 96;                      // x accumulator
+  const double L = inner == P64 ? 144 : inner == P32 ? (recon == 12 ? 48 : 72) : 24;
+  const double Cl = inner == P64 ? 576 : inner == P32 ? 288 : 144;
+  const double hop = 1320, clv = 504, xpay = 48;  // flops per site and source
+  Cost r = {0, 0};
+  switch (kc) {
+    case KC_DSLASH_CLOVER:
+    case KC_DSLASH_CLOVER_2:
+      if (na > 0) r = {Vh * (8 * L + Cl) + na * Vh * 2 * S, na * Vh * (hop + clv)};
+      break;
+    case KC_DSLASH_XPAY_ALPHA:
+      if (na > 0) r = {Vh * (8 * L + Cl) + na * Vh * 4 * S, na * Vh * (hop + clv + xpay + 48)};
+      break;
+    case KC_DSLASH_XPAY_OMEGA:
+      if (na > 0) r = {Vh * (8 * L + Cl) + na * Vh * 3 * S, na * Vh * (hop + clv + xpay + 96)};
+      break;
+    case KC_S_UPDATE: r = {na * Vh * 3 * S, na * Vh * 48}; break;
+    case KC_XR_UPDATE: r = {na * Vh * (2 * SX + 5 * S), na * Vh * 240}; break;
+    case KC_P_UPDATE: r = {na * Vh * 4 * S, na * Vh * 96}; break;
+    case KC_PLAN: break;
+    case KC_REL_X: r = {nu * Vh * (4 * 192 + 2 * SX), nu * Vh * 48}; break;
+    case KC_REL_DSLASH1:
+      if (nu > 0) r = {Vh * (8 * 144 + 576) + nu * Vh * 2 * 192, nu * Vh * (hop + clv)};
+      break;
+    case KC_REL_DSLASH2:
+      if (nu > 0) r = {Vh * (8 * 144 + 576) + nu * Vh * 3 * 192, nu * Vh * (hop + clv + xpay + 48)};
+      break;
+    case KC_REL_R: r = {nu * Vh * (192 + 2 * S), nu * Vh * 48}; break;
+    default: break;
+  }
+  return r;
+}
 
 // FP64 full-lattice residual norms^2 of (x64 even, x64o odd) -> scal[0..n) even, scal[n..2n) odd
 static void launch_full_residual(sq_ctx* c, const CloverSet& cs, double kappa, cudaStream_t s) {
@@ -439,6 +586,7 @@ static void launch_full_residual(sq_ctx* c, const CloverSet& cs, double kappa, c
   RedArgs ra = red_args(w);
   launch_norm2(c, w.r64, P64, n, w.scal, ra, s);
   launch_norm2(c, w.t64o, P64, n, w.scal + n, ra, s);
+  c->launches += 6;
 }
 
 sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, double* sol, int n, double tol,
@@ -454,7 +602,12 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
   if (prm.inner_prec < P64 || prm.inner_prec > P16) return set_error(c, SQ_ERR_ARG, "sq_solve: bad inner_prec");
   if (prm.io != SQ_HOST && prm.io != SQ_DEVICE) return set_error(c, SQ_ERR_ARG, "sq_solve: bad io");
   if (prm.max_iter <= 0) return set_error(c, SQ_ERR_ARG, "sq_solve: max_iter must be > 0");
+  if (!(prm.delta < 1.0)) return set_error(c, SQ_ERR_ARG, "sq_solve: delta must be < 1");
+  // FP32 keeps ~7 digits of the iterated residual, so one FP64 update per
+  // four decades is safe; FP16 (11-bit mantissa) needs one per 2.5 decades
+  if (!(prm.delta > 0.0)) prm.delta = prm.inner_prec == P16 ? 3e-3 : 1e-4;
   if (prm.chunk <= 0) prm.chunk = 16;
+  if (prm.chunk > 256) return set_error(c, SQ_ERR_ARG, "sq_solve: chunk must be <= 256");
   if (!c->have_gauge) return set_error(c, SQ_ERR_STATE, "sq_solve: no gauge field loaded");
   const int inner = prm.inner_prec;
   CloverSet* cs = nullptr;
@@ -477,6 +630,7 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
   if (bad) return set_error(c, SQ_ERR_NONFINITE, "sq_solve: NaN or Inf in the sources");
   launch_pack(c, w.eta_e, dsrc, 0, P64, n, s);
   launch_pack(c, w.eta_o, dsrc, 1, P64, n, s);
+  c->launches += 3;
   // initial guess (even sites) or zero
   if (prm.use_x0) {
     const double* dx0 = sol;
@@ -489,6 +643,7 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
     if (st != SQ_OK) return st;
     if (bad) return set_error(c, SQ_ERR_NONFINITE, "sq_solve: NaN or Inf in the initial guess");
     launch_pack(c, w.x64, dx0, 0, P64, n, s);
+    c->launches += 2;
   } else {
     cudaMemsetAsync(w.x64.data, 0, field_bytes(c->Vh, P64, n), s);
   }
@@ -513,6 +668,7 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
   d.out = w.r64; d.in = w.t64o; d.x = w.eta_e; d.p_out = 0; d.xpay = 1; d.a = kappa;
   launch_dslash(c, d, s);
   launch_clover64(c, *cs, w.b64, none, w.r64, 0, 0.0, 1.0, 1, n, s);
+  c->launches += 5;
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_check(c, e, "sq_solve setup");
   std::vector<double> target2(n), enorm2(n);
@@ -544,21 +700,55 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
   IterFn iter;
   UpdFn upd;
   fns_for(inner, &iter, &upd);
+  const bool prof = prm.profile != 0;
+  const int chunk = prm.chunk;
+  if (prof) {
+    const size_t need = (size_t)chunk * (KC_N + 1);
+    if (w.pev.size() < need) {
+      for (size_t i = w.pev.size(); i < need; i++) {
+        cudaEvent_t ev;
+        cudaEventCreate(&ev);
+        w.pev.push_back(ev);
+      }
+    }
+    if (w.hist_chunk < chunk) {
+      if (w.hist) cudaFree(w.hist);
+      w.hist = nullptr;
+      e = cudaMalloc((void**)&w.hist, 2 * chunk * sizeof(int));
+      if (e != cudaSuccess) return cuda_check(c, e, "profile buffers");
+      w.hist_chunk = chunk;
+    }
+    for (int k = 0; k < KC_N; k++) c->prof[k] = KStat();
+    c->prof_valid = 0;
+    c->prof_inner = inner;
+  }
   int* h_active = nullptr;
-  cudaMallocHost((void**)&h_active, sizeof(int));
+  cudaMallocHost((void**)&h_active, (1 + 2 * chunk) * sizeof(int));
   const double delta = inner == P64 ? 0.0 : prm.delta;
   double* d_t2 = w.scal;  // scratch for the targets
   sq_status result = SQ_OK;
+  const int recon_in = inner == P64 ? 18 : (inner == P16 ? 12 : c->recon);
   for (int attempt = 0; attempt < 4; attempt++) {
     cudaMemcpyAsync(d_t2, target2.data(), n * sizeof(double), cudaMemcpyHostToDevice, s);
     k_init<<<(n + 127) / 128, 128, 0, s>>>(w.st, w.ctl, w.update_list, d_t2, delta * delta, prm.max_iter,
                                           prm.outer == SQ_OUTER_DEFECT ? 1 : 0, n);
-    upd(c, *cs, kappa, s);
-    // graph of `chunk` iterations (captured once per workspace / shape / kappa)
-    const int key[8] = {n, inner, sh.sx, sh.ry, prm.chunk, (int)(cs - c->clover.data()),
-                        (int)(kappa * 1e9), c->recon};
-    bool use_graph = prm.use_graph != 0;
-    if (use_graph && (!w.graph || memcmp(key, w.graph_key, sizeof(key)) != 0)) {
+    c->launches += 1;
+    // x = 0 only on the first pass without an initial guess
+    upd(c, *cs, kappa, s, attempt == 0 && !prm.use_x0);
+    // graph of `chunk` iterations; the key holds everything baked into it
+    std::vector<unsigned long long> key = {
+        (unsigned long long)n, (unsigned long long)inner, (unsigned long long)sh.sx, (unsigned long long)sh.ry,
+        (unsigned long long)chunk, (unsigned long long)prof, (unsigned long long)c->recon,
+        (unsigned long long)(uintptr_t)w.base, (unsigned long long)(uintptr_t)c->U64,
+        (unsigned long long)(uintptr_t)c->U32, (unsigned long long)(uintptr_t)c->U16,
+        (unsigned long long)(uintptr_t)cs->Ainv64, (unsigned long long)(uintptr_t)cs->Ainv32,
+        (unsigned long long)(uintptr_t)cs->Ainv16, (unsigned long long)(uintptr_t)w.hist,
+        (unsigned long long)(uintptr_t)(w.pev.empty() ? nullptr : w.pev[0])};
+    unsigned long long kb;
+    memcpy(&kb, &kappa, sizeof(kb));
+    key.push_back(kb);
+    const bool use_graph = prm.use_graph != 0;
+    if (use_graph && (!w.graph || key != w.graph_key)) {
       if (w.graph) {
         cudaGraphExecDestroy(w.graph);
         w.graph = nullptr;
@@ -566,7 +756,14 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
       cudaGraph_t g;
       e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        for (int i = 0; i < prm.chunk; i++) iter(c, *cs, kappa, sh, s);
+        for (int i = 0; i < chunk; i++) {
+          Marks m;
+          if (prof) {
+            m.ev = &w.pev[(size_t)i * (KC_N + 1)];
+            m.capture = true;
+          }
+          iter(c, *cs, kappa, sh, s, m, i, chunk);
+        }
         e = cudaStreamEndCapture(s, &g);
       }
       if (e == cudaSuccess) {
@@ -577,24 +774,46 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
         cudaFreeHost(h_active);
         return cuda_check(c, e, "graph capture of the inner loop");
       }
-      memcpy(w.graph_key, key, sizeof(key));
+      w.graph_key = key;
     }
     long long launched = 0;
-    const long long cap = (long long)prm.max_iter + 4LL * prm.chunk;
+    const long long cap = (long long)prm.max_iter + 4LL * chunk;
     for (;;) {
       if (use_graph) {
         e = cudaGraphLaunch(w.graph, s);
       } else {
-        for (int i = 0; i < prm.chunk; i++) iter(c, *cs, kappa, sh, s);
+        for (int i = 0; i < chunk; i++) {
+          Marks m;
+          if (prof) m.ev = &w.pev[(size_t)i * (KC_N + 1)];
+          iter(c, *cs, kappa, sh, s, m, i, chunk);
+        }
         e = cudaGetLastError();
       }
       if (e != cudaSuccess) break;
-      launched += prm.chunk;
+      c->launches += (long long)chunk * KC_N;
+      launched += chunk;
       cudaMemcpyAsync(h_active, &w.ctl->n_active, sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (prof) cudaMemcpyAsync(h_active + 1, w.hist, 2 * chunk * sizeof(int), cudaMemcpyDeviceToHost, s);
       e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) break;
-      if (prm.verbose) fprintf(stderr, "libstochq: %lld iterations, %d sources active\n", launched, *h_active);
-      if (*h_active == 0 || launched > cap) break;
+      if (prof) {
+        for (int i = 0; i < chunk; i++) {
+          const double na = h_active[1 + i], nu = h_active[1 + chunk + i];
+          for (int kc = 0; kc < KC_N; kc++) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, w.pev[(size_t)i * (KC_N + 1) + kc], w.pev[(size_t)i * (KC_N + 1) + kc + 1]);
+            Cost cost = class_cost(kc, inner, recon_in, (double)c->Vh, na, nu);
+            KStat& ks = c->prof[kc];
+            ks.launches += 1;
+            ks.ms += ms;
+            ks.bytes += cost.bytes;
+            ks.flops += cost.flops;
+          }
+        }
+        c->prof_valid = 1;
+      }
+      if (prm.verbose) fprintf(stderr, "libstochq: %lld iterations, %d sources active\n", launched, h_active[0]);
+      if (h_active[0] == 0 || launched > cap) break;
     }
     if (e != cudaSuccess) {
       cudaFreeHost(h_active);
@@ -606,6 +825,7 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
     d.count = nullptr;
     launch_dslash(c, d, s);
     launch_clover64(c, *cs, w.x64o, none, w.t64o, 1, 0.0, 1.0, 1, n, s);
+    c->launches += 2;
     launch_full_residual(c, *cs, kappa, s);
     std::vector<double> res2(2 * n);
     cudaMemcpyAsync(res2.data(), w.scal, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -649,6 +869,7 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
   double* dsol = prm.io == SQ_HOST ? w.lex : sol;
   launch_unpack(c, dsol, w.x64, 0, P64, n, s);
   launch_unpack(c, dsol, w.x64o, 1, P64, n, s);
+  c->launches += 2;
   if (prm.io == SQ_HOST)
     cudaMemcpyAsync(sol, w.lex, lex_doubles * sizeof(double), cudaMemcpyDeviceToHost, s);
   e = cudaStreamSynchronize(s);

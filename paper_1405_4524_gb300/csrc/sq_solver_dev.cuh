@@ -63,11 +63,6 @@ struct RedArgs {
   int nblk_stride;     // blocks per source in `partial`
 };
 
-__device__ __forceinline__ void append_update(const RedArgs& ra, int k) {
-  int slot = atomicAdd(&ra.ctl->n_update, 1);
-  ra.update_list[slot] = k;
-}
-
 template <int FIN>
 __device__ __forceinline__ void finalize(const RedArgs& ra, int k, const double* s) {
   RhsState& q = ra.st[k];
@@ -133,10 +128,8 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int k, const double*
     } else if (r2 < q.delta2 * q.maxr2) {
       upd = true;
     }
-    if (upd) {
-      q.want_update = 1;
-      append_update(ra, k);
-    }
+    // the update list itself is planned for all sources at once (k_plan)
+    if (upd) q.want_update = 1;
   } else if (FIN == FIN_UPDATE) {
     // r was replaced by the FP64 residual; rho = <rhat, r> with the rhat in
     // use (after a restart rhat = r, so rho = ||r||^2 up to rounding)
@@ -169,12 +162,13 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int k, const double*
 
 // Block-level reduction of NRED doubles per source slot (threadIdx.y) over
 // the sites of the block (threadIdx.x; blockDim.x is a multiple of 32), then
-// across blocks through `partial`: the last block of a source (per-source
-// arrival counter) sums the per-block partials in block order and runs the
-// finaliser. The summation order is fixed for a fixed launch shape, so the
-// result is bitwise reproducible. Every thread of the block must call this.
+// across the nblk site blocks of the launch through `partial` (this block is
+// site block bidx): the last block of a source (per-source arrival counter)
+// sums the per-block partials in block order and runs the finaliser. The
+// summation order is fixed for a fixed launch shape, so the result is
+// bitwise reproducible. Every thread of the block must call this.
 template <int NRED, int FIN>
-__device__ __forceinline__ void reduce_finalize(const RedArgs& ra, double v[NRED], int k) {
+__device__ __forceinline__ void reduce_finalize(const RedArgs& ra, double v[NRED], int k, int nblk, int bidx) {
   __shared__ double sm[32][NRED];  // one row per warp
   __shared__ int last[32];         // per slot: this block finishes source k
   const int lane = threadIdx.x & 31;
@@ -197,12 +191,12 @@ __device__ __forceinline__ void reduce_finalize(const RedArgs& ra, double v[NRED
       for (int w = 0; w < nwx; w++)
 #pragma unroll
         for (int i = 0; i < NRED; i++) acc[i] += sm[ty * nwx + w][i];
-      double* dst = ra.partial + ((size_t)k * ra.nblk_stride + blockIdx.x) * NRED;
+      double* dst = ra.partial + ((size_t)k * ra.nblk_stride + bidx) * NRED;
 #pragma unroll
       for (int i = 0; i < NRED; i++) dst[i] = acc[i];
       __threadfence();
       unsigned prev = atomicAdd(ra.counter + k, 1u);
-      is_last = (prev == gridDim.x - 1);
+      is_last = (prev == (unsigned)nblk - 1u);
     }
     last[ty] = is_last;
   }
@@ -213,7 +207,7 @@ __device__ __forceinline__ void reduce_finalize(const RedArgs& ra, double v[NRED
 #pragma unroll
     for (int i = 0; i < NRED; i++) acc[i] = 0.0;
     const double* src = ra.partial + (size_t)k * ra.nblk_stride * NRED;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
 #pragma unroll
       for (int i = 0; i < NRED; i++) acc[i] += __ldcg(src + (size_t)b * NRED + i);
 #pragma unroll

@@ -38,6 +38,7 @@ class sq_solve_params(C.Structure):
         ("max_iter", C.c_int), ("recon", C.c_int), ("sites_per_block", C.c_int),
         ("rhs_per_block", C.c_int), ("chunk", C.c_int), ("use_graph", C.c_int),
         ("io", C.c_int), ("use_x0", C.c_int), ("verbose", C.c_int),
+        ("profile", C.c_int),
     ]
 
 
@@ -45,6 +46,13 @@ class sq_solve_stats(C.Structure):
     _fields_ = [
         ("status", C.c_int), ("iterations", C.c_int), ("updates", C.c_int),
         ("restarts", C.c_int), ("true_residual", C.c_double), ("seconds", C.c_double),
+    ]
+
+
+class sq_kernel_stat(C.Structure):
+    _fields_ = [
+        ("name", C.c_char * 48), ("launches", C.c_longlong), ("ms", C.c_double),
+        ("bytes", C.c_double), ("flops", C.c_double),
     ]
 
 
@@ -87,6 +95,8 @@ _SIG = {
     "sq_solve_batch": (_i, [C.POINTER(sq_problem), _i, C.POINTER(sq_solve_params),
                             C.POINTER(sq_solve_stats)]),
     "sq_contract_pion": (_i, [_vp, _vp, _i, _vp, _vp, _i]),
+    "sq_get_profile": (_i, [_vp, C.POINTER(sq_kernel_stat), _i, C.POINTER(_i)]),
+    "sq_kernel_launches": (_i, [_vp, C.POINTER(C.c_longlong)]),
     "sq_status_string": (C.c_char_p, [_i]),
     "sq_last_error": (C.c_char_p, [_vp]),
 }
@@ -272,6 +282,22 @@ def sq_contract_pion(ctx, solutions, n_rhs: int, src_tslice=None) -> np.ndarray:
     _check(ctx, _lib.sq_contract_pion(ctx, _ptr(solutions), int(n_rhs), _ptr(ts), _ptr(Cout),
                                       _where(solutions)))
     return Cout
+
+
+def sq_get_profile(ctx):
+    """Per kernel class totals of the last profiled solve (list of dicts)."""
+    n = _i()
+    _check(ctx, _lib.sq_get_profile(ctx, None, 0, C.byref(n)))
+    arr = (sq_kernel_stat * n.value)()
+    _check(ctx, _lib.sq_get_profile(ctx, arr, n.value, C.byref(n)))
+    return [dict(name=a.name.decode(), launches=a.launches, ms=a.ms, bytes=a.bytes, flops=a.flops)
+            for a in arr]
+
+
+def sq_kernel_launches(ctx) -> int:
+    n = C.c_longlong()
+    _check(ctx, _lib.sq_kernel_launches(ctx, C.byref(n)))
+    return n.value
 
 
 class Lattice:

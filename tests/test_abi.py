@@ -53,7 +53,7 @@ def test_host_only_calls(lib):
     assert stochq.sq_status_string(0) == "SQ_OK"
     assert "NOCONV" in stochq.sq_status_string(6)
     p = stochq.sq_default_params()
-    assert p.inner_prec == stochq.SQ_F32 and p.max_iter > 0 and 0 < p.delta < 1
+    assert p.inner_prec == stochq.SQ_F32 and p.max_iter > 0 and p.delta == 0.0
     # argument validation happens before any CUDA call
     for dims in [(4, 4, 4, 7), (4, 0, 4, 8), (3, 4, 4, 8)]:
         with pytest.raises(stochq.StochqError) as e:
