@@ -185,6 +185,17 @@ sq_status sq_unpack_spinor(sq_ctx *ctx, double *lex_out, const void *eo_in,
 sq_status sq_dslash_eo(sq_ctx *ctx, void *out, const void *in, const void *x,
                        int out_parity, sq_prec prec, int n_rhs, int flags, double a);
 
+/* Per-source squared L2 norms of a device even-odd field (one parity,
+ * n_rhs sources, precision prec, layout above): out[k] = sum over the
+ * sites and 24 reals of source k of v^2 (FP16: the stored values times
+ * their site norm), accumulated in FP64 by a fixed-order two-level
+ * reduction (per-CTA partials, then the last CTA of each source sums them
+ * in block order), so the result is bitwise reproducible. The reduction
+ * scratch comes from the context stream's allocator. out: n_rhs doubles,
+ * host or device per `where`. Errors: SQ_ERR_ARG, SQ_ERR_OOM. */
+sq_status sq_norm2_eo(sq_ctx *ctx, const void *eo_field, sq_prec prec, int n_rhs, double *out,
+                      int where);
+
 /* Full-lattice FP64 operator: out = M in for n_rhs lexicographic FP64
  * spinors (host or device per `where`), with the clover term for
  * (kappa, c_sw) (built if not cached). Errors: SQ_ERR_ARG, SQ_ERR_STATE,

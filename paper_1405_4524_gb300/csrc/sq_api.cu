@@ -396,6 +396,36 @@ sq_status sq_dslash_eo(sq_ctx* c, void* out, const void* in, const void* x, int 
   return leave_stream(c);
 }
 
+sq_status sq_norm2_eo(sq_ctx* c, const void* field, sq_prec prec, int n, double* out, int where) {
+  if (!c) return SQ_ERR_ARG;
+  if (!field || !out || n <= 0 || prec < SQ_F64 || prec > SQ_F16 || (where != SQ_HOST && where != SQ_DEVICE))
+    return set_error(c, SQ_ERR_ARG, "sq_norm2_eo: bad argument");
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  const int nblk = (c->Vh + 127) / 128;
+  const size_t b_part = (size_t)n * nblk * sizeof(double), b_cnt = (size_t)n * sizeof(unsigned);
+  const size_t b_out = (size_t)n * sizeof(double);
+  char* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&scratch, b_part + b_cnt + b_out + 512, c->stream);
+  if (e != cudaSuccess) return cuda_check(c, e, "sq_norm2_eo scratch");
+  RedArgs ra;
+  memset(&ra, 0, sizeof(ra));
+  ra.partial = (double*)scratch;
+  ra.counter = (unsigned*)(scratch + ((b_part + 255) & ~(size_t)255));
+  double* dout = (double*)(scratch + ((b_part + 255) & ~(size_t)255) + ((b_cnt + 255) & ~(size_t)255));
+  ra.nblk_stride = nblk;
+  cudaMemsetAsync(ra.counter, 0, b_cnt, c->stream);
+  launch_norm2(c, make_field((void*)field, c->Vh, prec, n), prec, n, dout, ra, c->stream);
+  c->launches += 1;
+  e = cudaMemcpyAsync(out, dout, b_out, where == SQ_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                      c->stream);
+  cudaFreeAsync(scratch, c->stream);
+  if (e == cudaSuccess && where == SQ_HOST) e = cudaStreamSynchronize(c->stream);
+  s = cuda_check(c, e, "sq_norm2_eo");
+  if (s != SQ_OK) return s;
+  return leave_stream(c);
+}
+
 sq_status sq_apply_M(sq_ctx* c, double* out, const double* in, int n, double kappa, double csw, int where) {
   if (!c) return SQ_ERR_ARG;
   if (!out || !in || n <= 0 || (where != SQ_HOST && where != SQ_DEVICE) || !std::isfinite(kappa) ||

@@ -89,6 +89,7 @@ _SIG = {
     "sq_pack_spinor": (_i, [_vp, _vp, _vp, _i, _i, _i, _i]),
     "sq_unpack_spinor": (_i, [_vp, _vp, _vp, _i, _i, _i, _i]),
     "sq_dslash_eo": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _d]),
+    "sq_norm2_eo": (_i, [_vp, _vp, _i, _i, _vp, _i]),
     "sq_apply_M": (_i, [_vp, _vp, _vp, _i, _d, _d, _i]),
     "sq_solve": (_i, [_vp, _d, _d, _vp, _vp, _i, _d, C.POINTER(sq_solve_params),
                       C.POINTER(sq_solve_stats)]),
@@ -217,6 +218,14 @@ def sq_dslash_eo(ctx, out, inp, x, out_parity: int, prec: int, n_rhs: int, flags
                  a: float = 0.0) -> None:
     _check(ctx, _lib.sq_dslash_eo(ctx, _ptr(out), _ptr(inp), _ptr(x), int(out_parity), int(prec),
                                   int(n_rhs), int(flags), float(a)))
+
+
+def sq_norm2_eo(ctx, eo_field, prec: int, n_rhs: int, out=None) -> np.ndarray:
+    """Per-source squared norms of a device even-odd field (float64 array)."""
+    if out is None:
+        out = np.zeros(int(n_rhs), dtype=np.float64)
+    _check(ctx, _lib.sq_norm2_eo(ctx, _ptr(eo_field), int(prec), int(n_rhs), _ptr(out), _where(out)))
+    return out
 
 
 def sq_apply_M(ctx, out, inp, n_rhs: int, kappa: float, c_sw: float) -> None:
