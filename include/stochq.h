@@ -196,6 +196,27 @@ sq_status sq_dslash_eo(sq_ctx *ctx, void *out, const void *in, const void *x,
 sq_status sq_norm2_eo(sq_ctx *ctx, const void *eo_field, sq_prec prec, int n_rhs, double *out,
                       int where);
 
+/* Allocation-free variant of sq_norm2_eo (the paper has no counterpart;
+ * this is a service for callers of this library). It gives the same
+ * per-source squared norms (within FP64 rounding: the sum is taken in a
+ * different fixed order) but allocates no device memory at all, for callers
+ * that must not allocate at the point of the call: code that enqueues work
+ * while another thread captures a CUDA graph in global capture mode (an
+ * allocation there invalidates the capture), real-time loops that cannot
+ * afford the device synchronisation cudaMalloc may imply, and frameworks
+ * whose memory pool owns all device memory. The reduction scratch is a
+ * fixed static device array of 259 KiB that every GPU which loads the
+ * library keeps until the process exits; n_rhs is limited to 256 sources
+ * (larger n_rhs: SQ_ERR_ARG). The first call on a device looks up the
+ * array's device address for that device (one-time set-up); make that
+ * first call before any stream capture starts. Every call shares the
+ * array, which keeps the last call's contents: calls that overlap on one
+ * GPU (other streams, other contexts, other threads) race and must be
+ * serialised by the caller. Inputs and outputs as sq_norm2_eo.
+ * Errors: SQ_ERR_ARG, SQ_ERR_CUDA. */
+sq_status sq_norm2_eo_noalloc(sq_ctx *ctx, const void *eo_field, sq_prec prec, int n_rhs,
+                              double *out, int where);
+
 /* Full-lattice FP64 operator: out = M in for n_rhs lexicographic FP64
  * spinors (host or device per `where`), with the clover term for
  * (kappa, c_sw) (built if not cached). Errors: SQ_ERR_ARG, SQ_ERR_STATE,

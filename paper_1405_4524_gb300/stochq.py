@@ -90,6 +90,7 @@ _SIG = {
     "sq_unpack_spinor": (_i, [_vp, _vp, _vp, _i, _i, _i, _i]),
     "sq_dslash_eo": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _d]),
     "sq_norm2_eo": (_i, [_vp, _vp, _i, _i, _vp, _i]),
+    "sq_norm2_eo_noalloc": (_i, [_vp, _vp, _i, _i, _vp, _i]),
     "sq_apply_M": (_i, [_vp, _vp, _vp, _i, _d, _d, _i]),
     "sq_solve": (_i, [_vp, _d, _d, _vp, _vp, _i, _d, C.POINTER(sq_solve_params),
                       C.POINTER(sq_solve_stats)]),
@@ -225,6 +226,16 @@ def sq_norm2_eo(ctx, eo_field, prec: int, n_rhs: int, out=None) -> np.ndarray:
     if out is None:
         out = np.zeros(int(n_rhs), dtype=np.float64)
     _check(ctx, _lib.sq_norm2_eo(ctx, _ptr(eo_field), int(prec), int(n_rhs), _ptr(out), _where(out)))
+    return out
+
+
+def sq_norm2_eo_noalloc(ctx, eo_field, prec: int, n_rhs: int, out=None) -> np.ndarray:
+    """sq_norm2_eo without any device allocation (static scratch, at most
+    256 sources; overlapping calls on one GPU race)."""
+    if out is None:
+        out = np.zeros(int(n_rhs), dtype=np.float64)
+    _check(ctx, _lib.sq_norm2_eo_noalloc(ctx, _ptr(eo_field), int(prec), int(n_rhs), _ptr(out),
+                                         _where(out)))
     return out
 
 
