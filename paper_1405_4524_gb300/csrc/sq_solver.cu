@@ -232,10 +232,11 @@ __global__ void k_control(RhsState* st, Control* ctl, int* active_list, int n, i
 
 // Plan the FP64 updates of this iteration for all sources at once. A source
 // is updated when it asked for it, or - if any source asked - when its
-// iterated residual is already below sqrt(delta) of its maximum (halfway to
-// its own trigger on a log scale): the updates of sources that converge at
+// iterated residual is already within a factor 5 of its own trigger (a
+// couple of iterations away): the updates of sources that converge at
 // similar rates then share FP64 launches instead of each running an almost
-// empty one. The list is in ascending source order (deterministic).
+// empty one, without adding updates. The list is in ascending source order
+// (deterministic).
 __global__ void k_plan(RhsState* st, Control* ctl, int* update_list, int n) {
   const int lane = threadIdx.x;
   bool any = false;
@@ -252,7 +253,7 @@ __global__ void k_plan(RhsState* st, Control* ctl, int* update_list, int n) {
       if (k < n && st[k].active) {
         RhsState& q = st[k];
         const double ref = q.defect ? q.rstart2 : q.maxr2;
-        on = q.want_update || q.rnorm2 < sqrt(q.delta2) * ref;
+        on = q.want_update || q.rnorm2 < 25.0 * q.delta2 * ref || q.rnorm2 < 25.0 * q.target2;
         if (on) {
           q.want_update = 1;
           if (q.defect) q.want_restart = 1;
