@@ -252,11 +252,16 @@ typedef struct sq_problem {
   double tol;
 } sq_problem;
 
-/* Solve several problems (different lattices and/or kappa) in one
- * iteration loop whose kernels each cover every source of every problem;
- * converged sources retire from all launches. All contexts must share the
- * same CUDA device. stats holds sum(n_rhs) entries in problem order.
- * Errors as sq_solve. */
+/* Solve several problems (different lattices and/or kappa; several
+ * problems may share a context) in one iteration loop: every chunk of
+ * iterations of every problem is one branch of a single captured CUDA
+ * graph, so all problems advance concurrently from one graph launch, and
+ * converged sources retire from every kernel of their problem. Each
+ * problem keeps its own workspace (cached in the first problem's context
+ * between calls). All contexts must be on the same CUDA device; params
+ * apply to every problem (params->profile is ignored). stats holds
+ * sum(n_rhs) entries in problem order. Errors as sq_solve (the message is
+ * kept in the first problem's context). */
 sq_status sq_solve_batch(const sq_problem *probs, int n_probs,
                          const sq_solve_params *params, sq_solve_stats *stats);
 

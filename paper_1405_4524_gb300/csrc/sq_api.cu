@@ -1,6 +1,7 @@
 // The extern "C" boundary of libstochq (declared in include/stochq.h):
 // argument validation, context and stream handling, host <-> device
 // staging, and dispatch to the kernels of the other translation units.
+#include <atomic>
 #include <cstdarg>
 #include <cmath>
 #include <cstdio>
@@ -197,6 +198,8 @@ sq_status sq_create(sq_ctx** out, const int dims[4], int t_bc, void* cuda_stream
     return e == cudaErrorMemoryAllocation ? SQ_ERR_OOM : SQ_ERR_CUDA;
   }
   c->user_stream = (cudaStream_t)cuda_stream;
+  static std::atomic<unsigned long long> next_uid{1};
+  c->uid = next_uid++;
   *out = c;
   return SQ_OK;
 }
@@ -560,18 +563,23 @@ sq_status sq_kernel_launches(const sq_ctx* c, long long* n) {
 sq_status sq_solve_batch(const sq_problem* probs, int n_probs, const sq_solve_params* params,
                          sq_solve_stats* stats) {
   if (!probs || n_probs <= 0) return SQ_ERR_ARG;
-  // Problems are solved one after the other until the fused batch path is in.
-  sq_status worst = SQ_OK;
-  size_t off = 0;
+  std::vector<sq_ctx*> ctxs;
   for (int i = 0; i < n_probs; i++) {
-    const sq_problem& p = probs[i];
-    if (!p.ctx) return SQ_ERR_ARG;
-    sq_status s = sq_solve(p.ctx, p.kappa, p.c_sw, p.sources, p.solutions, p.n_rhs, p.tol, params,
-                           stats ? stats + off : nullptr);
-    off += p.n_rhs > 0 ? p.n_rhs : 0;
-    if (s != SQ_OK && worst == SQ_OK) worst = s;
+    if (!probs[i].ctx) return SQ_ERR_ARG;
+    bool seen = false;
+    for (auto* c : ctxs) seen = seen || c == probs[i].ctx;
+    if (!seen) ctxs.push_back(probs[i].ctx);
   }
-  return worst;
+  for (auto* c : ctxs) {
+    sq_status s = enter_stream(c);
+    if (s != SQ_OK) return s;
+  }
+  sq_status s = solve_batch_impl(probs, n_probs, params, stats);
+  for (auto* c : ctxs) {
+    sq_status s2 = leave_stream(c);
+    if (s == SQ_OK) s = s2;
+  }
+  return s;
 }
 
 }  // extern "C"

@@ -38,6 +38,7 @@ struct Workspace {
   void* base = nullptr;
   int n_rhs = 0;
   int inner = -1;
+  int Vh = 0;
   // FP64 fields (even parity unless noted), n_rhs sources each
   Field b64, x64, r64, t64o, x64o;  // t64o, x64o: odd parity
   // inner-precision fields
@@ -62,6 +63,16 @@ struct Workspace {
   std::vector<cudaEvent_t> pev;
   int* hist = nullptr;  // [2][chunk]: sources active / updated per iteration
   int hist_chunk = 0;
+};
+
+// Workspaces, streams and the captured graph of sq_solve_batch, kept in the
+// first problem's context between calls.
+struct BatchCache {
+  std::vector<Workspace*> ws;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> events;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<unsigned long long> key;
 };
 
 // Kernel classes of one solver iteration (profiling), in launch order.
@@ -111,6 +122,8 @@ struct sq_ctx {
   // device error word
   int* d_err = nullptr;
   sq::Workspace ws;
+  sq::BatchCache* batch = nullptr;
+  unsigned long long uid = 0;  // unique per context (graph cache keys)
   std::map<long long, sq::Shape> tuned;
   std::string last_error;
   long long launches = 0;          // kernels launched (graph nodes included)
@@ -169,6 +182,8 @@ Shape tune_dslash(sq_ctx* c, DslashCall d, cudaStream_t s);
 // ---- solver (sq_solver.cu)
 sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, double* sol, int n,
                      double tol, const sq_solve_params* prm, sq_solve_stats* stats);
+sq_status solve_batch_impl(const sq_problem* probs, int n_probs, const sq_solve_params* prm,
+                           sq_solve_stats* stats);
 
 void release_workspace(sq_ctx* c);
 

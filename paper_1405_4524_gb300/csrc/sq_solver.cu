@@ -300,8 +300,7 @@ __global__ void k_init(RhsState* st, Control* ctl, int* update_list, const doubl
 // ---------------------------------------------------------------------------
 static inline int px_of(int inner) { return inner == P64 ? P64 : P32; }
 
-static void free_ws(sq_ctx* c) {
-  Workspace& w = c->ws;
+static void free_ws(Workspace& w) {
   if (w.graph) cudaGraphExecDestroy(w.graph);
   for (auto e : w.pev) cudaEventDestroy(e);
   if (w.hist) cudaFree(w.hist);
@@ -309,12 +308,25 @@ static void free_ws(sq_ctx* c) {
   w = Workspace();
 }
 
-void release_workspace(sq_ctx* c) { free_ws(c); }
+void release_workspace(sq_ctx* c) {
+  free_ws(c->ws);
+  if (c->batch) {
+    BatchCache* b = c->batch;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (auto* w : b->ws) {
+      free_ws(*w);
+      delete w;
+    }
+    for (auto s : b->streams) cudaStreamDestroy(s);
+    for (auto e : b->events) cudaEventDestroy(e);
+    delete b;
+    c->batch = nullptr;
+  }
+}
 
-static sq_status alloc_ws(sq_ctx* c, int n, int inner) {
-  Workspace& w = c->ws;
-  if (w.base && w.n_rhs == n && w.inner == inner) return SQ_OK;
-  free_ws(c);
+static sq_status alloc_ws(sq_ctx* c, Workspace& w, int n, int inner) {
+  if (w.base && w.n_rhs == n && w.inner == inner && w.Vh == c->Vh) return SQ_OK;
+  free_ws(w);
   const int Vh = c->Vh;
   const size_t f64 = field_bytes(Vh, P64, n), fin = field_bytes(Vh, inner, n);
   const size_t fx = field_bytes(Vh, px_of(inner), n);
@@ -343,6 +355,7 @@ static sq_status alloc_ws(sq_ctx* c, int n, int inner) {
   w.bytes = tot;
   w.n_rhs = n;
   w.inner = inner;
+  w.Vh = Vh;
   Field* f64s[7] = {&w.b64, &w.x64, &w.r64, &w.t64o, &w.x64o, &w.eta_e, &w.eta_o};
   for (int i = 0; i < 7; i++) *f64s[i] = make_field(b + o_f64 + al(f64) * i, Vh, P64, n);
   Field* fins[7] = {&w.r, &w.rh, &w.p, &w.v, &w.s, &w.t, &w.to};
@@ -357,8 +370,8 @@ static sq_status alloc_ws(sq_ctx* c, int n, int inner) {
   w.update_list = (int*)(b + o_ul);
   w.scal = (double*)(b + o_sc);
   w.nblk_stride = nblk;
-  cudaMemsetAsync(w.counter, 0, (size_t)n * sizeof(unsigned), c->stream);
-  return SQ_OK;
+  e = cudaMemset(w.counter, 0, (size_t)n * sizeof(unsigned));
+  return cuda_check(c, e, "workspace counters");
 }
 
 static RedArgs red_args(const Workspace& w) {
@@ -400,9 +413,8 @@ struct Marks {
 };
 
 template <int P, int PX>
-static void launch_iteration(sq_ctx* c, const CloverSet& cs, double kappa, Shape sh, cudaStream_t s, Marks m,
-                             int it, int chunk) {
-  Workspace& w = c->ws;
+static void launch_iteration(sq_ctx* c, Workspace& w, const CloverSet& cs, double kappa, Shape sh, cudaStream_t s,
+                             Marks m, int it, int chunk) {
   const int n = w.n_rhs;
   dim3 bb(kBlasShape.sx, kBlasShape.ry);
   dim3 bg((c->Vh + kBlasShape.sx - 1) / kBlasShape.sx, (n + kBlasShape.ry - 1) / kBlasShape.ry);
@@ -473,8 +485,7 @@ static void launch_iteration(sq_ctx* c, const CloverSet& cs, double kappa, Shape
 // the FP64 update alone (used once at the start: r = bhat - Mhat x0; with
 // x0 = 0 the residual is bhat itself and no operator is applied)
 template <int P, int PX>
-static void launch_update(sq_ctx* c, const CloverSet& cs, double kappa, cudaStream_t s, bool zero_x) {
-  Workspace& w = c->ws;
+static void launch_update(sq_ctx* c, Workspace& w, const CloverSet& cs, double kappa, cudaStream_t s, bool zero_x) {
   const int n = w.n_rhs;
   dim3 bb(kBlasShape.sx, kBlasShape.ry);
   dim3 bg((c->Vh + kBlasShape.sx - 1) / kBlasShape.sx, (n + kBlasShape.ry - 1) / kBlasShape.ry);
@@ -512,8 +523,8 @@ static void launch_update(sq_ctx* c, const CloverSet& cs, double kappa, cudaStre
   c->launches += 6;
 }
 
-typedef void (*IterFn)(sq_ctx*, const CloverSet&, double, Shape, cudaStream_t, Marks, int, int);
-typedef void (*UpdFn)(sq_ctx*, const CloverSet&, double, cudaStream_t, bool);
+typedef void (*IterFn)(sq_ctx*, Workspace&, const CloverSet&, double, Shape, cudaStream_t, Marks, int, int);
+typedef void (*UpdFn)(sq_ctx*, Workspace&, const CloverSet&, double, cudaStream_t, bool);
 
 static void fns_for(int inner, IterFn* it, UpdFn* up) {
   if (inner == P64) { *it = launch_iteration<P64, P64>; *up = launch_update<P64, P64>; }
@@ -565,8 +576,7 @@ static Cost class_cost(int kc, int inner, int recon, double Vh, double na, doubl
 }
 
 // FP64 full-lattice residual norms^2 of (x64 even, x64o odd) -> scal[0..n) even, scal[n..2n) odd
-static void launch_full_residual(sq_ctx* c, const CloverSet& cs, double kappa, cudaStream_t s) {
-  Workspace& w = c->ws;
+static void launch_full_residual(sq_ctx* c, Workspace& w, const CloverSet& cs, double kappa, cudaStream_t s) {
   const int n = w.n_rhs;
   DslashCall d;
   memset(&d, 0, sizeof(d));
@@ -590,16 +600,25 @@ static void launch_full_residual(sq_ctx* c, const CloverSet& cs, double kappa, c
   c->launches += 6;
 }
 
-sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, double* sol, int n, double tol,
-                     const sq_solve_params* prm_in, sq_solve_stats* stats) {
-  auto t0 = std::chrono::steady_clock::now();
-  sq_solve_params prm;
-  if (prm_in) prm = *prm_in;
-  else sq_default_params(&prm);
-  if (!c) return SQ_ERR_ARG;
-  if (!src || !sol || n <= 0) return set_error(c, SQ_ERR_ARG, "sq_solve: null buffer or n_rhs <= 0");
-  if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(c, SQ_ERR_ARG, "sq_solve: tol must be > 0");
-  if (!std::isfinite(kappa) || !std::isfinite(csw)) return set_error(c, SQ_ERR_ARG, "sq_solve: non-finite kappa/c_sw");
+// One problem of a solve: a lattice (context), kappa, its sources.
+struct Prob {
+  sq_ctx* c = nullptr;
+  double kappa = 0, csw = 0, tol = 0;
+  const double* src = nullptr;
+  double* sol = nullptr;
+  int n = 0;
+  sq_solve_stats* stats = nullptr;
+  CloverSet* cs = nullptr;
+  Workspace* w = nullptr;
+  cudaStream_t s = nullptr;
+  Shape sh;
+  IterFn iter = nullptr;
+  UpdFn upd = nullptr;
+  int recon_in = 12;
+  std::vector<double> enorm2, target2;
+};
+
+static sq_status validate_params(sq_ctx* c, sq_solve_params& prm) {
   if (prm.inner_prec < P64 || prm.inner_prec > P16) return set_error(c, SQ_ERR_ARG, "sq_solve: bad inner_prec");
   if (prm.io != SQ_HOST && prm.io != SQ_DEVICE) return set_error(c, SQ_ERR_ARG, "sq_solve: bad io");
   if (prm.max_iter <= 0) return set_error(c, SQ_ERR_ARG, "sq_solve: max_iter must be > 0");
@@ -609,36 +628,61 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
   if (!(prm.delta > 0.0)) prm.delta = prm.inner_prec == P16 ? 3e-3 : 1e-4;
   if (prm.chunk <= 0) prm.chunk = 16;
   if (prm.chunk > 256) return set_error(c, SQ_ERR_ARG, "sq_solve: chunk must be <= 256");
-  if (!c->have_gauge) return set_error(c, SQ_ERR_STATE, "sq_solve: no gauge field loaded");
+  if (prm.sites_per_block > 0 || prm.rhs_per_block > 0) {
+    if (prm.sites_per_block <= 0 || prm.rhs_per_block <= 0 || prm.sites_per_block % 32 ||
+        prm.sites_per_block * prm.rhs_per_block > 256)
+      return set_error(c, SQ_ERR_ARG, "sq_solve: bad CTA shape");
+  }
+  return SQ_OK;
+}
+
+// Per problem, on its stream: clover, workspace, sources, Schur source, norms,
+// targets and the tuned dslash shape.
+static sq_status setup_problem(Prob& p, const sq_solve_params& prm) {
+  sq_ctx* c = p.c;
   const int inner = prm.inner_prec;
-  CloverSet* cs = nullptr;
-  sq_status st = find_clover(c, kappa, csw, &cs);
+  if (!p.src || !p.sol || p.n <= 0) return set_error(c, SQ_ERR_ARG, "sq_solve: null buffer or n_rhs <= 0");
+  if (!(p.tol > 0.0) || !std::isfinite(p.tol)) return set_error(c, SQ_ERR_ARG, "sq_solve: tol must be > 0");
+  if (!std::isfinite(p.kappa) || !std::isfinite(p.csw))
+    return set_error(c, SQ_ERR_ARG, "sq_solve: non-finite kappa/c_sw");
+  if (!c->have_gauge) return set_error(c, SQ_ERR_STATE, "sq_solve: no gauge field loaded");
+  if (inner == P16 && !c->su3) return set_error(c, SQ_ERR_ARG, "sq_solve: FP16 inner solves need SU(3) links");
+  sq_status st = find_clover(c, p.kappa, p.csw, &p.cs);
   if (st != SQ_OK) return st;
-  st = alloc_ws(c, n, inner);
+  st = alloc_ws(c, *p.w, p.n, inner);
   if (st != SQ_OK) return st;
-  Workspace& w = c->ws;
-  cudaStream_t s = c->stream;
+  Workspace& w = *p.w;
+  cudaStream_t s = p.s;
+  const int n = p.n;
   const size_t lex_doubles = (size_t)n * c->V * 24;
-  // sources to the device, finiteness
-  const double* dsrc = src;
+  const double* dsrc = p.src;
   if (prm.io == SQ_HOST) {
-    cudaMemcpyAsync(w.lex, src, lex_doubles * sizeof(double), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(w.lex, p.src, lex_doubles * sizeof(double), cudaMemcpyHostToDevice, s);
     dsrc = w.lex;
   }
+  // the context stream is used by check_finite; order it after this stream
+  cudaEvent_t ev;
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  cudaEventRecord(ev, s);
+  cudaStreamWaitEvent(c->stream, ev, 0);
   int bad = 0;
   st = check_finite(c, dsrc, lex_doubles, &bad);
+  if (st == SQ_OK && bad) st = set_error(c, SQ_ERR_NONFINITE, "sq_solve: NaN or Inf in the sources");
+  cudaEventDestroy(ev);
   if (st != SQ_OK) return st;
-  if (bad) return set_error(c, SQ_ERR_NONFINITE, "sq_solve: NaN or Inf in the sources");
   launch_pack(c, w.eta_e, dsrc, 0, P64, n, s);
   launch_pack(c, w.eta_o, dsrc, 1, P64, n, s);
   c->launches += 3;
-  // initial guess (even sites) or zero
   if (prm.use_x0) {
-    const double* dx0 = sol;
+    const double* dx0 = p.sol;
     if (prm.io == SQ_HOST) {
-      cudaMemcpyAsync(w.lex, sol, lex_doubles * sizeof(double), cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(w.lex, p.sol, lex_doubles * sizeof(double), cudaMemcpyHostToDevice, s);
       dx0 = w.lex;
     }
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaEventRecord(ev, s);
+    cudaStreamWaitEvent(c->stream, ev, 0);
+    cudaEventDestroy(ev);
     bad = 0;
     st = check_finite(c, dx0, lex_doubles, &bad);
     if (st != SQ_OK) return st;
@@ -657,228 +701,390 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
   cudaMemcpyAsync(eta2.data(), w.scal, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, s);
   // bhat = A_ee^{-1} (eta_e + k D_eo A_oo^{-1} eta_o)
   Field none = make_field(nullptr, c->Vh, P64, n);
-  launch_clover64(c, *cs, w.t64o, none, w.eta_o, 1, 0.0, 1.0, 1, n, s);
+  launch_clover64(c, *p.cs, w.t64o, none, w.eta_o, 1, 0.0, 1.0, 1, n, s);
   DslashCall d;
   memset(&d, 0, sizeof(d));
   d.prec = P64;
   d.recon = 18;
-  d.cs = cs;
+  d.cs = p.cs;
   d.n = n;
   d.shape = kBlasShape;
   d.ra = ra;
-  d.out = w.r64; d.in = w.t64o; d.x = w.eta_e; d.p_out = 0; d.xpay = 1; d.a = kappa;
+  d.out = w.r64; d.in = w.t64o; d.x = w.eta_e; d.p_out = 0; d.xpay = 1; d.a = p.kappa;
   launch_dslash(c, d, s);
-  launch_clover64(c, *cs, w.b64, none, w.r64, 0, 0.0, 1.0, 1, n, s);
+  launch_clover64(c, *p.cs, w.b64, none, w.r64, 0, 0.0, 1.0, 1, n, s);
   c->launches += 5;
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_check(c, e, "sq_solve setup");
-  std::vector<double> target2(n), enorm2(n);
+  p.target2.resize(n);
+  p.enorm2.resize(n);
   for (int k = 0; k < n; k++) {
-    enorm2[k] = eta2[k] + eta2[n + k];
-    double t = tol * std::sqrt(enorm2[k]) / cs->a_bound;
-    target2[k] = t * t;
+    p.enorm2[k] = eta2[k] + eta2[n + k];
+    double t = p.tol * std::sqrt(p.enorm2[k]) / p.cs->a_bound;
+    p.target2[k] = t * t;
   }
-  // dslash launch shape
-  Shape sh;
   if (prm.sites_per_block > 0 && prm.rhs_per_block > 0) {
-    sh.sx = prm.sites_per_block;
-    sh.ry = prm.rhs_per_block;
-    if (sh.sx % 32 || sh.sx * sh.ry > 256) return set_error(c, SQ_ERR_ARG, "sq_solve: bad CTA shape");
+    p.sh.sx = prm.sites_per_block;
+    p.sh.ry = prm.rhs_per_block;
+    p.sh.order = 0;
   } else {
     DslashCall tcall;
     memset(&tcall, 0, sizeof(tcall));
     tcall.prec = inner;
     tcall.recon = inner == P64 ? 18 : (inner == P16 ? 12 : c->recon);
-    tcall.cs = cs;
+    tcall.cs = p.cs;
     tcall.clover = 1;
     tcall.out = w.to;
     tcall.in = w.p;
     tcall.p_out = 1;
     tcall.n = n;
     cudaMemsetAsync(w.p.data, 0, field_bytes(c->Vh, inner, n), s);
-    sh = tune_dslash(c, tcall, s);
+    p.sh = tune_dslash(c, tcall, s);
   }
-  IterFn iter;
-  UpdFn upd;
-  fns_for(inner, &iter, &upd);
-  const bool prof = prm.profile != 0;
+  p.recon_in = inner == P64 ? 18 : (inner == P16 ? 12 : c->recon);
+  fns_for(inner, &p.iter, &p.upd);
+  return SQ_OK;
+}
+
+// The iteration loop of all problems: each problem's `chunk` iterations are
+// a branch of one captured CUDA graph (fork/join through events), so the
+// problems advance concurrently from a single graph launch per chunk; the
+// host reads one integer per problem (sources still active) per launch.
+// Then per problem: reconstruction, FP64 full residual, solutions out.
+static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, cudaStream_t sb,
+                              cudaGraphExec_t* graph, std::vector<unsigned long long>* gkey,
+                              std::vector<cudaEvent_t>& evs, sq_status* result) {
+  const int np = (int)P.size();
+  const bool prof = prm.profile != 0 && np == 1;
   const int chunk = prm.chunk;
+  const double delta = prm.inner_prec == P64 ? 0.0 : prm.delta;
+  sq_ctx* c0 = P[0].c;
+  cudaError_t e = cudaSuccess;
   if (prof) {
+    Workspace& w = *P[0].w;
     const size_t need = (size_t)chunk * (KC_N + 1);
-    if (w.pev.size() < need) {
-      for (size_t i = w.pev.size(); i < need; i++) {
-        cudaEvent_t ev;
-        cudaEventCreate(&ev);
-        w.pev.push_back(ev);
-      }
+    for (size_t i = w.pev.size(); i < need; i++) {
+      cudaEvent_t ev;
+      cudaEventCreate(&ev);
+      w.pev.push_back(ev);
     }
     if (w.hist_chunk < chunk) {
       if (w.hist) cudaFree(w.hist);
       w.hist = nullptr;
       e = cudaMalloc((void**)&w.hist, 2 * chunk * sizeof(int));
-      if (e != cudaSuccess) return cuda_check(c, e, "profile buffers");
+      if (e != cudaSuccess) return cuda_check(c0, e, "profile buffers");
       w.hist_chunk = chunk;
     }
-    for (int k = 0; k < KC_N; k++) c->prof[k] = KStat();
-    c->prof_valid = 0;
-    c->prof_inner = inner;
+    for (int k = 0; k < KC_N; k++) c0->prof[k] = KStat();
+    c0->prof_valid = 0;
+    c0->prof_inner = prm.inner_prec;
+  }
+  while ((int)evs.size() < 2 * np + 2) {
+    cudaEvent_t ev;
+    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    evs.push_back(ev);
   }
   int* h_active = nullptr;
-  cudaMallocHost((void**)&h_active, (1 + 2 * chunk) * sizeof(int));
-  const double delta = inner == P64 ? 0.0 : prm.delta;
-  double* d_t2 = w.scal;  // scratch for the targets
-  sq_status result = SQ_OK;
-  const int recon_in = inner == P64 ? 18 : (inner == P16 ? 12 : c->recon);
+  e = cudaMallocHost((void**)&h_active, (np + 2 * chunk) * sizeof(int));
+  if (e != cudaSuccess) return cuda_check(c0, e, "pinned read-back buffer");
+  std::vector<int> tot_it(np, 0);
   for (int attempt = 0; attempt < 4; attempt++) {
-    cudaMemcpyAsync(d_t2, target2.data(), n * sizeof(double), cudaMemcpyHostToDevice, s);
-    k_init<<<(n + 127) / 128, 128, 0, s>>>(w.st, w.ctl, w.update_list, d_t2, delta * delta, prm.max_iter,
-                                          prm.outer == SQ_OUTER_DEFECT ? 1 : 0, n);
-    c->launches += 1;
-    // x = 0 only on the first pass without an initial guess
-    upd(c, *cs, kappa, s, attempt == 0 && !prm.use_x0);
-    // graph of `chunk` iterations; the key holds everything baked into it
-    std::vector<unsigned long long> key = {
-        (unsigned long long)n, (unsigned long long)inner, (unsigned long long)sh.sx, (unsigned long long)sh.ry,
-        (unsigned long long)chunk, (unsigned long long)prof, (unsigned long long)c->recon,
-        (unsigned long long)(uintptr_t)w.base, (unsigned long long)(uintptr_t)c->U64,
-        (unsigned long long)(uintptr_t)c->U32, (unsigned long long)(uintptr_t)c->U16,
-        (unsigned long long)(uintptr_t)cs->Ainv64, (unsigned long long)(uintptr_t)cs->Ainv32,
-        (unsigned long long)(uintptr_t)cs->Ainv16, (unsigned long long)(uintptr_t)w.hist,
-        (unsigned long long)(uintptr_t)(w.pev.empty() ? nullptr : w.pev[0])};
-    unsigned long long kb;
-    memcpy(&kb, &kappa, sizeof(kb));
-    key.push_back(kb);
-    const bool use_graph = prm.use_graph != 0;
-    if (use_graph && (!w.graph || key != w.graph_key)) {
-      if (w.graph) {
-        cudaGraphExecDestroy(w.graph);
-        w.graph = nullptr;
+    for (int i = 0; i < np; i++) {
+      Prob& p = P[i];
+      Workspace& w = *p.w;
+      cudaMemcpyAsync(w.scal, p.target2.data(), p.n * sizeof(double), cudaMemcpyHostToDevice, p.s);
+      k_init<<<(p.n + 127) / 128, 128, 0, p.s>>>(w.st, w.ctl, w.update_list, w.scal, delta * delta, prm.max_iter,
+                                                 prm.outer == SQ_OUTER_DEFECT ? 1 : 0, p.n);
+      p.c->launches += 1;
+      p.upd(p.c, w, *p.cs, p.kappa, p.s, attempt == 0 && !prm.use_x0);
+      if (p.s != sb) {
+        cudaEventRecord(evs[i], p.s);
+        cudaStreamWaitEvent(sb, evs[i], 0);
       }
-      cudaGraph_t g;
-      e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-      if (e == cudaSuccess) {
-        for (int i = 0; i < chunk; i++) {
+    }
+    // the graph key holds everything baked into the captured kernels
+    std::vector<unsigned long long> key = {(unsigned long long)np, (unsigned long long)prm.inner_prec,
+                                           (unsigned long long)chunk, (unsigned long long)prof};
+    for (auto& p : P) {
+      unsigned long long kb;
+      memcpy(&kb, &p.kappa, sizeof(kb));
+      const unsigned long long v[] = {p.c->uid, (unsigned long long)p.n, (unsigned long long)p.sh.sx,
+                                      (unsigned long long)p.sh.ry, (unsigned long long)p.sh.order,
+                                      (unsigned long long)p.c->recon, (unsigned long long)(uintptr_t)p.w->base,
+                                      (unsigned long long)(uintptr_t)p.c->U64, (unsigned long long)(uintptr_t)p.c->U32,
+                                      (unsigned long long)(uintptr_t)p.c->U16,
+                                      (unsigned long long)(uintptr_t)p.cs->Ainv64,
+                                      (unsigned long long)(uintptr_t)p.cs->Ainv32,
+                                      (unsigned long long)(uintptr_t)p.cs->Ainv16,
+                                      (unsigned long long)(uintptr_t)p.w->hist,
+                                      (unsigned long long)(uintptr_t)(p.w->pev.empty() ? nullptr : p.w->pev[0]),
+                                      (unsigned long long)(uintptr_t)p.s, kb};
+      key.insert(key.end(), v, v + sizeof(v) / sizeof(v[0]));
+    }
+    const bool use_graph = prm.use_graph != 0;
+    auto launch_chunk = [&](bool capture) {
+      for (int i = 0; i < np; i++) {
+        Prob& p = P[i];
+        cudaStream_t ps = np == 1 ? sb : p.s;
+        if (ps != sb) {  // fork
+          cudaEventRecord(evs[np + i], sb);
+          cudaStreamWaitEvent(ps, evs[np + i], 0);
+        }
+        for (int it = 0; it < chunk; it++) {
           Marks m;
           if (prof) {
-            m.ev = &w.pev[(size_t)i * (KC_N + 1)];
-            m.capture = true;
+            m.ev = &p.w->pev[(size_t)it * (KC_N + 1)];
+            m.capture = capture;
           }
-          iter(c, *cs, kappa, sh, s, m, i, chunk);
+          p.iter(p.c, *p.w, *p.cs, p.kappa, p.sh, ps, m, it, chunk);
         }
-        e = cudaStreamEndCapture(s, &g);
+        if (ps != sb) {  // join
+          cudaEventRecord(evs[i], ps);
+          cudaStreamWaitEvent(sb, evs[i], 0);
+        }
+      }
+    };
+    if (use_graph && (!*graph || key != *gkey)) {
+      if (*graph) {
+        cudaGraphExecDestroy(*graph);
+        *graph = nullptr;
+      }
+      cudaGraph_t g;
+      e = cudaStreamBeginCapture(sb, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        launch_chunk(true);
+        e = cudaStreamEndCapture(sb, &g);
       }
       if (e == cudaSuccess) {
-        e = cudaGraphInstantiate(&w.graph, g, 0);
+        e = cudaGraphInstantiate(graph, g, 0);
         cudaGraphDestroy(g);
       }
       if (e != cudaSuccess) {
         cudaFreeHost(h_active);
-        return cuda_check(c, e, "graph capture of the inner loop");
+        return cuda_check(c0, e, "graph capture of the inner loop");
       }
-      w.graph_key = key;
+      *gkey = key;
     }
     long long launched = 0;
     const long long cap = (long long)prm.max_iter + 4LL * chunk;
     for (;;) {
-      if (use_graph) {
-        e = cudaGraphLaunch(w.graph, s);
-      } else {
-        for (int i = 0; i < chunk; i++) {
-          Marks m;
-          if (prof) m.ev = &w.pev[(size_t)i * (KC_N + 1)];
-          iter(c, *cs, kappa, sh, s, m, i, chunk);
-        }
+      if (use_graph) e = cudaGraphLaunch(*graph, sb);
+      else {
+        launch_chunk(false);
         e = cudaGetLastError();
       }
       if (e != cudaSuccess) break;
-      c->launches += (long long)chunk * KC_N;
+      for (auto& p : P) p.c->launches += (long long)chunk * KC_N;
       launched += chunk;
-      cudaMemcpyAsync(h_active, &w.ctl->n_active, sizeof(int), cudaMemcpyDeviceToHost, s);
-      if (prof) cudaMemcpyAsync(h_active + 1, w.hist, 2 * chunk * sizeof(int), cudaMemcpyDeviceToHost, s);
-      e = cudaStreamSynchronize(s);
+      for (int i = 0; i < np; i++)
+        cudaMemcpyAsync(h_active + i, &P[i].w->ctl->n_active, sizeof(int), cudaMemcpyDeviceToHost, sb);
+      if (prof) cudaMemcpyAsync(h_active + np, P[0].w->hist, 2 * chunk * sizeof(int), cudaMemcpyDeviceToHost, sb);
+      e = cudaStreamSynchronize(sb);
       if (e != cudaSuccess) break;
       if (prof) {
+        Workspace& w = *P[0].w;
         for (int i = 0; i < chunk; i++) {
-          const double na = h_active[1 + i], nu = h_active[1 + chunk + i];
+          const double na = h_active[np + i], nu = h_active[np + chunk + i];
           for (int kc = 0; kc < KC_N; kc++) {
             float ms = 0;
             cudaEventElapsedTime(&ms, w.pev[(size_t)i * (KC_N + 1) + kc], w.pev[(size_t)i * (KC_N + 1) + kc + 1]);
-            Cost cost = class_cost(kc, inner, recon_in, (double)c->Vh, na, nu);
-            KStat& ks = c->prof[kc];
+            Cost cost = class_cost(kc, prm.inner_prec, P[0].recon_in, (double)P[0].c->Vh, na, nu);
+            KStat& ks = c0->prof[kc];
             ks.launches += 1;
             ks.ms += ms;
             ks.bytes += cost.bytes;
             ks.flops += cost.flops;
           }
         }
-        c->prof_valid = 1;
+        c0->prof_valid = 1;
       }
-      if (prm.verbose) fprintf(stderr, "libstochq: %lld iterations, %d sources active\n", launched, h_active[0]);
-      if (h_active[0] == 0 || launched > cap) break;
+      int active = 0;
+      for (int i = 0; i < np; i++) active += h_active[i];
+      if (prm.verbose) fprintf(stderr, "libstochq: %lld iterations, %d sources active\n", launched, active);
+      if (active == 0 || launched > cap) break;
     }
     if (e != cudaSuccess) {
       cudaFreeHost(h_active);
-      return cuda_check(c, e, "inner loop");
+      return cuda_check(c0, e, "inner loop");
     }
-    // psi_o = A_oo^{-1} (eta_o + k D_oe psi_e), then the full FP64 residual
-    d.out = w.t64o; d.in = w.x64; d.x = w.eta_o; d.p_out = 1; d.xpay = 1; d.a = kappa; d.fin = FIN_NONE;
-    d.list = nullptr;
-    d.count = nullptr;
-    launch_dslash(c, d, s);
-    launch_clover64(c, *cs, w.x64o, none, w.t64o, 1, 0.0, 1.0, 1, n, s);
-    c->launches += 2;
-    launch_full_residual(c, *cs, kappa, s);
-    std::vector<double> res2(2 * n);
-    cudaMemcpyAsync(res2.data(), w.scal, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, s);
-    std::vector<RhsState> hs(n);
-    cudaMemcpyAsync(hs.data(), w.st, n * sizeof(RhsState), cudaMemcpyDeviceToHost, s);
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      cudaFreeHost(h_active);
-      return cuda_check(c, e, "final residual");
-    }
+    // per problem: psi_o = A_oo^{-1} (eta_o + k D_oe psi_e), full FP64 residual
     bool retry = false;
-    result = SQ_OK;
-    for (int k = 0; k < n; k++) {
-      double rr = enorm2[k] > 0 ? std::sqrt((res2[k] + res2[n + k]) / enorm2[k]) : 0.0;
-      int status = hs[k].status;
-      if (status == SQ_OK && !(rr <= tol)) {
-        if (attempt < 3) {
-          retry = true;
-          target2[k] *= 1.0 / 16.0;
-        } else {
-          status = SQ_ERR_NOCONV;
+    for (int i = 0; i < np; i++) {
+      Prob& p = P[i];
+      sq_ctx* c = p.c;
+      Workspace& w = *p.w;
+      const int n = p.n;
+      DslashCall d;
+      memset(&d, 0, sizeof(d));
+      d.prec = P64;
+      d.recon = 18;
+      d.cs = p.cs;
+      d.n = n;
+      d.shape = kBlasShape;
+      d.ra = red_args(w);
+      d.out = w.t64o; d.in = w.x64; d.x = w.eta_o; d.p_out = 1; d.xpay = 1; d.a = p.kappa;
+      launch_dslash(c, d, sb);
+      Field none = make_field(nullptr, c->Vh, P64, n);
+      launch_clover64(c, *p.cs, w.x64o, none, w.t64o, 1, 0.0, 1.0, 1, n, sb);
+      c->launches += 2;
+      launch_full_residual(c, w, *p.cs, p.kappa, sb);
+      std::vector<double> res2(2 * n);
+      cudaMemcpyAsync(res2.data(), w.scal, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, sb);
+      std::vector<RhsState> hs(n);
+      cudaMemcpyAsync(hs.data(), w.st, n * sizeof(RhsState), cudaMemcpyDeviceToHost, sb);
+      e = cudaStreamSynchronize(sb);
+      if (e != cudaSuccess) {
+        cudaFreeHost(h_active);
+        return cuda_check(c0, e, "final residual");
+      }
+      for (int k = 0; k < n; k++) {
+        double rr = p.enorm2[k] > 0 ? std::sqrt((res2[k] + res2[n + k]) / p.enorm2[k]) : 0.0;
+        int status = hs[k].status;
+        if (status == SQ_OK && !(rr <= p.tol)) {
+          if (attempt < 3) {
+            retry = true;
+            p.target2[k] *= 1.0 / 16.0;
+          } else {
+            status = SQ_ERR_NOCONV;
+          }
         }
+        if (p.stats) {
+          sq_solve_stats& o = p.stats[k];
+          if (attempt == 0) memset(&o, 0, sizeof(o));
+          o.status = status;
+          o.iterations += hs[k].iter;
+          o.updates += hs[k].updates;
+          o.restarts += hs[k].restarts;
+          o.true_residual = rr;
+        }
+        if (status != SQ_OK && *result == SQ_OK) *result = (sq_status)status;
       }
-      if (stats) {
-        sq_solve_stats& o = stats[k];
-        if (attempt == 0) memset(&o, 0, sizeof(o));
-        o.status = status;
-        o.iterations += hs[k].iter;
-        o.updates += hs[k].updates;
-        o.restarts += hs[k].restarts;
-        o.true_residual = rr;
-      }
-      if (status != SQ_OK && result == SQ_OK) result = (sq_status)status;
     }
     if (!retry) break;
+    *result = SQ_OK;
     if (prm.verbose) fprintf(stderr, "libstochq: tightening the Schur target\n");
-    // continue from the current x (even sites already in x64)
+    // the next pass continues from the current x (even sites in x64)
+    for (auto& p : P)
+      if (p.s != sb) {
+        cudaEventRecord(evs[0], sb);
+        cudaStreamWaitEvent(p.s, evs[0], 0);
+      }
   }
   cudaFreeHost(h_active);
   // solutions out
-  double* dsol = prm.io == SQ_HOST ? w.lex : sol;
-  launch_unpack(c, dsol, w.x64, 0, P64, n, s);
-  launch_unpack(c, dsol, w.x64o, 1, P64, n, s);
-  c->launches += 2;
-  if (prm.io == SQ_HOST)
-    cudaMemcpyAsync(sol, w.lex, lex_doubles * sizeof(double), cudaMemcpyDeviceToHost, s);
-  e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_check(c, e, "solution copy");
+  for (auto& p : P) {
+    sq_ctx* c = p.c;
+    Workspace& w = *p.w;
+    double* dsol = prm.io == SQ_HOST ? w.lex : p.sol;
+    launch_unpack(c, dsol, w.x64, 0, P64, p.n, sb);
+    launch_unpack(c, dsol, w.x64o, 1, P64, p.n, sb);
+    c->launches += 2;
+    if (prm.io == SQ_HOST)
+      cudaMemcpyAsync(p.sol, w.lex, (size_t)p.n * c->V * 24 * sizeof(double), cudaMemcpyDeviceToHost, sb);
+  }
+  e = cudaStreamSynchronize(sb);
+  return cuda_check(c0, e, "solution copy");
+}
+
+sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, double* sol, int n, double tol,
+                     const sq_solve_params* prm_in, sq_solve_stats* stats) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!c) return SQ_ERR_ARG;
+  sq_solve_params prm;
+  if (prm_in) prm = *prm_in;
+  else sq_default_params(&prm);
+  sq_status st = validate_params(c, prm);
+  if (st != SQ_OK) return st;
+  std::vector<Prob> P(1);
+  Prob& p = P[0];
+  p.c = c;
+  p.kappa = kappa;
+  p.csw = csw;
+  p.tol = tol;
+  p.src = src;
+  p.sol = sol;
+  p.n = n;
+  p.stats = stats;
+  p.w = &c->ws;
+  p.s = c->stream;
+  st = setup_problem(p, prm);
+  if (st != SQ_OK) return st;
+  std::vector<cudaEvent_t> evs;
+  sq_status result = SQ_OK;
+  st = run_problems(P, prm, c->stream, &c->ws.graph, &c->ws.graph_key, evs, &result);
+  for (auto ev : evs) cudaEventDestroy(ev);
+  if (st != SQ_OK) return st;
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats)
     for (int k = 0; k < n; k++) stats[k].seconds = secs;
   if (result != SQ_OK) set_error(c, result, "sq_solve: some sources did not converge (see stats)");
+  return result;
+}
+
+sq_status solve_batch_impl(const sq_problem* probs, int np, const sq_solve_params* prm_in, sq_solve_stats* stats) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (!probs || np <= 0) return SQ_ERR_ARG;
+  for (int i = 0; i < np; i++)
+    if (!probs[i].ctx) return SQ_ERR_ARG;
+  sq_ctx* c0 = probs[0].ctx;
+  for (int i = 1; i < np; i++)
+    if (probs[i].ctx->device != c0->device) return set_error(c0, SQ_ERR_ARG, "sq_solve_batch: mixed devices");
+  sq_solve_params prm;
+  if (prm_in) prm = *prm_in;
+  else sq_default_params(&prm);
+  sq_status st = validate_params(c0, prm);
+  if (st != SQ_OK) return st;
+  if (!c0->batch) c0->batch = new BatchCache();
+  BatchCache& B = *c0->batch;
+  while ((int)B.ws.size() < np) B.ws.push_back(new Workspace());
+  while ((int)B.streams.size() < np) {
+    cudaStream_t s;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_check(c0, e, "sq_solve_batch streams");
+    B.streams.push_back(s);
+  }
+  // order every problem's stream after its context's stream
+  std::vector<Prob> P(np);
+  cudaEvent_t ev;
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  size_t off = 0;
+  for (int i = 0; i < np; i++) {
+    Prob& p = P[i];
+    p.c = probs[i].ctx;
+    p.kappa = probs[i].kappa;
+    p.csw = probs[i].c_sw;
+    p.tol = probs[i].tol;
+    p.src = probs[i].sources;
+    p.sol = probs[i].solutions;
+    p.n = probs[i].n_rhs;
+    p.stats = stats ? stats + off : nullptr;
+    off += p.n > 0 ? p.n : 0;
+    p.w = B.ws[i];
+    p.s = B.streams[i];
+    cudaEventRecord(ev, p.c->stream);
+    cudaStreamWaitEvent(p.s, ev, 0);
+  }
+  for (int i = 0; i < np; i++) {
+    st = setup_problem(P[i], prm);
+    if (st != SQ_OK) {
+      cudaEventDestroy(ev);
+      if (P[i].c != c0) set_error(c0, st, "sq_solve_batch: problem %d: %s", i, P[i].c->last_error.c_str());
+      return st;
+    }
+  }
+  // the batch stream (first context's) waits for every problem's set-up
+  for (auto& p : P) {
+    cudaEventRecord(ev, p.s);
+    cudaStreamWaitEvent(c0->stream, ev, 0);
+  }
+  cudaEventDestroy(ev);
+  sq_status result = SQ_OK;
+  st = run_problems(P, prm, c0->stream, &B.graph, &B.key, B.events, &result);
+  if (st != SQ_OK) return st;
+  double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats)
+    for (size_t k = 0; k < off; k++) stats[k].seconds = secs;
+  if (result != SQ_OK) set_error(c0, result, "sq_solve_batch: some sources did not converge (see stats)");
   return result;
 }
 

@@ -216,3 +216,41 @@ def test_state_and_argument_errors():
         assert e.value.status == sq.SQ_ERR_ARG
     finally:
         sq.sq_destroy(ctx)
+
+
+def test_solve_batch_mixed_lattices_and_kappas():
+    """Three problems in one batch: two kappas sharing one lattice and a
+    second lattice; every source against the oracle, and the same
+    solutions as sq_solve gives problem by problem."""
+    from paper_1405_4524_gb300 import stochq as sq
+
+    dimsA, dimsB = (4, 4, 4, 8), (6, 4, 4, 6)
+    sA, sB = Setup(dimsA, 0.25, 1003), Setup(dimsB, 0.25, 1004)
+    try:
+        csw = 1.0
+        probs = [(sA, 0.118, 3, 91), (sA, 0.124, 2, 92), (sB, 0.121, 3, 93)]
+        srcs = [inputs.make_z4(s.dims, n, seed) for (s, k, n, seed) in probs]
+        sols = [np.zeros_like(e) for e in srcs]
+        batch = [dict(ctx=s.ctx, kappa=k, c_sw=csw, sources=srcs[i], solutions=sols[i], n_rhs=n, tol=1e-10)
+                 for i, (s, k, n, seed) in enumerate(probs)]
+        st, stats = sq.sq_solve_batch(batch, sq.sq_default_params(inner_prec=1))
+        assert st == 0 and len(stats) == 8
+        assert all(x["status"] == 0 and x["true_residual"] <= 1e-10 for x in stats)
+        for i, (s, k, n, seed) in enumerate(probs):
+            for j in range(n):
+                ref, _, res = oracle.solve(s.U, srcs[i][j], k, csw, -1.0, tol=1e-13, F=s.F)
+                assert rel(sols[i][j], ref) <= 1e-9, (i, j)
+            single = np.zeros_like(srcs[i])
+            s.sq.sq_solve(s.ctx, k, csw, srcs[i], single, n, 1e-10, sq.sq_default_params(inner_prec=1))
+            for j in range(n):
+                assert rel(single[j], sols[i][j]) <= 1e-9
+        # a second call reuses the cached graph and gives identical results
+        again = [np.zeros_like(e) for e in srcs]
+        for i, b in enumerate(batch):
+            b["solutions"] = again[i]
+        sq.sq_solve_batch(batch, sq.sq_default_params(inner_prec=1))
+        for i in range(3):
+            assert np.array_equal(again[i], sols[i])
+    finally:
+        sA.close()
+        sB.close()
