@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--extras", type=int, default=1, help="FP64/FP16 comparison solves")
     p.add_argument("--e2e", type=int, default=1, help="end-to-end host-buffer measurement")
     p.add_argument("--cpu", type=int, default=1, help="CPU oracle baseline")
+    p.add_argument("--workloads", type=int, default=0,
+                   help="also time the 24^3x48, 32^3x64 and batch workloads (minutes)")
     return p.parse_args()
 
 
@@ -57,6 +59,26 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
     return rank, world, local
+
+
+def reduce_max(x: float, world: int) -> float:
+    """Max of a per-rank scalar over all ranks (the slowest rank times the
+    whole job). Uses a device tensor under NCCL and a host tensor under gloo."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_local: int, world: int, max_ms: float) -> float:
+    """Whole-job sources/s: every rank solves n_local sources per step and
+    the step takes as long as the slowest rank."""
+    return n_local * world / (max_ms / 1000.0)
 
 
 def peaks():
@@ -173,6 +195,61 @@ def cpu_baseline(workload, seconds_budget=12.0):
                        f"(tests/golden/oracle_iterations.json)")}
 
 
+def other_workloads(sq):
+    """Sources/s of the larger workloads (one timed solve each after a
+    warm-up solve), device-resident inputs, tol 1e-10."""
+    import torch
+
+    from paper_1405_4524_gb300 import inputs
+
+    out = {}
+
+    def timed_solve(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, st
+
+    for name, prm in [("24x24x24x48", sq.sq_default_params(inner_prec=sq.SQ_F16)),
+                      ("32x32x32x64", sq.sq_default_params(inner_prec=sq.SQ_F16, outer=sq.SQ_OUTER_DEFECT,
+                                                           delta=1e-3))]:
+        spec, U, eta = inputs.workload(name)
+        ctx = sq.sq_create(spec["dims"], -1)
+        sq.sq_load_gauge(ctx, U, 12)
+        e = torch.from_numpy(eta).cuda()
+        x = torch.zeros_like(e)
+        dt, (_, st) = timed_solve(lambda: sq.sq_solve(ctx, spec["kappa"], spec["csw"], e, x, spec["n_rhs"], TOL, prm))
+        out[name] = {"sources_per_s": round(spec["n_rhs"] / dt, 2), "n_sources": spec["n_rhs"],
+                     "iterations": int(np.mean([s["iterations"] for s in st])),
+                     "max_true_residual": max(s["true_residual"] for s in st),
+                     "solver": "FP16 inner, " + ("defect correction" if prm.outer else "reliable updates")}
+        del e, x
+        sq.sq_destroy(ctx)
+    # 96 sources: 16^3x32 and 24^3x48 at kappa 0.118, 0.121, 0.124 in one batch
+    ctxs, probs, bufs = [], [], []
+    for gi, name in enumerate(["16x16x16x32", "24x24x24x48"]):
+        spec = inputs.WORKLOADS[name]
+        ctx = sq.sq_create(spec["dims"], -1)
+        sq.sq_load_gauge(ctx, inputs.make_links(spec["dims"], spec["eps"], spec["link_seed"]), 12)
+        ctxs.append(ctx)
+        for ki, kappa in enumerate([0.118, 0.121, 0.124]):
+            e = torch.from_numpy(inputs.make_z4(spec["dims"], 16, 3000 + 10 * gi + ki)).cuda()
+            x = torch.zeros_like(e)
+            bufs += [e, x]
+            probs.append(dict(ctx=ctx, kappa=kappa, c_sw=1.0, sources=e, solutions=x, n_rhs=16, tol=TOL))
+    prm = sq.sq_default_params(inner_prec=sq.SQ_F16)
+    dt, (_, st) = timed_solve(lambda: sq.sq_solve_batch(probs, prm))
+    out["batch_96_two_lattices_three_kappas"] = {
+        "sources_per_s": round(96 / dt, 2), "max_true_residual": max(s["true_residual"] for s in st),
+        "iterations_min_max": [int(min(s["iterations"] for s in st)), int(max(s["iterations"] for s in st))]}
+    del bufs
+    for ctx in ctxs:
+        sq.sq_destroy(ctx)
+    return out
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return
@@ -280,11 +357,7 @@ def main():
         wall = time.perf_counter() - w0
         barrier()
         launches = sq.sq_kernel_launches(ctx) - l0
-        ms = sum(a.elapsed_time(b) for a, b in ev) / k
-        if world > 1:
-            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = reduce_max(sum(a.elapsed_time(b) for a, b in ev) / k, world)
         return ms, wall, launches, agg
 
     for _ in range(max(3, args.warmup)):
@@ -295,7 +368,7 @@ def main():
     clk = clocks.stop()
     stats = last["stats"]
     assert all(s["status"] == 0 and s["true_residual"] <= TOL for s in stats), stats
-    value = n * world / (ms / 1000.0)
+    value = job_throughput(n, world, ms)
 
     # end to end through the public API with host buffers (pinned)
     e2e = None
@@ -306,7 +379,7 @@ def main():
         assert all(s["status"] == 0 and s["true_residual"] <= TOL for s in last["stats_e2e"])
         h2d = U.nbytes + eta.nbytes + eta.nbytes  # links, sources, solutions re-read by the contraction
         d2h = eta.nbytes + n * T * 8  # solutions, correlator
-        e2e = {"value": round(n * world / (ms_e2e / 1000.0), 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": round(job_throughput(n, world, ms_e2e), 3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms_e2e, 3)}
 
     # dominant kernel: the dslash class with the largest device time
@@ -350,6 +423,9 @@ def main():
             del sol2
         if "sources_per_s" in extras["fp64_solver"]:
             extras["speedup_vs_fp64_solver"] = round(value / world / extras["fp64_solver"]["sources_per_s"], 2)
+
+    if args.workloads and rank == 0:
+        extras["workloads"] = other_workloads(sq)
 
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,

@@ -35,10 +35,13 @@ struct KArgs {
   RedArgs ra;
 };
 
-// Register budget: __launch_bounds__(256, SQ_DSLASH_MINB) caps registers at
-// 65536 / (256 * SQ_DSLASH_MINB) per thread (2: 128, 3: 85, 4: 64).
-#ifndef SQ_DSLASH_MINB
-#define SQ_DSLASH_MINB 2
+// Register budget of the FP32 / FP16 kernels (per thread). Uncapped, the
+// compiler takes ~200 registers for them (one 256-thread CTA per SM); with
+// the cap two stay resident. Measured on GB300 (16^3x32, 16 sources): caps
+// of 80..128 give 87..101 us per clover dslash, 128 the fastest. The FP64
+// kernel is ALU-bound and stays uncapped (~146 registers).
+#ifndef SQ_DSLASH_LP_REGS
+#define SQ_DSLASH_LP_REGS 128
 #endif
 
 // h = psi_up + SIGN * B_mu psi_dn   (SIGN = -1: forward hop, +1: backward)
@@ -160,7 +163,7 @@ __device__ __forceinline__ void hop_dir(const KArgs& a, int k, int cb, Coord c,
 }
 
 template <int P, int RECON, int CLOV, int XPAY, int FIN>
-__global__ void __launch_bounds__(256, SQ_DSLASH_MINB) k_dslash(const KArgs a) {
+__device__ __forceinline__ void dslash_body(const KArgs& a) {
   typedef typename Real<P>::T R;
   constexpr int NRED = FIN == FIN_ALPHA ? 2 : FIN == FIN_OMEGA ? 3 : 1;
   int sb, rb;
@@ -242,6 +245,16 @@ __global__ void __launch_bounds__(256, SQ_DSLASH_MINB) k_dslash(const KArgs a) {
   if (FIN != FIN_NONE) reduce_finalize<NRED, FIN>(a.ra, red, k, a.nsb, sb);
 }
 
+template <int P, int RECON, int CLOV, int XPAY, int FIN>
+__global__ void __maxnreg__(SQ_DSLASH_LP_REGS) k_dslash(const KArgs a) {
+  dslash_body<P, RECON, CLOV, XPAY, FIN>(a);
+}
+
+template <int CLOV, int XPAY, int FIN>
+__global__ void __launch_bounds__(256) k_dslash64(const KArgs a) {
+  dslash_body<P64, 18, CLOV, XPAY, FIN>(a);
+}
+
 // ---------------------------------------------------------------------------
 // host launcher
 // ---------------------------------------------------------------------------
@@ -249,7 +262,8 @@ int dslash_nblk(const sq_ctx* c, Shape sh) { return (c->Vh + sh.sx - 1) / sh.sx;
 
 template <int P, int RECON, int CLOV, int XPAY, int FIN>
 static void go(const KArgs& a, dim3 grid, dim3 block, cudaStream_t s) {
-  k_dslash<P, RECON, CLOV, XPAY, FIN><<<grid, block, 0, s>>>(a);
+  if (P == P64) k_dslash64<CLOV, XPAY, FIN><<<grid, block, 0, s>>>(a);
+  else k_dslash<P, RECON, CLOV, XPAY, FIN><<<grid, block, 0, s>>>(a);
 }
 
 template <int P, int RECON>

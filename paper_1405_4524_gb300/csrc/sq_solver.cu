@@ -253,7 +253,7 @@ __global__ void k_plan(RhsState* st, Control* ctl, int* update_list, int n) {
       if (k < n && st[k].active) {
         RhsState& q = st[k];
         const double ref = q.defect ? q.rstart2 : q.maxr2;
-        on = q.want_update || q.rnorm2 < 25.0 * q.delta2 * ref || q.rnorm2 < 25.0 * q.target2;
+        on = q.want_update || q.rnorm2 < 25.0 * q.delta2 * ref;
         if (on) {
           q.want_update = 1;
           if (q.defect) q.want_restart = 1;
@@ -267,14 +267,37 @@ __global__ void k_plan(RhsState* st, Control* ctl, int* update_list, int n) {
   if (lane == 0) ctl->n_update = base;
 }
 
+// x64 += xs ; xs = 0 for every source (after the loop: sources that retired
+// on their iterated residual still hold their last correction in xs).
+// f0 = x64, f1 = xs (PX)
+template <int PX>
+__global__ void __launch_bounds__(256) k_flush(const VArgs a) {
+  typedef typename Real<PX>::T RX;
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (cb >= a.Vh || k >= a.n) return;
+  cx<double> x[12];
+  cx<RX> xs[12];
+  SpinorIO<P64>::load(a.f0, k, cb, x);
+  SpinorIO<PX>::load(a.f1, k, cb, xs);
+#pragma unroll
+  for (int j = 0; j < 12; j++) {
+    x[j] = mk(x[j].re + (double)xs[j].re, x[j].im + (double)xs[j].im);
+    xs[j] = mk((RX)0, (RX)0);
+  }
+  SpinorIO<P64>::store(a.f0, k, cb, x);
+  SpinorIO<PX>::store(a.f1, k, cb, xs);
+}
+
 // Initial state: every source asks for an FP64 update with restart.
 __global__ void k_init(RhsState* st, Control* ctl, int* update_list, const double* target2, double delta2,
-                       int max_iter, int defect, int n) {
+                       double margin2, int max_iter, int defect, int n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) {
     RhsState q;
     memset(&q, 0, sizeof(q));
     q.target2 = target2[k];
+    q.conv2 = target2[k] * margin2;
     q.delta2 = delta2;
     q.max_iter = max_iter;
     q.defect = defect;
@@ -793,7 +816,11 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       Prob& p = P[i];
       Workspace& w = *p.w;
       cudaMemcpyAsync(w.scal, p.target2.data(), p.n * sizeof(double), cudaMemcpyHostToDevice, p.s);
-      k_init<<<(p.n + 127) / 128, 128, 0, p.s>>>(w.st, w.ctl, w.update_list, w.scal, delta * delta, prm.max_iter,
+      // the iterated residual of FP16 fields can sit below the true one by
+      // a few tens of percent, FP32 by much less: retire with a margin
+      const double margin = prm.inner_prec == P16 ? 0.5 : prm.inner_prec == P32 ? 0.8 : 1.0;
+      k_init<<<(p.n + 127) / 128, 128, 0, p.s>>>(w.st, w.ctl, w.update_list, w.scal, delta * delta,
+                                                 margin * margin, prm.max_iter,
                                                  prm.outer == SQ_OUTER_DEFECT ? 1 : 0, p.n);
       p.c->launches += 1;
       p.upd(p.c, w, *p.cs, p.kappa, p.s, attempt == 0 && !prm.use_x0);
@@ -907,13 +934,23 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       cudaFreeHost(h_active);
       return cuda_check(c0, e, "inner loop");
     }
-    // per problem: psi_o = A_oo^{-1} (eta_o + k D_oe psi_e), full FP64 residual
+    // per problem: x64 += xs, psi_o = A_oo^{-1} (eta_o + k D_oe psi_e), full
+    // FP64 residual
     bool retry = false;
     for (int i = 0; i < np; i++) {
       Prob& p = P[i];
       sq_ctx* c = p.c;
       Workspace& w = *p.w;
       const int n = p.n;
+      {
+        VArgs f = vargs(c, w, false);
+        f.f0 = w.x64;
+        f.f1 = w.xs;
+        const dim3 fg((c->Vh + 127) / 128, n);
+        if (prm.inner_prec == P64) k_flush<P64><<<fg, 128, 0, sb>>>(f);
+        else k_flush<P32><<<fg, 128, 0, sb>>>(f);
+        c->launches += 1;
+      }
       DslashCall d;
       memset(&d, 0, sizeof(d));
       d.prec = P64;

@@ -23,6 +23,9 @@ struct RhsState {
   double maxr2;    // max iterated ||r||^2 since the last FP64 update
   double rstart2;  // ||r||^2 at the last FP64 update
   double target2;  // stop when the FP64 Schur residual^2 <= target2
+  double conv2;    // retire when the iterated residual^2 <= conv2 (target2
+                   // times a safety margin for the inner precision); the
+                   // full-lattice FP64 residual after the loop confirms it
   double true_r2;  // last FP64 Schur residual norm^2
   double delta2;   // update trigger (squared)
   int iter, updates, restarts, breakdowns;
@@ -119,7 +122,15 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int k, const double*
       q.breakdowns++;
     }
     if (bad) q.want_restart = 1;
-    bool upd = q.want_restart || r2 <= q.target2 || q.iter >= q.max_iter;
+    if (!q.want_restart && r2 <= q.conv2) {
+      // converged on the iterated residual: retire; x is flushed and the
+      // FP64 full-lattice residual is checked after the loop
+      q.active = 0;
+      q.status = 0;
+      q.true_r2 = r2;
+      return;
+    }
+    bool upd = q.want_restart || q.iter >= q.max_iter;
     if (q.defect) {
       if (r2 < q.delta2 * q.rstart2) {
         upd = true;
