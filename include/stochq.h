@@ -98,7 +98,7 @@ typedef struct sq_solve_params {
   double delta;        /* FP64 update when ||r|| < delta * max||r|| since the
                           last update (reliable) or < delta * ||r_start||
                           (defect correction); <= 0 picks the default for
-                          the inner precision (FP32 1e-4, FP16 3e-3);
+                          the inner precision (FP32 3e-6, FP16 3e-3);
                           ignored for SQ_F64                               */
   int max_iter;        /* inner iterations per source (default 20000)      */
   int recon;           /* low-precision links: 12 or 18 (FP16 always 12)   */
