@@ -254,74 +254,194 @@ __device__ void pack_herm(const cx<double> m[36], double o[36]) {
     }
 }
 
-__global__ void k_clover(Geom g, const double2* U64, double kappa, double csw, double2* A64, double2* Ainv64,
-                         float4* Ainv32, uint4* Ainv16, unsigned long long* abound, int* err) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * g.Vh) return;
-  Coord x;
-  x.x = i % g.X;
-  int r = i / g.X;
-  x.y = r % g.Y;
-  r /= g.Y;
-  x.z = r % g.Z;
-  x.t = r / g.Z;
-  const int p = (x.x + x.y + x.z + x.t) & 1;
-  const int cb = i >> 1;
-  // planes: 01 02 03 12 13 23
-  M3 F01 = fhat(g, U64, x, 0, 1), F02 = fhat(g, U64, x, 0, 2), F03 = fhat(g, U64, x, 0, 3);
-  M3 F12 = fhat(g, U64, x, 1, 2), F13 = fhat(g, U64, x, 1, 3), F23 = fhat(g, U64, x, 2, 3);
-  const double kc = kappa * csw;
-  double packA[72], packI[72];
+// Inverse of a packed Hermitian 6x6 block by A = L D L^+ (unit lower L,
+// real D) with fully static indexing, so everything stays in registers:
+// A^{-1}_ij = sum_{k >= max(i,j)} conj(M_ki) M_kj / d_k with M = L^{-1}.
+// Returns false when a pivot is below 5% of the largest diagonal (the block
+// is then not safely positive definite; the caller uses pivoted
+// Gauss-Jordan instead).
+__device__ bool herm6_inverse_ldl(const double a[36], double out[36]) {
+  double d[6], id[6], lr[15], li[15], mr[15], mi[15];
+  double scale = 0;
+#pragma unroll
+  for (int i = 0; i < 6; i++) scale = fmax(scale, fabs(a[i]));
   bool ok = true;
-  double bound = 0;
-  for (int ch = 0; ch < 2; ch++) {
-    const double sg = ch == 0 ? -1.0 : 1.0;
-    // G1 (s1), G2 (s2), G3 (s3) for this chirality
-    M3 G1, G2, G3;
-    for (int e = 0; e < 9; e++) {
-      G1.e[e] = F12.e[e] + sg * F03.e[e];
-      G2.e[e] = F02.e[e] - sg * F13.e[e];
-      G3.e[e] = F01.e[e] + sg * F23.e[e];
-    }
-    // A = 1 + i kc [[G3, G1 - i G2], [G1 + i G2, -G3]]  (spin-major 6x6)
-    cx<double> A[36], Ai[36];
-    for (int a = 0; a < 3; a++)
-      for (int b = 0; b < 3; b++) {
-        cx<double> g1 = G1.e[a * 3 + b], g2 = G2.e[a * 3 + b], g3 = G3.e[a * 3 + b];
-        cx<double> d00 = g3, d01 = g1 - itimes(g2), d10 = g1 + itimes(g2), d11 = mk(-g3.re, -g3.im);
-        A[(0 + a) * 6 + (0 + b)] = kc * itimes(d00);
-        A[(0 + a) * 6 + (3 + b)] = kc * itimes(d01);
-        A[(3 + a) * 6 + (0 + b)] = kc * itimes(d10);
-        A[(3 + a) * 6 + (3 + b)] = kc * itimes(d11);
+#pragma unroll
+  for (int j = 0; j < 6; j++) {
+    double dj = a[j];
+#pragma unroll
+    for (int k = 0; k < j; k++) dj -= (lr[tri(j, k)] * lr[tri(j, k)] + li[tri(j, k)] * li[tri(j, k)]) * d[k];
+    ok = ok && (dj > 0.05 * scale);
+    d[j] = dj;
+    id[j] = 1.0 / dj;
+#pragma unroll
+    for (int i = j + 1; i < 6; i++) {
+      double sr = a[6 + 2 * tri(i, j)], si = a[6 + 2 * tri(i, j) + 1];
+#pragma unroll
+      for (int k = 0; k < j; k++) {  // - L_ik conj(L_jk) d_k
+        const double xr = lr[tri(i, k)], xi = li[tri(i, k)], yr = lr[tri(j, k)], yi = li[tri(j, k)];
+        sr -= (xr * yr + xi * yi) * d[k];
+        si -= (xi * yr - xr * yi) * d[k];
       }
-    for (int d = 0; d < 6; d++) A[d * 6 + d].re += 1.0;
-    for (int a = 0; a < 6; a++) {
-      double rs = 0;
-      for (int b = 0; b < 6; b++) rs += sqrt(A[a * 6 + b].re * A[a * 6 + b].re + A[a * 6 + b].im * A[a * 6 + b].im);
-      bound = fmax(bound, rs);
+      lr[tri(i, j)] = sr * id[j];
+      li[tri(i, j)] = si * id[j];
     }
-    pack_herm(A, packA + 36 * ch);
-    cx<double> work[36];
-    for (int e = 0; e < 36; e++) work[e] = A[e];
-    ok = inv6(work, Ai) && ok;
-    pack_herm(Ai, packI + 36 * ch);
   }
-  if (!ok) atomicOr(err, 2);
+  if (!ok) return false;
+#pragma unroll
+  for (int j = 0; j < 6; j++)
+#pragma unroll
+    for (int i = j + 1; i < 6; i++) {  // M_ij = -(L_ij + sum_{j<k<i} L_ik M_kj)
+      double sr = lr[tri(i, j)], si = li[tri(i, j)];
+#pragma unroll
+      for (int k = j + 1; k < i; k++) {
+        sr += lr[tri(i, k)] * mr[tri(k, j)] - li[tri(i, k)] * mi[tri(k, j)];
+        si += lr[tri(i, k)] * mi[tri(k, j)] + li[tri(i, k)] * mr[tri(k, j)];
+      }
+      mr[tri(i, j)] = -sr;
+      mi[tri(i, j)] = -si;
+    }
+#pragma unroll
+  for (int i = 0; i < 6; i++) {
+    double s = id[i];
+#pragma unroll
+    for (int k = i + 1; k < 6; k++) s += (mr[tri(k, i)] * mr[tri(k, i)] + mi[tri(k, i)] * mi[tri(k, i)]) * id[k];
+    out[i] = s;
+  }
+#pragma unroll
+  for (int i = 1; i < 6; i++)
+#pragma unroll
+    for (int j = 0; j < i; j++) {
+      double sr = mr[tri(i, j)] * id[i], si = mi[tri(i, j)] * id[i];
+#pragma unroll
+      for (int k = i + 1; k < 6; k++) {  // conj(M_ki) M_kj / d_k
+        const double ar = mr[tri(k, i)], ai = mi[tri(k, i)], br = mr[tri(k, j)], bi = mi[tri(k, j)];
+        sr += (ar * br + ai * bi) * id[k];
+        si += (ar * bi - ai * br) * id[k];
+      }
+      out[6 + 2 * tri(i, j)] = sr;
+      out[6 + 2 * tri(i, j) + 1] = si;
+    }
+  return true;
+}
+
+// Clover build, S sites per CTA in two phases.
+// Phase 1, three threads per site: thread q computes the field strengths of
+// two planes and their chirality combinations (q = 0: G3 from F01, F23;
+// q = 1: G2 from F02, F13; q = 2: G1 from F12, F03) into shared memory.
+// Phase 2, two threads per site: chiral block ch forms
+// A = 1 + i kc [[G3, G1 - i G2], [G1 + i G2, -G3]] packed, bounds its norm,
+// inverts it and writes A, A^{-1} (FP64) and the FP32 / FP16 copies.
+constexpr int kCloverSites = 32;
+
+__global__ void __launch_bounds__(3 * kCloverSites) k_clover(Geom g, const double2* U64, double kappa, double csw,
+                                                             double2* A64, double2* Ainv64, float4* Ainv32,
+                                                             uint4* Ainv16, unsigned long long* abound, int* err) {
+  __shared__ M3 sG[kCloverSites][2][3];
+  const int t = threadIdx.x;
+  const int V = 2 * g.Vh;
+  {
+    const int s = t / 3, q = t - 3 * (t / 3);
+    const int i = blockIdx.x * kCloverSites + s;
+    if (i < V) {
+      Coord x;
+      x.x = i % g.X;
+      int r = i / g.X;
+      x.y = r % g.Y;
+      r /= g.Y;
+      x.z = r % g.Z;
+      x.t = r / g.Z;
+      const int ma = q == 0 ? 0 : q == 1 ? 0 : 1, na = q == 0 ? 1 : q == 1 ? 2 : 2;  // F01, F02, F12
+      const int mb = q == 0 ? 2 : q == 1 ? 1 : 0, nb = q == 0 ? 3 : q == 1 ? 3 : 3;  // F23, F13, F03
+      // chirality 0 / 1: G3 = F01 -+ F23, G2 = F02 +- F13, G1 = F12 -+ F03
+      const double sb0 = q == 1 ? 1.0 : -1.0;
+      const M3 Fa = fhat(g, U64, x, ma, na), Fb = fhat(g, U64, x, mb, nb);
+#pragma unroll
+      for (int e = 0; e < 9; e++) {
+        sG[s][0][q].e[e] = Fa.e[e] + sb0 * Fb.e[e];
+        sG[s][1][q].e[e] = Fa.e[e] - sb0 * Fb.e[e];
+      }
+    }
+  }
+  __syncthreads();
+  if (t >= 2 * kCloverSites) return;
+  const int s = t >> 1, ch = t & 1;
+  const int i = blockIdx.x * kCloverSites + s;
+  if (i >= V) return;
+  int xi = i % g.X, r = i / g.X, yi = r % g.Y;
+  r /= g.Y;
+  const int zi = r % g.Z, ti = r / g.Z;
+  const int p = (xi + yi + zi + ti) & 1;
+  const int cb = i >> 1;
+  const double kc = kappa * csw;
+  const M3& G1 = sG[s][ch][2];
+  const M3& G2 = sG[s][ch][1];
+  const M3& G3 = sG[s][ch][0];
+  // element (row, col) of i kc [[G3, G1 - iG2], [G1 + iG2, -G3]]
+  auto elem = [&](int row, int col) -> cx<double> {
+    const int sr = row / 3, a = row % 3, sc = col / 3, b = col % 3;
+    const cx<double> g1 = G1.e[a * 3 + b], g2 = G2.e[a * 3 + b], g3 = G3.e[a * 3 + b];
+    cx<double> d;
+    if (sr == 0 && sc == 0) d = g3;
+    else if (sr == 0) d = g1 - itimes(g2);
+    else if (sc == 0) d = g1 + itimes(g2);
+    else d = mk(-g3.re, -g3.im);
+    return kc * itimes(d);
+  };
+  double pa[36], pi[36];
+#pragma unroll
+  for (int k = 0; k < 6; k++) pa[k] = 1.0 + elem(k, k).re;
+#pragma unroll
+  for (int row = 1; row < 6; row++)
+#pragma unroll
+    for (int col = 0; col < row; col++) {
+      const cx<double> v = elem(row, col);
+      pa[6 + 2 * tri(row, col)] = v.re;
+      pa[6 + 2 * tri(row, col) + 1] = v.im;
+    }
+  // Gershgorin bound on ||A||_2 from the packed Hermitian rows
+  double bound = 0;
+#pragma unroll
+  for (int row = 0; row < 6; row++) {
+    double rs = fabs(pa[row]);
+#pragma unroll
+    for (int col = 0; col < 6; col++) {
+      if (col == row) continue;
+      const int hi = row > col ? row : col, lo = row > col ? col : row;
+      rs += sqrt(pa[6 + 2 * tri(hi, lo)] * pa[6 + 2 * tri(hi, lo)] +
+                 pa[6 + 2 * tri(hi, lo) + 1] * pa[6 + 2 * tri(hi, lo) + 1]);
+    }
+    bound = fmax(bound, rs);
+  }
   atomicMax(abound, (unsigned long long)__double_as_longlong(bound));
-  for (int j = 0; j < 36; j++) {
-    A64[((size_t)p * 36 + j) * g.Vh + cb] = make_double2(packA[2 * j], packA[2 * j + 1]);
-    Ainv64[((size_t)p * 36 + j) * g.Vh + cb] = make_double2(packI[2 * j], packI[2 * j + 1]);
+#pragma unroll
+  for (int m = 0; m < 18; m++) A64[((size_t)p * 36 + 18 * ch + m) * g.Vh + cb] = make_double2(pa[2 * m], pa[2 * m + 1]);
+  if (!herm6_inverse_ldl(pa, pi)) {
+    cx<double> A[36], Ai[36];
+    for (int row = 0; row < 6; row++)
+      for (int col = 0; col < 6; col++) {
+        cx<double> v = elem(row, col);
+        if (row == col) v.re += 1.0;
+        A[row * 6 + col] = v;
+      }
+    if (!inv6(A, Ai)) atomicOr(err, 2);
+    pack_herm(Ai, pi);
   }
-  for (int j = 0; j < 18; j++)
-    Ainv32[((size_t)p * 18 + j) * g.Vh + cb] = make_float4((float)packI[4 * j], (float)packI[4 * j + 1],
-                                                           (float)packI[4 * j + 2], (float)packI[4 * j + 3]);
-  for (int j = 0; j < 9; j++) {
-    uint4 h;
-    h.x = f2h((float)packI[8 * j + 0], (float)packI[8 * j + 1]);
-    h.y = f2h((float)packI[8 * j + 2], (float)packI[8 * j + 3]);
-    h.z = f2h((float)packI[8 * j + 4], (float)packI[8 * j + 5]);
-    h.w = f2h((float)packI[8 * j + 6], (float)packI[8 * j + 7]);
-    Ainv16[((size_t)p * 9 + j) * g.Vh + cb] = h;
+#pragma unroll
+  for (int m = 0; m < 18; m++)
+    Ainv64[((size_t)p * 36 + 18 * ch + m) * g.Vh + cb] = make_double2(pi[2 * m], pi[2 * m + 1]);
+#pragma unroll
+  for (int m = 0; m < 9; m++)
+    Ainv32[((size_t)p * 18 + 9 * ch + m) * g.Vh + cb] =
+        make_float4((float)pi[4 * m], (float)pi[4 * m + 1], (float)pi[4 * m + 2], (float)pi[4 * m + 3]);
+  // FP16: 18 half2 words per block; block 0 = words 0..17, block 1 = 18..35
+  // of the site's 36 words (4 words per uint4 chunk)
+  uint32_t* w16 = (uint32_t*)Ainv16;
+#pragma unroll
+  for (int m = 0; m < 18; m++) {
+    const int word = 18 * ch + m;
+    const size_t chunk = (size_t)p * 9 + (word >> 2);
+    w16[(chunk * g.Vh + cb) * 4 + (word & 3)] = f2h((float)pi[2 * m], (float)pi[2 * m + 1]);
   }
 }
 
@@ -331,8 +451,8 @@ sq_status clover_build(sq_ctx* c, CloverSet& cs, double kappa, double csw) {
   cudaError_t e = cudaMallocAsync((void**)&d_bound, sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess) return cuda_check(c, e, "clover bound alloc");
   cudaMemsetAsync(d_bound, 0, sizeof(unsigned long long), c->stream);
-  k_clover<<<(2 * c->Vh + 127) / 128, 128, 0, c->stream>>>(g, c->U64, kappa, csw, cs.A64, cs.Ainv64, cs.Ainv32,
-                                                          cs.Ainv16, d_bound, c->d_err);
+  k_clover<<<(2 * c->Vh + kCloverSites - 1) / kCloverSites, 3 * kCloverSites, 0, c->stream>>>(
+      g, c->U64, kappa, csw, cs.A64, cs.Ainv64, cs.Ainv32, cs.Ainv16, d_bound, c->d_err);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(c, e, "clover launch");
   unsigned long long hb = 0;
