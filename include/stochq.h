@@ -112,7 +112,9 @@ typedef struct sq_solve_params {
   int verbose;         /* 1: progress lines on stderr                      */
   int profile;         /* 1: time every kernel of the inner loop with CUDA
                           events on the context's stream (event nodes in
-                          the captured graph); read with sq_get_profile    */
+                          the captured graph); 2: time only the two clover
+                          dslash launches per iteration (fewer event
+                          nodes); read with sq_get_profile                 */
 } sq_solve_params;
 
 typedef struct sq_solve_stats {

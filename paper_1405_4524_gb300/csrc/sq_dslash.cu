@@ -181,9 +181,9 @@ __device__ __forceinline__ void dslash_body(const KArgs& a) {
   const int k = slot < cnt ? (a.list ? a.list[slot] : slot) : -1;
   const int cb = sb * blockDim.x + threadIdx.x;
   const bool ok = (k >= 0) && (cb < a.g.Vh);
-  double red[NRED];
+  R red[NRED];  // FP64 fields reduce in FP64, FP32 / FP16 in FP32 per warp
 #pragma unroll
-  for (int i = 0; i < NRED; i++) red[i] = 0.0;
+  for (int i = 0; i < NRED; i++) red[i] = (R)0;
   if (ok) {
     cx<R> acc[12];
 #pragma unroll
@@ -242,7 +242,10 @@ __device__ __forceinline__ void dslash_body(const KArgs& a) {
       red[0] = tt;
     }
   }
-  if (FIN != FIN_NONE) reduce_finalize<NRED, FIN>(a.ra, red, k, a.nsb, sb);
+  if (FIN == FIN_ALPHA || FIN == FIN_OMEGA)
+    warp_partials<NRED>(a.ra, red, k, sb * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5));
+  else if (FIN != FIN_NONE)
+    reduce_finalize<NRED, FIN>(a.ra, red, k, a.nsb, sb);
 }
 
 template <int P, int RECON, int CLOV, int XPAY, int FIN>
@@ -322,6 +325,16 @@ void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s) {
     ok = dispatch_mode<P16, 12>(d, a, grid, block, s);
   }
   if (!ok) fprintf(stderr, "libstochq: internal error: no dslash variant for this call\n");
+  if (d.fin == FIN_ALPHA || d.fin == FIN_OMEGA) {  // per-source sums and scalars
+    const int nparts = a.nsb * (int)(block.x >> 5);
+    if (d.prec == P64) {
+      if (d.fin == FIN_ALPHA) k_finish<double, 2, FIN_ALPHA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
+      else k_finish<double, 3, FIN_OMEGA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
+    } else {
+      if (d.fin == FIN_ALPHA) k_finish<float, 2, FIN_ALPHA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
+      else k_finish<float, 3, FIN_OMEGA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
+    }
+  }
 }
 
 // Pick (sites, sources) per CTA by timing the candidates on the call's own

@@ -29,6 +29,9 @@
 namespace sq {
 
 static const Shape kBlasShape = {128, 2, 0};
+// kernels per inner iteration: one per class plus the three k_finish
+// launches (after the two fused dslash reductions and the x, r update)
+static const int kIterLaunches = KC_N + 3;
 // FP64 dslash: ~146 registers per thread; 64-thread CTAs keep 7 per SM resident
 static const Shape k64Shape = {64, 1, 0};
 
@@ -75,7 +78,7 @@ __global__ void __launch_bounds__(256) k_xr_update(const VArgs a) {
   typedef typename Real<P>::T R;
   typedef typename Real<PX>::T RX;
   SLOT_PROLOGUE
-  double red[3] = {0.0, 0.0, 0.0};
+  R red[3] = {(R)0, (R)0, (R)0};
   if (ok) {
     const RhsState& q = a.st[k];
     const R ar = (R)q.alpha_re, ai = (R)q.alpha_im, wr = (R)q.omega_re, wi = (R)q.omega_im;
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(256) k_xr_update(const VArgs a) {
     red[1] = dr;
     red[2] = di;
   }
-  reduce_finalize<3, FIN_ITER>(a.ra, red, k, (int)gridDim.x, (int)blockIdx.x);
+  warp_partials<3>(a.ra, red, k, (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)));
 }
 
 // p = r + beta (p - omega v)     f0 = r, f1 = p, f2 = v
@@ -162,7 +165,7 @@ template <int P>
 __global__ void __launch_bounds__(256) k_rel_r(const VArgs a) {
   typedef typename Real<P>::T R;
   SLOT_PROLOGUE
-  double red[2] = {0.0, 0.0};
+  R red[2] = {(R)0, (R)0};
   if (ok) {
     const bool restart = a.st[k].want_restart != 0;
     cx<double> r64[12];
@@ -353,7 +356,9 @@ static sq_status alloc_ws(sq_ctx* c, Workspace& w, int n, int inner) {
   const int Vh = c->Vh;
   const size_t f64 = field_bytes(Vh, P64, n), fin = field_bytes(Vh, inner, n);
   const size_t fx = field_bytes(Vh, px_of(inner), n);
-  const int nblk = (Vh + 31) / 32;
+  // per source: one partial per warp of the widest launch (sites / 32,
+  // rounded up per CTA of up to 32 warps)
+  const int nblk = (Vh + 31) / 32 + 32;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   size_t tot = 0;
   size_t o_f64 = tot; tot += al(f64) * 7;
@@ -425,19 +430,32 @@ static VArgs vargs(const sq_ctx* c, const Workspace& w, bool update_list) {
 // a stream capture the records become event-record graph nodes.
 struct Marks {
   cudaEvent_t* ev = nullptr;  // KC_N + 1 events for this iteration
+  unsigned mask = 0;          // marks that record (mark kc opens class kc)
   bool capture = false;
   int i = 0;
   void mark(cudaStream_t s) {
     if (!ev) return;
-    if (capture) cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
-    else cudaEventRecord(ev[i], s);
+    if ((mask >> i) & 1u) {
+      if (capture) cudaEventRecordWithFlags(ev[i], s, cudaEventRecordExternal);
+      else cudaEventRecord(ev[i], s);
+    }
     i++;
   }
 };
 
+// profile = 1: every class; profile = 2: the two clover dslash launches
+// only (four event nodes per iteration instead of fourteen)
+static unsigned profile_mask(int profile) {
+  if (profile == 2)
+    return (1u << KC_DSLASH_CLOVER) | (1u << (KC_DSLASH_CLOVER + 1)) | (1u << KC_DSLASH_CLOVER_2) |
+           (1u << (KC_DSLASH_CLOVER_2 + 1));
+  return (1u << (KC_N + 1)) - 1u;
+}
+
 template <int P, int PX>
 static void launch_iteration(sq_ctx* c, Workspace& w, const CloverSet& cs, double kappa, Shape sh, cudaStream_t s,
                              Marks m, int it, int chunk) {
+  typedef typename Real<P>::T R;
   const int n = w.n_rhs;
   dim3 bb(kBlasShape.sx, kBlasShape.ry);
   dim3 bg((c->Vh + kBlasShape.sx - 1) / kBlasShape.sx, (n + kBlasShape.ry - 1) / kBlasShape.ry);
@@ -474,6 +492,7 @@ static void launch_iteration(sq_ctx* c, Workspace& w, const CloverSet& cs, doubl
   m.mark(s);
   a.f0 = w.xs; a.f1 = w.p; a.f2 = w.s; a.f3 = w.t; a.f4 = w.r; a.f5 = w.rh;
   k_xr_update<P, PX><<<bg, bb, 0, s>>>(a);
+  k_finish<R, 3, FIN_ITER><<<n, 256, 0, s>>>(a.ra, w.active_list, &w.ctl->n_active, n, (int)bg.x * (kBlasShape.sx / 32));
   m.mark(s);
   a.f0 = w.r; a.f1 = w.p; a.f2 = w.v;
   k_p_update<P><<<bg, bb, 0, s>>>(a);
@@ -779,6 +798,7 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
                               std::vector<cudaEvent_t>& evs, sq_status* result) {
   const int np = (int)P.size();
   const bool prof = prm.profile != 0 && np == 1;
+  const unsigned pmask = profile_mask(prm.profile);
   const int chunk = prm.chunk;
   const double delta = prm.inner_prec == P64 ? 0.0 : prm.delta;
   sq_ctx* c0 = P[0].c;
@@ -831,7 +851,8 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
     }
     // the graph key holds everything baked into the captured kernels
     std::vector<unsigned long long> key = {(unsigned long long)np, (unsigned long long)prm.inner_prec,
-                                           (unsigned long long)chunk, (unsigned long long)prof};
+                                           (unsigned long long)chunk, (unsigned long long)prof,
+                                           (unsigned long long)prm.profile};
     for (auto& p : P) {
       unsigned long long kb;
       memcpy(&kb, &p.kappa, sizeof(kb));
@@ -861,6 +882,7 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
           Marks m;
           if (prof) {
             m.ev = &p.w->pev[(size_t)it * (KC_N + 1)];
+            m.mask = pmask;
             m.capture = capture;
           }
           p.iter(p.c, *p.w, *p.cs, p.kappa, p.sh, ps, m, it, chunk);
@@ -901,7 +923,7 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
         e = cudaGetLastError();
       }
       if (e != cudaSuccess) break;
-      for (auto& p : P) p.c->launches += (long long)chunk * KC_N;
+      for (auto& p : P) p.c->launches += (long long)chunk * kIterLaunches;
       launched += chunk;
       for (int i = 0; i < np; i++)
         cudaMemcpyAsync(h_active + i, &P[i].w->ctl->n_active, sizeof(int), cudaMemcpyDeviceToHost, sb);
@@ -913,6 +935,7 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
         for (int i = 0; i < chunk; i++) {
           const double na = h_active[np + i], nu = h_active[np + chunk + i];
           for (int kc = 0; kc < KC_N; kc++) {
+            if (!((pmask >> kc) & 1u) || !((pmask >> (kc + 1)) & 1u)) continue;
             float ms = 0;
             cudaEventElapsedTime(&ms, w.pev[(size_t)i * (KC_N + 1) + kc], w.pev[(size_t)i * (KC_N + 1) + kc + 1]);
             Cost cost = class_cost(kc, prm.inner_prec, P[0].recon_in, (double)P[0].c->Vh, na, nu);

@@ -171,40 +171,27 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int k, const double*
   }
 }
 
-// Block-level reduction of NRED doubles per source slot (threadIdx.y) over
-// the sites of the block (threadIdx.x; blockDim.x is a multiple of 32), then
-// across the nblk site blocks of the launch through `partial` (this block is
-// site block bidx): the last block of a source (per-source arrival counter)
-// sums the per-block partials in block order and runs the finaliser. The
-// summation order is fixed for a fixed launch shape, so the result is
-// bitwise reproducible. Every thread of the block must call this.
+// Second half of every reduction: thread x = 0 of slot ty holds the block's
+// NRED sums for source k (k < 0: idle slot). They go to `partial` (this is
+// site block bidx of nblk); the last block of a source (per-source arrival
+// counter) sums the per-block partials in block order in FP64 and runs the
+// finaliser. The summation order is fixed for a fixed launch shape, so the
+// result is bitwise reproducible. Every thread of the block must call this.
 template <int NRED, int FIN>
-__device__ __forceinline__ void reduce_finalize(const RedArgs& ra, double v[NRED], int k, int nblk, int bidx) {
+__device__ __forceinline__ void reduce_across_blocks(const RedArgs& ra, const double blk[NRED], int k, int nblk,
+                                                     int bidx) {
   __shared__ double sm[32][NRED];  // one row per warp
   __shared__ int last[32];         // per slot: this block finishes source k
   const int lane = threadIdx.x & 31;
   const int wx = threadIdx.x >> 5;
   const int nwx = blockDim.x >> 5;
   const int ty = threadIdx.y;
-#pragma unroll
-  for (int i = 0; i < NRED; i++) v[i] = warp_sum(v[i]);
-  if (lane == 0) {
-#pragma unroll
-    for (int i = 0; i < NRED; i++) sm[ty * nwx + wx][i] = v[i];
-  }
-  __syncthreads();
   if (threadIdx.x == 0) {
     int is_last = 0;
     if (k >= 0) {
-      double acc[NRED];
-#pragma unroll
-      for (int i = 0; i < NRED; i++) acc[i] = 0.0;
-      for (int w = 0; w < nwx; w++)
-#pragma unroll
-        for (int i = 0; i < NRED; i++) acc[i] += sm[ty * nwx + w][i];
       double* dst = ra.partial + ((size_t)k * ra.nblk_stride + bidx) * NRED;
 #pragma unroll
-      for (int i = 0; i < NRED; i++) dst[i] = acc[i];
+      for (int i = 0; i < NRED; i++) dst[i] = blk[i];
       __threadfence();
       unsigned prev = atomicAdd(ra.counter + k, 1u);
       is_last = (prev == (unsigned)nblk - 1u);
@@ -223,8 +210,6 @@ __device__ __forceinline__ void reduce_finalize(const RedArgs& ra, double v[NRED
       for (int i = 0; i < NRED; i++) acc[i] += __ldcg(src + (size_t)b * NRED + i);
 #pragma unroll
     for (int i = 0; i < NRED; i++) acc[i] = warp_sum(acc[i]);
-    // second level inside this slot's warps: reuse sm rows of this slot
-    __syncwarp();
     if (lane == 0) {
 #pragma unroll
       for (int i = 0; i < NRED; i++) sm[ty * nwx + wx][i] = acc[i];
@@ -245,6 +230,113 @@ __device__ __forceinline__ void reduce_finalize(const RedArgs& ra, double v[NRED
       finalize<FIN>(ra, k, tot);
     }
     ra.counter[k] = 0u;
+  }
+}
+
+// Block-level reduction of NRED doubles per source slot (threadIdx.y) over
+// the sites of the block (threadIdx.x; blockDim.x is a multiple of 32),
+// then across blocks (reduce_across_blocks). Used by the FP64 update path
+// and the norms; the inner iteration uses warp_partials + k_finish.
+template <int NRED, int FIN>
+__device__ __forceinline__ void reduce_finalize(const RedArgs& ra, double v[NRED], int k, int nblk, int bidx) {
+  __shared__ double sm[32][NRED];
+  const int lane = threadIdx.x & 31;
+  const int wx = threadIdx.x >> 5;
+  const int nwx = blockDim.x >> 5;
+  const int ty = threadIdx.y;
+#pragma unroll
+  for (int i = 0; i < NRED; i++) v[i] = warp_sum(v[i]);
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < NRED; i++) sm[ty * nwx + wx][i] = v[i];
+  }
+  __syncthreads();
+  double blk[NRED];
+#pragma unroll
+  for (int i = 0; i < NRED; i++) blk[i] = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < nwx; w++)
+#pragma unroll
+      for (int i = 0; i < NRED; i++) blk[i] += sm[ty * nwx + w][i];
+  reduce_across_blocks<NRED, FIN>(ra, blk, k, nblk, bidx);
+}
+
+// FP32 per-thread values on the same path (the FP64 update path's
+// reductions of FP32 fields): summed in FP64 from the warp level up.
+template <int NRED, int FIN>
+__device__ __forceinline__ void reduce_finalize(const RedArgs& ra, float v[NRED], int k, int nblk, int bidx) {
+  double d[NRED];
+#pragma unroll
+  for (int i = 0; i < NRED; i++) d[i] = (double)v[i];
+  reduce_finalize<NRED, FIN>(ra, d, k, nblk, bidx);
+}
+
+// Per-warp partial sums for the reductions of the inner iteration (no
+// cross-block synchronisation in the producing kernel): warp j of source k
+// writes its NRED sums to partial[(k * nblk_stride + j) * NRED + i], and
+// k_finish adds them up per source in a fixed order in FP64 and runs the
+// finaliser. A fence-and-counter "last block" scheme here made every CTA
+// wait for its own output stores; the kernel boundary orders them for free.
+// FP32 values (FP32 / FP16 fields) are summed across the warp in FP32 and
+// stored as float (they are sums of FP32 products already); FP64 in FP64.
+// All 32 lanes of the warp must call this.
+template <int NRED>
+__device__ __forceinline__ void warp_partials(const RedArgs& ra, float v[NRED], int k, int j) {
+#pragma unroll
+  for (int i = 0; i < NRED; i++)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  if ((threadIdx.x & 31) == 0 && k >= 0) {
+    float* dst = (float*)ra.partial + ((size_t)k * ra.nblk_stride + j) * NRED;
+#pragma unroll
+    for (int i = 0; i < NRED; i++) dst[i] = v[i];
+  }
+}
+
+template <int NRED>
+__device__ __forceinline__ void warp_partials(const RedArgs& ra, double v[NRED], int k, int j) {
+#pragma unroll
+  for (int i = 0; i < NRED; i++) v[i] = warp_sum(v[i]);
+  if ((threadIdx.x & 31) == 0 && k >= 0) {
+    double* dst = ra.partial + ((size_t)k * ra.nblk_stride + j) * NRED;
+#pragma unroll
+    for (int i = 0; i < NRED; i++) dst[i] = v[i];
+  }
+}
+
+// One CTA per source slot: sum the nparts per-warp partials of source k in
+// FP64 (fixed thread assignment and tree: bitwise reproducible for a fixed
+// launch shape) and run the finaliser. T is the partials' type.
+template <typename T, int NRED, int FIN>
+__global__ void __launch_bounds__(256) k_finish(const RedArgs ra, const int* list, const int* count, int n,
+                                                int nparts) {
+  __shared__ double sm[8][NRED];
+  const int cnt = count ? *count : n;
+  const int slot = blockIdx.x;
+  if (slot >= cnt) return;
+  const int k = list ? list[slot] : slot;
+  const T* src = (const T*)ra.partial + (size_t)k * ra.nblk_stride * NRED;
+  double acc[NRED];
+#pragma unroll
+  for (int i = 0; i < NRED; i++) acc[i] = 0.0;
+  for (int j = threadIdx.x; j < nparts; j += blockDim.x)
+#pragma unroll
+    for (int i = 0; i < NRED; i++) acc[i] += (double)src[(size_t)j * NRED + i];
+#pragma unroll
+  for (int i = 0; i < NRED; i++) acc[i] = warp_sum(acc[i]);
+  const int wx = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < NRED; i++) sm[wx][i] = acc[i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot[NRED];
+#pragma unroll
+    for (int i = 0; i < NRED; i++) tot[i] = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++)
+#pragma unroll
+      for (int i = 0; i < NRED; i++) tot[i] += sm[w][i];
+    finalize<FIN>(ra, k, tot);
   }
 }
 
