@@ -115,6 +115,15 @@ typedef struct sq_solve_params {
                           the captured graph); 2: time only the two clover
                           dslash launches per iteration (fewer event
                           nodes); read with sq_get_profile                 */
+  double *pion;        /* optional fused epilogue (NULL: none): the pion
+                          correlator of every solution, exactly as
+                          sq_contract_pion computes it, written to
+                          pion[n_rhs][T] in host or device memory per io.
+                          On the device it runs from the solutions while
+                          the final FP64 residual check is in flight.
+                          Ignored by sq_solve_batch.                       */
+  const int *pion_tslice; /* [n_rhs] source time slices for pion, same
+                          memory kind as pion; NULL: all 0                  */
 } sq_solve_params;
 
 typedef struct sq_solve_stats {

@@ -56,6 +56,12 @@ struct Workspace {
   int* update_list = nullptr;
   double* scal = nullptr;       // n_rhs * 4 doubles of scratch results
   int nblk_stride = 0;
+  // solution output: unpack, copy-out and pion epilogue run on `aux`,
+  // overlapped with the FP64 residual check on the solve stream
+  double* pion = nullptr;       // n_rhs * T correlator (device)
+  int* tsl = nullptr;           // n_rhs source time slices (device)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_rec = nullptr, ev_out = nullptr;
   // cached graph of `chunk` iterations, keyed by everything baked into it
   cudaGraphExec_t graph = nullptr;
   std::vector<unsigned long long> graph_key;

@@ -327,6 +327,12 @@ __global__ void k_init(RhsState* st, Control* ctl, int* update_list, const doubl
 static inline int px_of(int inner) { return inner == P64 ? P64 : P32; }
 
 static void free_ws(Workspace& w) {
+  if (w.aux) {
+    cudaStreamSynchronize(w.aux);
+    cudaStreamDestroy(w.aux);
+  }
+  if (w.ev_rec) cudaEventDestroy(w.ev_rec);
+  if (w.ev_out) cudaEventDestroy(w.ev_out);
   if (w.graph) cudaGraphExecDestroy(w.graph);
   for (auto e : w.pev) cudaEventDestroy(e);
   if (w.hist) cudaFree(w.hist);
@@ -372,6 +378,8 @@ static sq_status alloc_ws(sq_ctx* c, Workspace& w, int n, int inner) {
   size_t o_al = tot; tot += al((size_t)n * sizeof(int));
   size_t o_ul = tot; tot += al((size_t)n * sizeof(int));
   size_t o_sc = tot; tot += al((size_t)n * 8 * sizeof(double));
+  size_t o_pi = tot; tot += al((size_t)n * c->dims[3] * sizeof(double));
+  size_t o_ts = tot; tot += al((size_t)n * sizeof(int));
   void* base = nullptr;
   cudaError_t e = cudaMalloc(&base, tot);
   if (e != cudaSuccess) {
@@ -397,7 +405,13 @@ static sq_status alloc_ws(sq_ctx* c, Workspace& w, int n, int inner) {
   w.active_list = (int*)(b + o_al);
   w.update_list = (int*)(b + o_ul);
   w.scal = (double*)(b + o_sc);
+  w.pion = (double*)(b + o_pi);
+  w.tsl = (int*)(b + o_ts);
   w.nblk_stride = nblk;
+  e = cudaStreamCreateWithFlags(&w.aux, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev_rec, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev_out, cudaEventDisableTiming);
+  if (e != cudaSuccess) return cuda_check(c, e, "workspace stream");
   e = cudaMemset(w.counter, 0, (size_t)n * sizeof(unsigned));
   return cuda_check(c, e, "workspace counters");
 }
@@ -701,6 +715,8 @@ static sq_status setup_problem(Prob& p, const sq_solve_params& prm) {
   if (prm.io == SQ_HOST) {
     cudaMemcpyAsync(w.lex, p.src, lex_doubles * sizeof(double), cudaMemcpyHostToDevice, s);
     dsrc = w.lex;
+    if (prm.pion && prm.pion_tslice)
+      cudaMemcpyAsync(w.tsl, prm.pion_tslice, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s);
   }
   // the context stream is used by check_finite; order it after this stream
   cudaEvent_t ev;
@@ -786,6 +802,28 @@ static sq_status setup_problem(Prob& p, const sq_solve_params& prm) {
   p.recon_in = inner == P64 ? 18 : (inner == P16 ? 12 : c->recon);
   fns_for(inner, &p.iter, &p.upd);
   return SQ_OK;
+}
+
+// Solutions from the even-odd FP64 fields to the caller's lexicographic
+// layout (through the staging buffer and one copy for host I/O), and the
+// optional pion epilogue on the device solutions, all on stream s.
+static void output_solutions(Prob& p, const sq_solve_params& prm, cudaStream_t s) {
+  sq_ctx* c = p.c;
+  Workspace& w = *p.w;
+  double* dsol = prm.io == SQ_HOST ? w.lex : p.sol;
+  launch_unpack(c, dsol, w.x64, 0, P64, p.n, s);
+  launch_unpack(c, dsol, w.x64o, 1, P64, p.n, s);
+  c->launches += 2;
+  if (prm.pion) {
+    double* dC = prm.io == SQ_HOST ? w.pion : prm.pion;
+    const int* dt = prm.pion_tslice ? (prm.io == SQ_HOST ? w.tsl : prm.pion_tslice) : nullptr;
+    launch_pion(c, dsol, p.n, dt, dC, s);
+    c->launches += 1;
+    if (prm.io == SQ_HOST)
+      cudaMemcpyAsync(prm.pion, w.pion, (size_t)p.n * c->dims[3] * sizeof(double), cudaMemcpyDeviceToHost, s);
+  }
+  if (prm.io == SQ_HOST)
+    cudaMemcpyAsync(p.sol, w.lex, (size_t)p.n * c->V * 24 * sizeof(double), cudaMemcpyDeviceToHost, s);
 }
 
 // The iteration loop of all problems: each problem's `chunk` iterations are
@@ -987,6 +1025,12 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       Field none = make_field(nullptr, c->Vh, P64, n);
       launch_clover64(c, *p.cs, w.x64o, none, w.t64o, 1, 0.0, 1.0, 1, n, sb);
       c->launches += 2;
+      // solutions out (and the pion epilogue) on the side stream while the
+      // FP64 check runs; a failed check redoes them after the next pass
+      cudaEventRecord(w.ev_rec, sb);
+      cudaStreamWaitEvent(w.aux, w.ev_rec, 0);
+      output_solutions(p, prm, w.aux);
+      cudaEventRecord(w.ev_out, w.aux);
       launch_full_residual(c, w, *p.cs, p.kappa, sb);
       std::vector<double> res2(2 * n);
       cudaMemcpyAsync(res2.data(), w.scal, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, sb);
@@ -1023,7 +1067,9 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
     if (!retry) break;
     *result = SQ_OK;
     if (prm.verbose) fprintf(stderr, "libstochq: tightening the Schur target\n");
-    // the next pass continues from the current x (even sites in x64)
+    // the next pass continues from the current x (even sites in x64); it
+    // rewrites x64 / x64o, so it waits for the output copies of this one
+    for (auto& p : P) cudaStreamWaitEvent(sb, p.w->ev_out, 0);
     for (auto& p : P)
       if (p.s != sb) {
         cudaEventRecord(evs[0], sb);
@@ -1031,18 +1077,10 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       }
   }
   cudaFreeHost(h_active);
-  // solutions out
   for (auto& p : P) {
-    sq_ctx* c = p.c;
-    Workspace& w = *p.w;
-    double* dsol = prm.io == SQ_HOST ? w.lex : p.sol;
-    launch_unpack(c, dsol, w.x64, 0, P64, p.n, sb);
-    launch_unpack(c, dsol, w.x64o, 1, P64, p.n, sb);
-    c->launches += 2;
-    if (prm.io == SQ_HOST)
-      cudaMemcpyAsync(p.sol, w.lex, (size_t)p.n * c->V * 24 * sizeof(double), cudaMemcpyDeviceToHost, sb);
+    e = cudaStreamSynchronize(p.w->aux);
+    if (e != cudaSuccess) break;
   }
-  e = cudaStreamSynchronize(sb);
   return cuda_check(c0, e, "solution copy");
 }
 
@@ -1094,6 +1132,8 @@ sq_status solve_batch_impl(const sq_problem* probs, int np, const sq_solve_param
   else sq_default_params(&prm);
   sq_status st = validate_params(c0, prm);
   if (st != SQ_OK) return st;
+  prm.pion = nullptr;  // the pion epilogue is a single-problem option
+  prm.pion_tslice = nullptr;
   if (!c0->batch) c0->batch = new BatchCache();
   BatchCache& B = *c0->batch;
   while ((int)B.ws.size() < np) B.ws.push_back(new Workspace());

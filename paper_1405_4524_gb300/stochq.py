@@ -38,7 +38,7 @@ class sq_solve_params(C.Structure):
         ("max_iter", C.c_int), ("recon", C.c_int), ("sites_per_block", C.c_int),
         ("rhs_per_block", C.c_int), ("chunk", C.c_int), ("use_graph", C.c_int),
         ("io", C.c_int), ("use_x0", C.c_int), ("verbose", C.c_int),
-        ("profile", C.c_int),
+        ("profile", C.c_int), ("pion", C.c_void_p), ("pion_tslice", C.c_void_p),
     ]
 
 
@@ -247,8 +247,11 @@ def sq_apply_M(ctx, out, inp, n_rhs: int, kappa: float, c_sw: float) -> None:
 
 
 def sq_solve(ctx, kappa: float, c_sw: float, sources, solutions, n_rhs: int, tol: float,
-             params: sq_solve_params | None = None, raise_on_error: bool = True):
-    """Returns (status, list of per-source stats dicts)."""
+             params: sq_solve_params | None = None, raise_on_error: bool = True,
+             pion=None, pion_tslice=None):
+    """Returns (status, list of per-source stats dicts). pion: optional
+    (n_rhs, T) float64 output of the fused pion epilogue (same memory kind
+    as the sources); pion_tslice: optional (n_rhs,) int32 time slices."""
     if params is None:
         params = sq_default_params()
     params = sq_solve_params.from_buffer_copy(params)
@@ -256,6 +259,25 @@ def sq_solve(ctx, kappa: float, c_sw: float, sources, solutions, n_rhs: int, tol
     if isinstance(sources, np.ndarray):
         _host_c128(sources, "sources")
         _host_c128(solutions, "solutions")
+    keep = []
+    if pion is not None:
+        if _where(pion) != params.io:
+            raise ValueError("pion must live where the sources live")
+        if isinstance(pion, np.ndarray) and (pion.dtype != np.float64 or not pion.flags.c_contiguous):
+            raise ValueError("pion must be a C-contiguous float64 array")
+        shp = getattr(sources, "shape", None)
+        if shp is not None and len(shp) == 7 and tuple(pion.shape) != (int(n_rhs), int(shp[1])):
+            raise ValueError("pion must have shape (n_rhs, T)")
+        params.pion = _ptr(pion)
+        if pion_tslice is not None:
+            if isinstance(pion_tslice, np.ndarray) or isinstance(pion_tslice, (list, tuple)):
+                if params.io != SQ_HOST:
+                    raise ValueError("pion_tslice must live where the sources live")
+                pion_tslice = np.ascontiguousarray(pion_tslice, dtype=np.int32)
+            if len(pion_tslice) != int(n_rhs):
+                raise ValueError("pion_tslice must have n_rhs entries")
+            keep.append(pion_tslice)
+            params.pion_tslice = _ptr(pion_tslice)
     stats = (sq_solve_stats * int(n_rhs))()
     st = _lib.sq_solve(ctx, float(kappa), float(c_sw), _ptr(sources), _ptr(solutions), int(n_rhs),
                        float(tol), C.byref(params), stats)

@@ -118,6 +118,36 @@ def test_pion_contraction(small):
         assert np.allclose(C[k], want, rtol=1e-14, atol=0)
 
 
+def test_fused_pion_epilogue(small):
+    """sq_solve's pion output equals sq_contract_pion on the returned
+    solutions (same kernel, same data) and the oracle's correlator, for
+    host and device I/O, with and without time slices."""
+    import torch
+
+    s, spec, eta, ref = small
+    sq = s.sq
+    n, T = eta.shape[0], spec["dims"][3]
+    ts = np.array([0, 3, 7, 5], dtype=np.int32)
+    sol = np.zeros_like(eta)
+    C = np.full((n, T), np.nan)
+    sq.sq_solve(s.ctx, spec["kappa"], spec["csw"], eta, sol, n, 1e-10, pion=C, pion_tslice=ts)
+    assert np.array_equal(C, sq.sq_contract_pion(s.ctx, sol, n, list(ts)))
+    for k in range(n):
+        assert rel(sol[k], ref[k]) <= 1e-9
+        assert np.allclose(C[k], oracle.pion_correlator(sol[k], int(ts[k])), rtol=1e-13, atol=0)
+    src = torch.from_numpy(eta).cuda()
+    sold = torch.zeros_like(src)
+    Cd = torch.full((n, T), float("nan"), dtype=torch.float64, device="cuda")
+    sq.sq_solve(s.ctx, spec["kappa"], spec["csw"], src, sold, n, 1e-10, pion=Cd)
+    assert np.array_equal(Cd.cpu().numpy(), sq.sq_contract_pion(s.ctx, sold.cpu().numpy(), n))
+    Cd.fill_(float("nan"))
+    sq.sq_solve(s.ctx, spec["kappa"], spec["csw"], src, sold, n, 1e-10, pion=Cd,
+                pion_tslice=torch.from_numpy(ts).cuda())
+    assert np.array_equal(Cd.cpu().numpy(), C)
+    with pytest.raises(ValueError):
+        sq.sq_solve(s.ctx, spec["kappa"], spec["csw"], eta, sol, n, 1e-10, pion=np.zeros((n, T + 1)))
+
+
 def test_time_diluted_sources():
     dims = (4, 4, 4, 8)
     s = Setup(dims, 0.25, 1003)
