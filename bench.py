@@ -135,6 +135,14 @@ class Clocks:
                                        "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+            return
+        # let the sampler finish starting up (its first query) before the
+        # timed region begins
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and self.p.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
 
     def stop(self):
         if not self.p:
@@ -366,7 +374,9 @@ def main():
         wall = time.perf_counter() - w0
         barrier()
         launches = sq.sq_kernel_launches(ctx) - l0
-        ms = reduce_max(sum(a.elapsed_time(b) for a, b in ev) / k, world)
+        per = [a.elapsed_time(b) for a, b in ev]
+        last["step_ms"] = per
+        ms = reduce_max(sum(per) / k, world)
         return ms, wall, launches, agg
 
     for _ in range(max(3, args.warmup)):
@@ -376,6 +386,7 @@ def main():
     ms, wall, launches, agg = timed(step_device, args.steps, prof=True)
     clk = clocks.stop()
     stats = last["stats"]
+    step_ms = last["step_ms"]
     assert all(s["status"] == 0 and s["true_residual"] <= TOL for s in stats), stats
     value = job_throughput(n, world, ms)
 
@@ -442,6 +453,8 @@ def main():
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms, 3),
+        "step_ms_min_median_max": [round(min(step_ms), 3), round(statistics.median(step_ms), 3),
+                                   round(max(step_ms), 3)],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"f32": "f32", "f16": "f16", "f64": "f64"}[args.inner], "data": "synthetic",
         "config": {"workload": args.workload, "lattice": "x".join(map(str, dims)), "t_bc": "antiperiodic",

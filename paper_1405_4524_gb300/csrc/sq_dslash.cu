@@ -162,11 +162,8 @@ __device__ __forceinline__ void hop_dir(const KArgs& a, int k, int cb, Coord c,
   }
 }
 
-template <int P, int RECON, int CLOV, int XPAY, int FIN>
-__device__ __forceinline__ void dslash_body(const KArgs& a) {
-  typedef typename Real<P>::T R;
-  constexpr int NRED = FIN == FIN_ALPHA ? 2 : FIN == FIN_OMEGA ? 3 : 1;
-  int sb, rb;
+// CTA coordinates of the flattened grid: site block sb, slot block rb
+__device__ __forceinline__ void cta_blocks(const KArgs& a, int& sb, int& rb) {
   if (a.order == 0) {
     sb = blockIdx.x / a.nrb;
     rb = blockIdx.x - sb * a.nrb;
@@ -174,12 +171,17 @@ __device__ __forceinline__ void dslash_body(const KArgs& a) {
     rb = blockIdx.x / a.nsb;
     sb = blockIdx.x - rb * a.nsb;
   }
-  const int cnt = a.list ? *a.count : a.n;
-  const int slot0 = rb * blockDim.y;
-  if (slot0 >= cnt) return;  // whole CTA idle (uniform)
+}
+
+// One pass over source slots slot0 .. slot0 + blockDim.y - 1 for the sites
+// of site block sb. Every thread of the CTA calls it (reductions).
+template <int P, int RECON, int CLOV, int XPAY, int FIN>
+__device__ __forceinline__ void dslash_pass(const KArgs& a, int sb, int slot0, int cnt) {
+  typedef typename Real<P>::T R;
+  constexpr int NRED = FIN == FIN_ALPHA ? 2 : FIN == FIN_OMEGA ? 3 : 1;
+  const int cb = sb * blockDim.x + threadIdx.x;
   const int slot = slot0 + threadIdx.y;
   const int k = slot < cnt ? (a.list ? a.list[slot] : slot) : -1;
-  const int cb = sb * blockDim.x + threadIdx.x;
   const bool ok = (k >= 0) && (cb < a.g.Vh);
   R red[NRED];  // FP64 fields reduce in FP64, FP32 / FP16 in FP32 per warp
 #pragma unroll
@@ -242,20 +244,31 @@ __device__ __forceinline__ void dslash_body(const KArgs& a) {
       red[0] = tt;
     }
   }
-  if (FIN == FIN_ALPHA || FIN == FIN_OMEGA)
+  if (FIN != FIN_NONE)  // per-warp partials, added up by k_finish
     warp_partials<NRED>(a.ra, red, k, sb * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5));
-  else if (FIN != FIN_NONE)
-    reduce_finalize<NRED, FIN>(a.ra, red, k, a.nsb, sb);
+
 }
 
+// FP32 / FP16: one pass, a CTA row per slot block
 template <int P, int RECON, int CLOV, int XPAY, int FIN>
 __global__ void __maxnreg__(SQ_DSLASH_LP_REGS) k_dslash(const KArgs a) {
-  dslash_body<P, RECON, CLOV, XPAY, FIN>(a);
+  int sb, rb;
+  cta_blocks(a, sb, rb);
+  const int cnt = a.list ? *a.count : a.n;
+  const int slot0 = rb * blockDim.y;
+  if (slot0 >= cnt) return;  // whole CTA idle (uniform)
+  dslash_pass<P, RECON, CLOV, XPAY, FIN>(a, sb, slot0, cnt);
 }
 
+// FP64: the CTA rows stride over the slots (a single pass with the usual
+// one row per slot block)
 template <int CLOV, int XPAY, int FIN>
 __global__ void __launch_bounds__(256) k_dslash64(const KArgs a) {
-  dslash_body<P64, 18, CLOV, XPAY, FIN>(a);
+  int sb, rb;
+  cta_blocks(a, sb, rb);
+  const int cnt = a.list ? *a.count : a.n;
+  for (int slot0 = rb * blockDim.y; slot0 < cnt; slot0 += a.nrb * blockDim.y)
+    dslash_pass<P64, 18, CLOV, XPAY, FIN>(a, sb, slot0, cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -325,11 +338,12 @@ void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s) {
     ok = dispatch_mode<P16, 12>(d, a, grid, block, s);
   }
   if (!ok) fprintf(stderr, "libstochq: internal error: no dslash variant for this call\n");
-  if (d.fin == FIN_ALPHA || d.fin == FIN_OMEGA) {  // per-source sums and scalars
+  if (d.fin != FIN_NONE) {  // per-source sums and scalars
     const int nparts = a.nsb * (int)(block.x >> 5);
     if (d.prec == P64) {
       if (d.fin == FIN_ALPHA) k_finish<double, 2, FIN_ALPHA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
-      else k_finish<double, 3, FIN_OMEGA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
+      else if (d.fin == FIN_OMEGA) k_finish<double, 3, FIN_OMEGA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
+      else k_finish<double, 1, FIN_TRUE><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
     } else {
       if (d.fin == FIN_ALPHA) k_finish<float, 2, FIN_ALPHA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
       else k_finish<float, 3, FIN_OMEGA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);

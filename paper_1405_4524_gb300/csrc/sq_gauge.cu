@@ -479,6 +479,14 @@ __global__ void k_finite(const double* a, size_t n, int* bad) {
   if (__syncthreads_or(b) && threadIdx.x == 0) atomicOr(bad, 1);
 }
 
+void launch_finite(const sq_ctx* c, const double* dev, size_t n, int* flag, cudaStream_t s) {
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  size_t want = (n + 255) / 256;
+  unsigned grid = (unsigned)(want < (size_t)sms * 8 ? (want > 0 ? want : 1) : (size_t)sms * 8);
+  k_finite<<<grid, 256, 0, s>>>(dev, n, flag);
+}
+
 sq_status check_finite(sq_ctx* c, const double* dev, size_t n, int* bad) {
   int* d_bad = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&d_bad, sizeof(int), c->stream);

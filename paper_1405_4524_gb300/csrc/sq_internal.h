@@ -62,6 +62,8 @@ struct Workspace {
   int* tsl = nullptr;           // n_rhs source time slices (device)
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_rec = nullptr, ev_out = nullptr;
+  cudaEvent_t ev_in[4] = {nullptr, nullptr, nullptr, nullptr};  // source groups copied in
+  int* flag = nullptr;          // non-finite input flag
   // cached graph of `chunk` iterations, keyed by everything baked into it
   cudaGraphExec_t graph = nullptr;
   std::vector<unsigned long long> graph_key;
@@ -153,6 +155,8 @@ sq_status read_error_word(sq_ctx* c, int* bits);
 sq_status gauge_convert(sq_ctx* c, const double* dev_lex);
 sq_status clover_build(sq_ctx* c, CloverSet& cs, double kappa, double csw);
 sq_status check_finite(sq_ctx* c, const double* dev, size_t n, int* bad);
+// sets *flag (device) to 1 if any of the n doubles is not finite; no sync
+void launch_finite(const sq_ctx* c, const double* dev, size_t n, int* flag, cudaStream_t s);
 
 // ---- spinor layout, BLAS, reductions (sq_blas.cu)
 void launch_pack(const sq_ctx* c, Field out, const double* lex, int parity, int prec, int n, cudaStream_t s);

@@ -19,6 +19,7 @@
 // active / update lists from device memory, so `chunk` iterations are
 // captured once into a CUDA graph and replayed; the host reads one integer
 // (sources still active) per graph launch.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -29,9 +30,13 @@
 namespace sq {
 
 static const Shape kBlasShape = {128, 2, 0};
-// kernels per inner iteration: one per class plus the three k_finish
-// launches (after the two fused dslash reductions and the x, r update)
-static const int kIterLaunches = KC_N + 3;
+// kernels per inner iteration: one per class plus the five k_finish
+// launches (after the two fused dslash reductions, the x, r update, the
+// FP64 true-residual hop and the FP64 update's <rhat, r>)
+static const int kIterLaunches = KC_N + 5;
+// host sources are copied in this many groups, overlapped with the FP64
+// Schur-source build of the previous group
+static const int kSetupGroups = 4;
 // FP64 dslash: ~146 registers per thread; 64-thread CTAs keep 7 per SM resident
 static const Shape k64Shape = {64, 1, 0};
 
@@ -45,30 +50,36 @@ struct VArgs {
   RedArgs ra;
 };
 
-#define SLOT_PROLOGUE                                           \
-  const int cnt = *a.count;                                     \
-  const int slot0 = blockIdx.y * blockDim.y;                    \
-  if (slot0 >= cnt) return;                                     \
-  const int slot = slot0 + threadIdx.y;                         \
-  const int k = slot < cnt ? a.list[slot] : -1;                 \
-  const int cb = blockIdx.x * blockDim.x + threadIdx.x;         \
-  const bool ok = (k >= 0) && (cb < a.Vh);
+// Source slots of a list: CTA row y covers slots blockIdx.y * blockDim.y +
+// threadIdx.y, then strides by the grid's rows. The inner loop launches
+// ceil(n / rows) CTA rows (one pass); the FP64 update path launches one CTA
+// row that walks the list, so a launch with an empty list costs one row of
+// CTAs instead of n / rows of them. The trip count is uniform in a CTA.
+#define SLOT_LOOP_BEGIN                                                                   \
+  const int cnt = *a.count;                                                               \
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;                                   \
+  for (int slot0 = blockIdx.y * blockDim.y; slot0 < cnt; slot0 += gridDim.y * blockDim.y) { \
+    const int slot = slot0 + threadIdx.y;                                                 \
+    const int k = slot < cnt ? a.list[slot] : -1;                                         \
+    const bool ok = (k >= 0) && (cb < a.Vh);
+#define SLOT_LOOP_END }
 
 // s = r - alpha v          f0 = r, f1 = v, f2 = s
 template <int P>
 __global__ void __launch_bounds__(256) k_s_update(const VArgs a) {
   typedef typename Real<P>::T R;
-  SLOT_PROLOGUE
-  if (!ok) return;
-  const RhsState& q = a.st[k];
-  const R ar = (R)q.alpha_re, ai = (R)q.alpha_im;
-  cx<R> r[12], v[12];
-  SpinorIO<P>::load(a.f0, k, cb, r);
-  SpinorIO<P>::load(a.f1, k, cb, v);
+  SLOT_LOOP_BEGIN
+    if (!ok) continue;
+    const RhsState& q = a.st[k];
+    const R ar = (R)q.alpha_re, ai = (R)q.alpha_im;
+    cx<R> r[12], v[12];
+    SpinorIO<P>::load(a.f0, k, cb, r);
+    SpinorIO<P>::load(a.f1, k, cb, v);
 #pragma unroll
-  for (int j = 0; j < 12; j++)
-    r[j] = mk(r[j].re - (ar * v[j].re - ai * v[j].im), r[j].im - (ar * v[j].im + ai * v[j].re));
-  SpinorIO<P>::store(a.f2, k, cb, r);
+    for (int j = 0; j < 12; j++)
+      r[j] = mk(r[j].re - (ar * v[j].re - ai * v[j].im), r[j].im - (ar * v[j].im + ai * v[j].re));
+    SpinorIO<P>::store(a.f2, k, cb, r);
+  SLOT_LOOP_END
 }
 
 // x += alpha p + omega s ; r = s - omega t ; reduce ||r||^2, <rhat, r>
@@ -77,63 +88,65 @@ template <int P, int PX>
 __global__ void __launch_bounds__(256) k_xr_update(const VArgs a) {
   typedef typename Real<P>::T R;
   typedef typename Real<PX>::T RX;
-  SLOT_PROLOGUE
-  R red[3] = {(R)0, (R)0, (R)0};
-  if (ok) {
-    const RhsState& q = a.st[k];
-    const R ar = (R)q.alpha_re, ai = (R)q.alpha_im, wr = (R)q.omega_re, wi = (R)q.omega_im;
-    cx<R> p[12], s[12];
-    cx<RX> x[12];
-    SpinorIO<P>::load(a.f1, k, cb, p);
-    SpinorIO<P>::load(a.f2, k, cb, s);
-    SpinorIO<PX>::load(a.f0, k, cb, x);
+  SLOT_LOOP_BEGIN
+    R red[3] = {(R)0, (R)0, (R)0};
+    if (ok) {
+      const RhsState& q = a.st[k];
+      const R ar = (R)q.alpha_re, ai = (R)q.alpha_im, wr = (R)q.omega_re, wi = (R)q.omega_im;
+      cx<R> p[12], s[12];
+      cx<RX> x[12];
+      SpinorIO<P>::load(a.f1, k, cb, p);
+      SpinorIO<P>::load(a.f2, k, cb, s);
+      SpinorIO<PX>::load(a.f0, k, cb, x);
 #pragma unroll
-    for (int j = 0; j < 12; j++) {
-      R dr = ar * p[j].re - ai * p[j].im + wr * s[j].re - wi * s[j].im;
-      R di = ar * p[j].im + ai * p[j].re + wr * s[j].im + wi * s[j].re;
-      x[j] = mk((RX)(x[j].re + dr), (RX)(x[j].im + di));
+      for (int j = 0; j < 12; j++) {
+        R dr = ar * p[j].re - ai * p[j].im + wr * s[j].re - wi * s[j].im;
+        R di = ar * p[j].im + ai * p[j].re + wr * s[j].im + wi * s[j].re;
+        x[j] = mk((RX)(x[j].re + dr), (RX)(x[j].im + di));
+      }
+      SpinorIO<PX>::store(a.f0, k, cb, x);
+      cx<R> t[12], rh[12];
+      SpinorIO<P>::load(a.f3, k, cb, t);
+#pragma unroll
+      for (int j = 0; j < 12; j++)
+        s[j] = mk(s[j].re - (wr * t[j].re - wi * t[j].im), s[j].im - (wr * t[j].im + wi * t[j].re));
+      SpinorIO<P>::store(a.f4, k, cb, s);
+      SpinorIO<P>::load(a.f5, k, cb, rh);
+      R n2 = 0, dr = 0, di = 0;
+#pragma unroll
+      for (int j = 0; j < 12; j++) {
+        n2 += s[j].re * s[j].re + s[j].im * s[j].im;
+        dr += rh[j].re * s[j].re + rh[j].im * s[j].im;
+        di += rh[j].re * s[j].im - rh[j].im * s[j].re;
+      }
+      red[0] = n2;
+      red[1] = dr;
+      red[2] = di;
     }
-    SpinorIO<PX>::store(a.f0, k, cb, x);
-    cx<R> t[12], rh[12];
-    SpinorIO<P>::load(a.f3, k, cb, t);
-#pragma unroll
-    for (int j = 0; j < 12; j++)
-      s[j] = mk(s[j].re - (wr * t[j].re - wi * t[j].im), s[j].im - (wr * t[j].im + wi * t[j].re));
-    SpinorIO<P>::store(a.f4, k, cb, s);
-    SpinorIO<P>::load(a.f5, k, cb, rh);
-    R n2 = 0, dr = 0, di = 0;
-#pragma unroll
-    for (int j = 0; j < 12; j++) {
-      n2 += s[j].re * s[j].re + s[j].im * s[j].im;
-      dr += rh[j].re * s[j].re + rh[j].im * s[j].im;
-      di += rh[j].re * s[j].im - rh[j].im * s[j].re;
-    }
-    red[0] = n2;
-    red[1] = dr;
-    red[2] = di;
-  }
-  warp_partials<3>(a.ra, red, k, (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)));
+    warp_partials<3>(a.ra, red, k, (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)));
+  SLOT_LOOP_END
 }
 
 // p = r + beta (p - omega v)     f0 = r, f1 = p, f2 = v
 template <int P>
 __global__ void __launch_bounds__(256) k_p_update(const VArgs a) {
   typedef typename Real<P>::T R;
-  SLOT_PROLOGUE
-  if (!ok) return;
-  const RhsState& q = a.st[k];
-  const R br = (R)q.beta_re, bi = (R)q.beta_im, wr = (R)q.omega_re, wi = (R)q.omega_im;
-  cx<R> r[12], p[12], v[12];
-  SpinorIO<P>::load(a.f0, k, cb, r);
-  SpinorIO<P>::load(a.f1, k, cb, p);
-  SpinorIO<P>::load(a.f2, k, cb, v);
+  SLOT_LOOP_BEGIN
+    if (!ok) continue;
+    const RhsState& q = a.st[k];
+    const R br = (R)q.beta_re, bi = (R)q.beta_im, wr = (R)q.omega_re, wi = (R)q.omega_im;
+    cx<R> r[12], p[12], v[12];
+    SpinorIO<P>::load(a.f0, k, cb, r);
+    SpinorIO<P>::load(a.f1, k, cb, p);
+    SpinorIO<P>::load(a.f2, k, cb, v);
 #pragma unroll
-  for (int j = 0; j < 12; j++) {
-    R ur = p[j].re - (wr * v[j].re - wi * v[j].im);
-    R ui = p[j].im - (wr * v[j].im + wi * v[j].re);
-    p[j] = mk(r[j].re + br * ur - bi * ui, r[j].im + br * ui + bi * ur);
-  }
-  SpinorIO<P>::store(a.f1, k, cb, p);
+    for (int j = 0; j < 12; j++) {
+      R ur = p[j].re - (wr * v[j].re - wi * v[j].im);
+      R ui = p[j].im - (wr * v[j].im + wi * v[j].re);
+      p[j] = mk(r[j].re + br * ur - bi * ui, r[j].im + br * ui + bi * ur);
+    }
+    SpinorIO<P>::store(a.f1, k, cb, p);
+  SLOT_LOOP_END
 }
 
 // FP64 update, part 1: x64 += xs ; xs = 0 ; r64 = b64 - x64
@@ -141,22 +154,23 @@ __global__ void __launch_bounds__(256) k_p_update(const VArgs a) {
 template <int PX>
 __global__ void __launch_bounds__(256) k_rel_x(const VArgs a) {
   typedef typename Real<PX>::T RX;
-  SLOT_PROLOGUE
-  if (!ok) return;
-  cx<double> x[12], b[12];
-  cx<RX> xs[12];
-  SpinorIO<P64>::load(a.f0, k, cb, x);
-  SpinorIO<PX>::load(a.f1, k, cb, xs);
-  SpinorIO<P64>::load(a.f2, k, cb, b);
+  SLOT_LOOP_BEGIN
+    if (!ok) continue;
+    cx<double> x[12], b[12];
+    cx<RX> xs[12];
+    SpinorIO<P64>::load(a.f0, k, cb, x);
+    SpinorIO<PX>::load(a.f1, k, cb, xs);
+    SpinorIO<P64>::load(a.f2, k, cb, b);
 #pragma unroll
-  for (int j = 0; j < 12; j++) {
-    x[j] = mk(x[j].re + (double)xs[j].re, x[j].im + (double)xs[j].im);
-    b[j] = b[j] - x[j];
-    xs[j] = mk((RX)0, (RX)0);
-  }
-  SpinorIO<P64>::store(a.f0, k, cb, x);
-  SpinorIO<PX>::store(a.f1, k, cb, xs);
-  SpinorIO<P64>::store(a.f3, k, cb, b);
+    for (int j = 0; j < 12; j++) {
+      x[j] = mk(x[j].re + (double)xs[j].re, x[j].im + (double)xs[j].im);
+      b[j] = b[j] - x[j];
+      xs[j] = mk((RX)0, (RX)0);
+    }
+    SpinorIO<P64>::store(a.f0, k, cb, x);
+    SpinorIO<PX>::store(a.f1, k, cb, xs);
+    SpinorIO<P64>::store(a.f3, k, cb, b);
+  SLOT_LOOP_END
 }
 
 // FP64 update, part 2: r = r64 ; on restart rhat = r, p = r ; reduce <rhat, r>
@@ -164,50 +178,52 @@ __global__ void __launch_bounds__(256) k_rel_x(const VArgs a) {
 template <int P>
 __global__ void __launch_bounds__(256) k_rel_r(const VArgs a) {
   typedef typename Real<P>::T R;
-  SLOT_PROLOGUE
-  R red[2] = {(R)0, (R)0};
-  if (ok) {
-    const bool restart = a.st[k].want_restart != 0;
-    cx<double> r64[12];
-    SpinorIO<P64>::load(a.f0, k, cb, r64);
-    cx<R> r[12], rh[12];
+  SLOT_LOOP_BEGIN
+    R red[2] = {(R)0, (R)0};
+    if (ok) {
+      const bool restart = a.st[k].want_restart != 0;
+      cx<double> r64[12];
+      SpinorIO<P64>::load(a.f0, k, cb, r64);
+      cx<R> r[12], rh[12];
 #pragma unroll
-    for (int j = 0; j < 12; j++) r[j] = mk((R)r64[j].re, (R)r64[j].im);
-    SpinorIO<P>::store(a.f1, k, cb, r);
-    if (restart) {
-      SpinorIO<P>::store(a.f2, k, cb, r);
-      SpinorIO<P>::store(a.f3, k, cb, r);
+      for (int j = 0; j < 12; j++) r[j] = mk((R)r64[j].re, (R)r64[j].im);
+      SpinorIO<P>::store(a.f1, k, cb, r);
+      if (restart) {
+        SpinorIO<P>::store(a.f2, k, cb, r);
+        SpinorIO<P>::store(a.f3, k, cb, r);
 #pragma unroll
-      for (int j = 0; j < 12; j++) rh[j] = r[j];
-    } else {
-      SpinorIO<P>::load(a.f2, k, cb, rh);
+        for (int j = 0; j < 12; j++) rh[j] = r[j];
+      } else {
+        SpinorIO<P>::load(a.f2, k, cb, rh);
+      }
+      R dr = 0, di = 0;
+#pragma unroll
+      for (int j = 0; j < 12; j++) {
+        dr += rh[j].re * r[j].re + rh[j].im * r[j].im;
+        di += rh[j].re * r[j].im - rh[j].im * r[j].re;
+      }
+      red[0] = dr;
+      red[1] = di;
     }
-    R dr = 0, di = 0;
-#pragma unroll
-    for (int j = 0; j < 12; j++) {
-      dr += rh[j].re * r[j].re + rh[j].im * r[j].im;
-      di += rh[j].re * r[j].im - rh[j].im * r[j].re;
-    }
-    red[0] = dr;
-    red[1] = di;
-  }
-  reduce_finalize<2, FIN_UPDATE>(a.ra, red, k, (int)gridDim.x, (int)blockIdx.x);
+    warp_partials<2>(a.ra, red, k, (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)));
+  SLOT_LOOP_END
 }
 
 // ||r64||^2 into the sources' true residual (initial update with x = 0,
 // where r64 = bhat exactly and no FP64 operator is needed).  f0 = r64
 __global__ void __launch_bounds__(256) k_true_norm(const VArgs a) {
-  SLOT_PROLOGUE
-  double red[1] = {0.0};
-  if (ok) {
-    cx<double> r[12];
-    SpinorIO<P64>::load(a.f0, k, cb, r);
-    double t = 0;
+  SLOT_LOOP_BEGIN
+    double red[1] = {0.0};
+    if (ok) {
+      cx<double> r[12];
+      SpinorIO<P64>::load(a.f0, k, cb, r);
+      double t = 0;
 #pragma unroll
-    for (int j = 0; j < 12; j++) t += r[j].re * r[j].re + r[j].im * r[j].im;
-    red[0] = t;
-  }
-  reduce_finalize<1, FIN_TRUE>(a.ra, red, k, (int)gridDim.x, (int)blockIdx.x);
+      for (int j = 0; j < 12; j++) t += r[j].re * r[j].re + r[j].im * r[j].im;
+      red[0] = t;
+    }
+    reduce_finalize<1, FIN_TRUE>(a.ra, red, k, (int)gridDim.x, (int)blockIdx.x);
+  SLOT_LOOP_END
 }
 
 // Rebuild the active list (ascending source index) and clear the update list.
@@ -240,7 +256,8 @@ __global__ void k_control(RhsState* st, Control* ctl, int* active_list, int n, i
 // similar rates then share FP64 launches instead of each running an almost
 // empty one, without adding updates. The list is in ascending source order
 // (deterministic).
-__global__ void k_plan(RhsState* st, Control* ctl, int* update_list, int n) {
+__global__ void k_plan(RhsState* st, Control* ctl, int* update_list, int n, cudaGraphConditionalHandle h,
+                       int use_h) {
   const int lane = threadIdx.x;
   bool any = false;
   for (int k0 = 0; k0 < n; k0 += 32) {
@@ -267,7 +284,10 @@ __global__ void k_plan(RhsState* st, Control* ctl, int* update_list, int n) {
       base += __popc(m);
     }
   }
-  if (lane == 0) ctl->n_update = base;
+  if (lane == 0) {
+    ctl->n_update = base;
+    if (use_h) cudaGraphSetConditional(h, base > 0 ? 1u : 0u);
+  }
 }
 
 // x64 += xs ; xs = 0 for every source (after the loop: sources that retired
@@ -333,6 +353,8 @@ static void free_ws(Workspace& w) {
   }
   if (w.ev_rec) cudaEventDestroy(w.ev_rec);
   if (w.ev_out) cudaEventDestroy(w.ev_out);
+  for (auto ev : w.ev_in)
+    if (ev) cudaEventDestroy(ev);
   if (w.graph) cudaGraphExecDestroy(w.graph);
   for (auto e : w.pev) cudaEventDestroy(e);
   if (w.hist) cudaFree(w.hist);
@@ -380,6 +402,7 @@ static sq_status alloc_ws(sq_ctx* c, Workspace& w, int n, int inner) {
   size_t o_sc = tot; tot += al((size_t)n * 8 * sizeof(double));
   size_t o_pi = tot; tot += al((size_t)n * c->dims[3] * sizeof(double));
   size_t o_ts = tot; tot += al((size_t)n * sizeof(int));
+  size_t o_fl = tot; tot += al(sizeof(int));
   void* base = nullptr;
   cudaError_t e = cudaMalloc(&base, tot);
   if (e != cudaSuccess) {
@@ -407,10 +430,17 @@ static sq_status alloc_ws(sq_ctx* c, Workspace& w, int n, int inner) {
   w.scal = (double*)(b + o_sc);
   w.pion = (double*)(b + o_pi);
   w.tsl = (int*)(b + o_ts);
+  w.flag = (int*)(b + o_fl);
   w.nblk_stride = nblk;
-  e = cudaStreamCreateWithFlags(&w.aux, cudaStreamNonBlocking);
+  // highest priority: the output kernels are scheduled ahead of the pending
+  // CTAs of the FP64 check, so the copy-out starts early
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  e = cudaStreamCreateWithPriority(&w.aux, cudaStreamNonBlocking, prio_hi);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev_rec, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.ev_out, cudaEventDisableTiming);
+  for (int g = 0; g < kSetupGroups && e == cudaSuccess; g++)
+    e = cudaEventCreateWithFlags(&w.ev_in[g], cudaEventDisableTiming);
   if (e != cudaSuccess) return cuda_check(c, e, "workspace stream");
   e = cudaMemset(w.counter, 0, (size_t)n * sizeof(unsigned));
   return cuda_check(c, e, "workspace counters");
@@ -446,6 +476,7 @@ struct Marks {
   cudaEvent_t* ev = nullptr;  // KC_N + 1 events for this iteration
   unsigned mask = 0;          // marks that record (mark kc opens class kc)
   bool capture = false;
+  bool cond = false;          // capturing: FP64 update path under an IF node
   int i = 0;
   void mark(cudaStream_t s) {
     if (!ev) return;
@@ -511,13 +542,50 @@ static void launch_iteration(sq_ctx* c, Workspace& w, const CloverSet& cs, doubl
   a.f0 = w.r; a.f1 = w.p; a.f2 = w.v;
   k_p_update<P><<<bg, bb, 0, s>>>(a);
   m.mark(s);
-  k_plan<<<1, 32, 0, s>>>(w.st, w.ctl, w.update_list, n);
+  // FP64 update for the sources that asked for one - in most iterations
+  // none. In a captured graph the whole path sits under an IF node that
+  // k_plan switches on only when its update list is non-empty; otherwise
+  // (no graph, or profiling every kernel: event nodes may not sit inside a
+  // conditional body) its launches see an empty list and exit.
+  cudaGraphConditionalHandle hcond = 0;
+  bool cond = m.cond;
+  if (cond) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    cond = cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, nullptr, nullptr, nullptr) == cudaSuccess &&
+           cst == cudaStreamCaptureStatusActive &&
+           cudaGraphConditionalHandleCreate(&hcond, cg, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  }
+  k_plan<<<1, 32, 0, s>>>(w.st, w.ctl, w.update_list, n, hcond, cond ? 1 : 0);
   m.mark(s);
-  // FP64 update for the sources that asked for one
+  cudaStream_t us = s;
+  cudaGraphNode_t cnode = nullptr;
+  if (cond) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &nd);
+    // (the union inside has no default constructor: zeroed storage)
+    alignas(cudaGraphNodeParams) unsigned char cpbuf[sizeof(cudaGraphNodeParams)];
+    memset(cpbuf, 0, sizeof(cpbuf));
+    cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cpbuf);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hcond;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphAddNode(&cnode, cg, deps, nullptr, nd, &cp);
+    cudaStreamBeginCaptureToGraph(w.aux, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                  cudaStreamCaptureModeRelaxed);
+    us = w.aux;
+  }
+  // the BLAS launches walk the update list with a single CTA row; the FP64
+  // operator keeps a row per source (measured faster for real updates)
+  const dim3 bgu(bg.x, 1);
   VArgs u = vargs(c, w, true);
   u.f0 = w.x64; u.f1 = w.xs; u.f2 = w.b64; u.f3 = w.r64;
-  k_rel_x<PX><<<bg, bb, 0, s>>>(u);
-  m.mark(s);
+  k_rel_x<PX><<<bgu, bb, 0, us>>>(u);
+  m.mark(us);
   DslashCall d64 = d;
   d64.prec = P64;
   d64.recon = 18;
@@ -525,15 +593,21 @@ static void launch_iteration(sq_ctx* c, Workspace& w, const CloverSet& cs, doubl
   d64.count = &w.ctl->n_update;
   d64.shape = k64Shape;
   d64.out = w.t64o; d64.in = w.x64; d64.p_out = 1; d64.xpay = 0; d64.fin = FIN_NONE;
-  launch_dslash(c, d64, s);
-  m.mark(s);
+  launch_dslash(c, d64, us);
+  m.mark(us);
   d64.out = w.r64; d64.in = w.t64o; d64.x = w.r64; d64.p_out = 0; d64.xpay = 1; d64.a = kappa * kappa;
   d64.fin = FIN_TRUE;
-  launch_dslash(c, d64, s);
-  m.mark(s);
+  launch_dslash(c, d64, us);
+  m.mark(us);
   u.f0 = w.r64; u.f1 = w.r; u.f2 = w.rh; u.f3 = w.p;
-  k_rel_r<P><<<bg, bb, 0, s>>>(u);
-  m.mark(s);
+  k_rel_r<P><<<bgu, bb, 0, us>>>(u);
+  k_finish<R, 2, FIN_UPDATE><<<n, 256, 0, us>>>(u.ra, w.update_list, &w.ctl->n_update, n, (int)bgu.x * (kBlasShape.sx / 32));
+  m.mark(us);
+  if (cond) {
+    cudaGraph_t body = nullptr;
+    cudaStreamEndCapture(w.aux, &body);
+    cudaStreamUpdateCaptureDependencies(s, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+  }
   k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n, m.ev ? w.hist : nullptr, it, chunk);
   m.mark(s);
 }
@@ -542,6 +616,7 @@ static void launch_iteration(sq_ctx* c, Workspace& w, const CloverSet& cs, doubl
 // x0 = 0 the residual is bhat itself and no operator is applied)
 template <int P, int PX>
 static void launch_update(sq_ctx* c, Workspace& w, const CloverSet& cs, double kappa, cudaStream_t s, bool zero_x) {
+  typedef typename Real<P>::T R;
   const int n = w.n_rhs;
   dim3 bb(kBlasShape.sx, kBlasShape.ry);
   dim3 bg((c->Vh + kBlasShape.sx - 1) / kBlasShape.sx, (n + kBlasShape.ry - 1) / kBlasShape.ry);
@@ -553,8 +628,9 @@ static void launch_update(sq_ctx* c, Workspace& w, const CloverSet& cs, double k
     k_true_norm<<<bg, bb, 0, s>>>(u);
     u.f0 = w.r64; u.f1 = w.r; u.f2 = w.rh; u.f3 = w.p;
     k_rel_r<P><<<bg, bb, 0, s>>>(u);
+    k_finish<R, 2, FIN_UPDATE><<<n, 256, 0, s>>>(u.ra, w.update_list, &w.ctl->n_update, n, (int)bg.x * (kBlasShape.sx / 32));
     k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n, nullptr, 0, 0);
-    c->launches += 4;
+    c->launches += 5;
     return;
   }
   DslashCall d64;
@@ -575,8 +651,9 @@ static void launch_update(sq_ctx* c, Workspace& w, const CloverSet& cs, double k
   launch_dslash(c, d64, s);
   u.f0 = w.r64; u.f1 = w.r; u.f2 = w.rh; u.f3 = w.p;
   k_rel_r<P><<<bg, bb, 0, s>>>(u);
+  k_finish<R, 2, FIN_UPDATE><<<n, 256, 0, s>>>(u.ra, w.update_list, &w.ctl->n_update, n, (int)bg.x * (kBlasShape.sx / 32));
   k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n, nullptr, 0, 0);
-  c->launches += 6;
+  c->launches += 8;
 }
 
 typedef void (*IterFn)(sq_ctx*, Workspace&, const CloverSet&, double, Shape, cudaStream_t, Marks, int, int);
@@ -710,40 +787,74 @@ static sq_status setup_problem(Prob& p, const sq_solve_params& prm) {
   Workspace& w = *p.w;
   cudaStream_t s = p.s;
   const int n = p.n;
-  const size_t lex_doubles = (size_t)n * c->V * 24;
-  const double* dsrc = p.src;
-  if (prm.io == SQ_HOST) {
-    cudaMemcpyAsync(w.lex, p.src, lex_doubles * sizeof(double), cudaMemcpyHostToDevice, s);
-    dsrc = w.lex;
-    if (prm.pion && prm.pion_tslice)
-      cudaMemcpyAsync(w.tsl, prm.pion_tslice, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s);
+  const size_t lex_src = (size_t)c->V * 24;  // doubles per source
+  // Sources in groups: with host I/O the copy of group g + 1 (on the side
+  // stream) overlaps the FP64 work on group g. Per group: finite check
+  // (flag read once at the end), even / odd packing, norms and the Schur
+  // source bhat = A_ee^{-1} (eta_e + k D_eo A_oo^{-1} eta_o).
+  const int G = prm.io == SQ_HOST ? std::min(n, kSetupGroups) : 1;
+  const double* dsrc = prm.io == SQ_HOST ? w.lex : p.src;
+  if (prm.io == SQ_HOST && prm.pion && prm.pion_tslice)
+    cudaMemcpyAsync(w.tsl, prm.pion_tslice, (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s);
+  // the side stream must not overwrite the staging buffer while an earlier
+  // solve's output copy may still read it (it was synchronised, but keep
+  // the order explicit)
+  cudaEventRecord(w.ev_rec, s);
+  cudaStreamWaitEvent(w.aux, w.ev_rec, 0);
+  cudaMemsetAsync(w.flag, 0, sizeof(int), s);
+  auto sub64 = [&](const Field& f, int k0) {
+    return make_field((double2*)f.data + (size_t)k0 * 12 * c->Vh, c->Vh, P64, 0);
+  };
+  RedArgs ra = red_args(w);
+  Field none = make_field(nullptr, c->Vh, P64, n);
+  for (int g = 0; g < G; g++) {
+    const int k0 = g * n / G, k1 = (g + 1) * n / G, ng = k1 - k0;
+    if (ng <= 0) continue;
+    const double* gsrc = dsrc + (size_t)k0 * lex_src;
+    if (prm.io == SQ_HOST) {
+      cudaMemcpyAsync(w.lex + (size_t)k0 * lex_src, p.src + (size_t)k0 * lex_src, ng * lex_src * sizeof(double),
+                      cudaMemcpyHostToDevice, w.aux);
+      cudaEventRecord(w.ev_in[g], w.aux);
+      cudaStreamWaitEvent(s, w.ev_in[g], 0);
+    }
+    launch_finite(c, gsrc, ng * lex_src, w.flag, s);
+    launch_pack(c, sub64(w.eta_e, k0), gsrc, 0, P64, ng, s);
+    launch_pack(c, sub64(w.eta_o, k0), gsrc, 1, P64, ng, s);
+    launch_norm2(c, sub64(w.eta_e, k0), P64, ng, w.scal + k0, ra, s);
+    launch_norm2(c, sub64(w.eta_o, k0), P64, ng, w.scal + n + k0, ra, s);
+    launch_clover64(c, *p.cs, sub64(w.t64o, k0), none, sub64(w.eta_o, k0), 1, 0.0, 1.0, 1, ng, s);
+    DslashCall d;
+    memset(&d, 0, sizeof(d));
+    d.prec = P64;
+    d.recon = 18;
+    d.cs = p.cs;
+    d.n = ng;
+    d.shape = kBlasShape;
+    d.ra = ra;
+    d.out = sub64(w.r64, k0); d.in = sub64(w.t64o, k0); d.x = sub64(w.eta_e, k0); d.p_out = 0; d.xpay = 1;
+    d.a = p.kappa;
+    launch_dslash(c, d, s);
+    launch_clover64(c, *p.cs, sub64(w.b64, k0), none, sub64(w.r64, k0), 0, 0.0, 1.0, 1, ng, s);
+    c->launches += 8;
   }
-  // the context stream is used by check_finite; order it after this stream
-  cudaEvent_t ev;
-  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-  cudaEventRecord(ev, s);
-  cudaStreamWaitEvent(c->stream, ev, 0);
+  std::vector<double> eta2(2 * n);
   int bad = 0;
-  st = check_finite(c, dsrc, lex_doubles, &bad);
-  if (st == SQ_OK && bad) st = set_error(c, SQ_ERR_NONFINITE, "sq_solve: NaN or Inf in the sources");
-  cudaEventDestroy(ev);
-  if (st != SQ_OK) return st;
-  launch_pack(c, w.eta_e, dsrc, 0, P64, n, s);
-  launch_pack(c, w.eta_o, dsrc, 1, P64, n, s);
-  c->launches += 3;
+  cudaMemcpyAsync(eta2.data(), w.scal, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&bad, w.flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_check(c, e, "sq_solve setup");
+  if (bad) return set_error(c, SQ_ERR_NONFINITE, "sq_solve: NaN or Inf in the sources");
   if (prm.use_x0) {
     const double* dx0 = p.sol;
     if (prm.io == SQ_HOST) {
-      cudaMemcpyAsync(w.lex, p.sol, lex_doubles * sizeof(double), cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(w.lex, p.sol, (size_t)n * lex_src * sizeof(double), cudaMemcpyHostToDevice, s);
       dx0 = w.lex;
     }
-    cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    cudaEventRecord(ev, s);
-    cudaStreamWaitEvent(c->stream, ev, 0);
-    cudaEventDestroy(ev);
-    bad = 0;
-    st = check_finite(c, dx0, lex_doubles, &bad);
-    if (st != SQ_OK) return st;
+    cudaMemsetAsync(w.flag, 0, sizeof(int), s);
+    launch_finite(c, dx0, (size_t)n * lex_src, w.flag, s);
+    cudaMemcpyAsync(&bad, w.flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_check(c, e, "sq_solve initial guess");
     if (bad) return set_error(c, SQ_ERR_NONFINITE, "sq_solve: NaN or Inf in the initial guess");
     launch_pack(c, w.x64, dx0, 0, P64, n, s);
     c->launches += 2;
@@ -751,29 +862,6 @@ static sq_status setup_problem(Prob& p, const sq_solve_params& prm) {
     cudaMemsetAsync(w.x64.data, 0, field_bytes(c->Vh, P64, n), s);
   }
   cudaMemsetAsync(w.xs.data, 0, field_bytes(c->Vh, px_of(inner), n), s);
-  // ||eta||^2
-  RedArgs ra = red_args(w);
-  launch_norm2(c, w.eta_e, P64, n, w.scal, ra, s);
-  launch_norm2(c, w.eta_o, P64, n, w.scal + n, ra, s);
-  std::vector<double> eta2(2 * n);
-  cudaMemcpyAsync(eta2.data(), w.scal, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, s);
-  // bhat = A_ee^{-1} (eta_e + k D_eo A_oo^{-1} eta_o)
-  Field none = make_field(nullptr, c->Vh, P64, n);
-  launch_clover64(c, *p.cs, w.t64o, none, w.eta_o, 1, 0.0, 1.0, 1, n, s);
-  DslashCall d;
-  memset(&d, 0, sizeof(d));
-  d.prec = P64;
-  d.recon = 18;
-  d.cs = p.cs;
-  d.n = n;
-  d.shape = kBlasShape;
-  d.ra = ra;
-  d.out = w.r64; d.in = w.t64o; d.x = w.eta_e; d.p_out = 0; d.xpay = 1; d.a = p.kappa;
-  launch_dslash(c, d, s);
-  launch_clover64(c, *p.cs, w.b64, none, w.r64, 0, 0.0, 1.0, 1, n, s);
-  c->launches += 5;
-  cudaError_t e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_check(c, e, "sq_solve setup");
   p.target2.resize(n);
   p.enorm2.resize(n);
   for (int k = 0; k < n; k++) {
@@ -923,6 +1011,7 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
             m.mask = pmask;
             m.capture = capture;
           }
+          m.cond = capture && prm.profile != 1;
           p.iter(p.c, *p.w, *p.cs, p.kappa, p.sh, ps, m, it, chunk);
         }
         if (ps != sb) {  // join
