@@ -536,7 +536,8 @@ sq_status sq_get_profile(const sq_ctx* c, sq_kernel_stat* out, int max, int* n) 
   static const char* names[KC_N] = {
       "dslash_clover",         "dslash_clover_xpay_alpha", "blas_s_update",
       "dslash_clover",         "dslash_clover_xpay_omega", "blas_xr_update_norms",
-      "blas_p_update",         "plan_fp64_updates",        "fp64_update_x",
+      "blas_p_update",         "plan_updates",             "fp32_refresh",
+      "fp64_update_x",
       "fp64_dslash_clover",    "fp64_dslash_xpay_norm",    "fp64_update_r",
       "control"};
   if (!c || !n || max < 0) return SQ_ERR_ARG;

@@ -296,6 +296,7 @@ static bool dispatch_mode(const DslashCall& d, const KArgs& a, dim3 grid, dim3 b
   if (m != 3) return false;
   if (d.fin == FIN_ALPHA) { go<P, RECON, 1, 1, FIN_ALPHA>(a, grid, block, s); return true; }
   if (d.fin == FIN_OMEGA) { go<P, RECON, 1, 1, FIN_OMEGA>(a, grid, block, s); return true; }
+  if (d.fin == FIN_TRUE && P == P32) { go<P, RECON, 1, 1, FIN_TRUE>(a, grid, block, s); return true; }
   return false;
 }
 
@@ -346,7 +347,8 @@ void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s) {
       else k_finish<double, 1, FIN_TRUE><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
     } else {
       if (d.fin == FIN_ALPHA) k_finish<float, 2, FIN_ALPHA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
-      else k_finish<float, 3, FIN_OMEGA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
+      else if (d.fin == FIN_OMEGA) k_finish<float, 3, FIN_OMEGA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
+      else k_finish<float, 1, FIN_TRUE><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
     }
   }
 }

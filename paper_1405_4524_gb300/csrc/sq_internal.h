@@ -54,6 +54,8 @@ struct Workspace {
   Control* ctl = nullptr;
   int* active_list = nullptr;
   int* update_list = nullptr;
+  int* refresh_list = nullptr;  // sources whose update is an FP32 refresh
+  bool refresh = false;         // FP32 refreshes enabled for this solve
   double* scal = nullptr;       // n_rhs * 4 doubles of scratch results
   int nblk_stride = 0;
   // solution output: unpack, copy-out and pion epilogue run on `aux`,
@@ -92,7 +94,8 @@ enum KClass {
   KC_DSLASH_XPAY_OMEGA,    // t = s - k^2 ... ; <t, s>, <t, t>
   KC_XR_UPDATE,            // x += alpha p + omega s ; r = s - omega t ; norms
   KC_P_UPDATE,             // p = r + beta (p - omega v)
-  KC_PLAN,                 // FP64 update list (grouped across sources)
+  KC_PLAN,                 // update lists (grouped across sources)
+  KC_REFRESH,              // FP32 refresh: r = bhat - Mhat x in FP32
   KC_REL_X,                // FP64 update: x64 += xs ; r64 = b - x64
   KC_REL_DSLASH1,          // FP64 tmp = A^{-1} D x64
   KC_REL_DSLASH2,          // FP64 r64 += k^2 A^{-1} D tmp ; ||r64||^2

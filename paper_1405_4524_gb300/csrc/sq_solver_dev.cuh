@@ -7,7 +7,11 @@
 // t = Mhat s; omega = <t,s>/<t,t>; x += alpha p + omega s; r = s - omega t;
 // rho' = <rhat,r>; beta = (rho'/rho)(alpha/omega); p = r + beta (p - omega v).
 // FP64 updates (reliable updates, Sleijpen & van der Vorst 1996, or
-// defect-correction restarts) recompute r = bhat - Mhat x in FP64.
+// defect-correction restarts) recompute r = bhat - Mhat x in FP64. With an
+// FP16 inner recurrence the reliable updates whose residual is still far
+// above the FP32 floor recompute it in FP32 instead (a refresh: same
+// operator, FP32 fields, x = x64 + xs rounded once); below the floor they
+// are FP64 updates.
 #pragma once
 
 #include "sq_device.cuh"
@@ -28,6 +32,8 @@ struct RhsState {
                    // full-lattice FP64 residual after the loop confirms it
   double true_r2;  // last FP64 Schur residual norm^2
   double delta2;   // update trigger (squared)
+  double ref2;     // residual^2 of the first FP64 update (the reference for
+                   // FP32 refreshes)
   int iter, updates, restarts, breakdowns;
   int status;        // sq_status value
   int active;        // 1 while iterating
@@ -35,15 +41,16 @@ struct RhsState {
   int want_restart;  // BiCGStab restart requested with the update
   int max_iter;
   int defect;        // 1: restart at every FP64 update (defect correction)
-  int pad[2];
+  int refresh;       // 1: updates above the FP32 floor are FP32 refreshes
+  int refreshes;     // FP32 residual refreshes done
 };
 
 // control block shared by all sources of a solve
 struct Control {
   int n_active;   // length of the active list
   int n_update;   // length of the update list
+  int n_refresh;  // length of the refresh list
   int err;        // sticky device error bits
-  int pad;
 };
 
 enum FinKind {
@@ -53,7 +60,8 @@ enum FinKind {
   FIN_TRUE = 3,    // sums: ||r64||^2
   FIN_ITER = 4,    // sums: ||r||^2, <rhat,r> (re, im)
   FIN_UPDATE = 5,  // sums: <rhat,r> (re, im)
-  FIN_STORE = 6    // sums stored to out[k*NRED + i]
+  FIN_STORE = 6,   // sums stored to out[k*NRED + i]
+  FIN_REFRESH = 7  // sums: <rhat,r> (re, im) after an FP32 refresh
 };
 
 struct RedArgs {
@@ -149,6 +157,7 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int k, const double*
     q.rnorm2 = q.true_r2;
     q.maxr2 = q.true_r2;
     q.rstart2 = q.true_r2;
+    if (q.updates == 0) q.ref2 = q.true_r2;
     q.updates++;
     if (q.want_restart) q.restarts++;
     q.want_restart = 0;
@@ -165,6 +174,20 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int k, const double*
     } else if (q.breakdowns > 64) {
       q.active = 0;
       q.status = 7;  // SQ_ERR_BREAKDOWN
+    }
+  } else if (FIN == FIN_REFRESH) {
+    // r was replaced by the residual recomputed in FP32 (far above the
+    // FP32 floor, so its rounding is negligible); the Krylov space is kept
+    q.rho_re = s[0];
+    q.rho_im = s[1];
+    q.rnorm2 = q.true_r2;
+    q.maxr2 = q.true_r2;
+    q.rstart2 = q.true_r2;
+    q.refreshes++;
+    q.want_update = 0;
+    if (!isfinite(q.true_r2)) {
+      q.active = 0;
+      q.status = 4;  // SQ_ERR_NONFINITE
     }
   } else if (FIN == FIN_STORE) {
     // handled by the caller (needs NRED)
