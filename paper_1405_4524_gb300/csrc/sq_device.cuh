@@ -199,6 +199,22 @@ struct SpinorIO<P16> {
       v[4 * c + 3] = mk(e.x * s, e.y * s);
     }
   }
+  // values as stored (no norm applied); returns the site's norm: a linear
+  // stencil applies it once to its result instead of to all 24 inputs
+  static __device__ __forceinline__ float load_raw(const Field& f, int k, int cb, cx<float> v[12]) {
+    const uint4* p = (const uint4*)f.data + (size_t)k * 3 * f.Vh + cb;
+    const float s = __ldg(f.norm + (size_t)k * f.Vh + cb);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      uint4 q = __ldg(p + (size_t)c * f.Vh);
+      float2 a = h2f(q.x), b = h2f(q.y), d = h2f(q.z), e = h2f(q.w);
+      v[4 * c + 0] = mk(a.x, a.y);
+      v[4 * c + 1] = mk(b.x, b.y);
+      v[4 * c + 2] = mk(d.x, d.y);
+      v[4 * c + 3] = mk(e.x, e.y);
+    }
+    return s;
+  }
   static __device__ __forceinline__ void store(const Field& f, int k, int cb, const cx<float> v[12]) {
     float m = 0.f;
 #pragma unroll

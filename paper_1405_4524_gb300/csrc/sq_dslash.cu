@@ -132,15 +132,21 @@ __device__ __forceinline__ void hop_dir(const KArgs& a, int k, int cb, Coord c,
     Coord n = step(a.g, c, MU, +1);
     int ncb = cb_of(a.g, n.x, n.y, n.z, n.t);
     cx<R> v[12], h[6], w[6];
-    SpinorIO<P>::load(a.in, k, ncb, v);
+    R f = (R)1;
+    if (P == P16) f = SpinorIO<P16>::load_raw(a.in, k, ncb, (cx<float>*)v);  // norm applied to w
+    else SpinorIO<P>::load(a.in, k, ncb, v);
     project<MU, -1>(v, h);
     Link<R> u;
     LinkIO<P, RECON>::load(a.links, a.g.Vh, a.p_out, MU, cb, u);
     mv(u, h, w);
-    if (MU == 3 && c.t == a.g.T - 1) {
-      const R f = (R)a.g.tbc;
+    if (P == P16) {  // site norm, and the time-boundary sign
+      if (MU == 3 && c.t == a.g.T - 1) f *= (R)a.g.tbc;
 #pragma unroll
       for (int j = 0; j < 6; j++) w[j] = f * w[j];
+    } else if (MU == 3 && c.t == a.g.T - 1) {
+      const R tb = (R)a.g.tbc;
+#pragma unroll
+      for (int j = 0; j < 6; j++) w[j] = tb * w[j];
     }
     accum<MU, -1>(acc, w);
   }
@@ -148,15 +154,21 @@ __device__ __forceinline__ void hop_dir(const KArgs& a, int k, int cb, Coord c,
     Coord n = step(a.g, c, MU, -1);
     int ncb = cb_of(a.g, n.x, n.y, n.z, n.t);
     cx<R> v[12], h[6], w[6];
-    SpinorIO<P>::load(a.in, k, ncb, v);
+    R f = (R)1;
+    if (P == P16) f = SpinorIO<P16>::load_raw(a.in, k, ncb, (cx<float>*)v);  // norm applied to w
+    else SpinorIO<P>::load(a.in, k, ncb, v);
     project<MU, +1>(v, h);
     Link<R> u;
     LinkIO<P, RECON>::load(a.links, a.g.Vh, 1 - a.p_out, MU, ncb, u);
     mv_dag(u, h, w);
-    if (MU == 3 && c.t == 0) {
-      const R f = (R)a.g.tbc;
+    if (P == P16) {  // site norm, and the time-boundary sign
+      if (MU == 3 && c.t == 0) f *= (R)a.g.tbc;
 #pragma unroll
       for (int j = 0; j < 6; j++) w[j] = f * w[j];
+    } else if (MU == 3 && c.t == 0) {
+      const R tb = (R)a.g.tbc;
+#pragma unroll
+      for (int j = 0; j < 6; j++) w[j] = tb * w[j];
     }
     accum<MU, +1>(acc, w);
   }
