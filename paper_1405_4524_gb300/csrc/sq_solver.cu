@@ -30,10 +30,12 @@
 namespace sq {
 
 static const Shape kBlasShape = {128, 2, 0};
-// kernels per inner iteration: one per class plus the five k_finish
-// launches (after the two fused dslash reductions, the x, r update, the
-// FP64 true-residual hop and the FP64 update's <rhat, r>)
-static const int kIterLaunches = KC_N + 5;
+// kernels of one inner iteration outside the update paths (two plain and
+// two fused dslash, three k_finish, s / x,r / p updates, plan, control) and
+// inside each update path (FP64 update or FP32 refresh: x, two operator
+// launches, two k_finish, r)
+static const int kChainLaunches = 12;
+static const int kUpdateLaunches = 6;
 // host sources are copied in this many groups, overlapped with the FP64
 // Schur-source build of the previous group
 static const int kSetupGroups = 4;
@@ -326,6 +328,7 @@ __global__ void k_plan(RhsState* st, Control* ctl, int* update_list, int* refres
     if (use_h) {
       cudaGraphSetConditional(h_upd, nu > 0 ? 1u : 0u);
       if (h_ref) cudaGraphSetConditional(h_ref, nr > 0 ? 1u : 0u);
+      ctl->launched += (nu > 0 ? kUpdateLaunches : 0) + (nr > 0 && h_ref ? kUpdateLaunches : 0);
     }
   }
 }
@@ -379,6 +382,7 @@ __global__ void k_init(RhsState* st, Control* ctl, int* update_list, const doubl
     ctl->n_update = n;
     ctl->n_refresh = 0;
     ctl->n_active = 0;
+    ctl->launched = 0;
   }
 }
 
@@ -1144,7 +1148,11 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
         e = cudaGetLastError();
       }
       if (e != cudaSuccess) break;
-      for (auto& p : P) p.c->launches += (long long)chunk * (kIterLaunches + (p.w->refresh ? 6 : 0));
+      // launches inside conditional nodes are counted on the device
+      for (auto& p : P)
+        p.c->launches += (long long)chunk * (kChainLaunches + (use_graph && prm.profile != 1
+                                                                    ? 0
+                                                                    : kUpdateLaunches * (p.w->refresh ? 2 : 1)));
       launched += chunk;
       for (int i = 0; i < np; i++)
         cudaMemcpyAsync(h_active + i, &P[i].w->ctl->n_active, sizeof(int), cudaMemcpyDeviceToHost, sb);
@@ -1219,7 +1227,10 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       cudaMemcpyAsync(res2.data(), w.scal, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, sb);
       std::vector<RhsState> hs(n);
       cudaMemcpyAsync(hs.data(), w.st, n * sizeof(RhsState), cudaMemcpyDeviceToHost, sb);
+      Control hc;
+      cudaMemcpyAsync(&hc, w.ctl, sizeof(Control), cudaMemcpyDeviceToHost, sb);
       e = cudaStreamSynchronize(sb);
+      c->launches += hc.launched;
       if (e != cudaSuccess) {
         cudaFreeHost(h_active);
         return cuda_check(c0, e, "final residual");

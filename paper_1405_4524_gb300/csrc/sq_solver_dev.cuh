@@ -51,6 +51,9 @@ struct Control {
   int n_update;   // length of the update list
   int n_refresh;  // length of the refresh list
   int err;        // sticky device error bits
+  int launched;   // kernels run inside conditional graph nodes (counted by
+                  // k_plan when it switches a node on)
+  int pad;
 };
 
 enum FinKind {
