@@ -487,23 +487,4 @@ void launch_finite(const sq_ctx* c, const double* dev, size_t n, int* flag, cuda
   k_finite<<<grid, 256, 0, s>>>(dev, n, flag);
 }
 
-sq_status check_finite(sq_ctx* c, const double* dev, size_t n, int* bad) {
-  int* d_bad = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&d_bad, sizeof(int), c->stream);
-  if (e != cudaSuccess) return cuda_check(c, e, "finite check alloc");
-  cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream);
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  size_t want = (n + 255) / 256;
-  unsigned grid = (unsigned)(want < (size_t)sms * 8 ? (want > 0 ? want : 1) : (size_t)sms * 8);
-  k_finite<<<grid, 256, 0, c->stream>>>(dev, n, d_bad);
-  int h = 0;
-  cudaMemcpyAsync(&h, d_bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-  cudaFreeAsync(d_bad, c->stream);
-  e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_check(c, e, "finite check");
-  *bad = h;
-  return SQ_OK;
-}
-
 }  // namespace sq

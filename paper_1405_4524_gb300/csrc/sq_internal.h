@@ -157,7 +157,6 @@ sq_status read_error_word(sq_ctx* c, int* bits);
 // ---- gauge / clover (sq_gauge.cu)
 sq_status gauge_convert(sq_ctx* c, const double* dev_lex);
 sq_status clover_build(sq_ctx* c, CloverSet& cs, double kappa, double csw);
-sq_status check_finite(sq_ctx* c, const double* dev, size_t n, int* bad);
 // sets *flag (device) to 1 if any of the n doubles is not finite; no sync
 void launch_finite(const sq_ctx* c, const double* dev, size_t n, int* flag, cudaStream_t s);
 
