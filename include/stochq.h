@@ -99,7 +99,11 @@ typedef struct sq_solve_params {
                           last update (reliable) or < delta * ||r_start||
                           (defect correction); <= 0 picks the default for
                           the inner precision (FP32 3e-6, FP16 3e-3);
-                          ignored for SQ_F64                               */
+                          ignored for SQ_F64. With SQ_F16 and reliable
+                          updates, an update while ||r|| is more than 1e-6
+                          of the first FP64 residual recomputes r with the
+                          FP32 operator instead (a refresh; the Krylov
+                          space is kept); below that level updates are FP64 */
   int max_iter;        /* inner iterations per source (default 20000)      */
   int recon;           /* low-precision links: 12 or 18 (FP16 always 12)   */
   int sites_per_block; /* dslash CTA shape; 0 = autotune                   */
