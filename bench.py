@@ -234,6 +234,20 @@ def other_workloads(sq):
                      "iterations": int(np.mean([s["iterations"] for s in st])),
                      "max_true_residual": max(s["true_residual"] for s in st),
                      "solver": "FP16 inner, " + ("defect correction" if prm.outer else "reliable updates")}
+        # the FP16 clover dslash at this size: one more solve with events
+        # around its launches (algorithmic bytes: links, clover once; every
+        # active source's spinor in and out once)
+        prm_p = sq.sq_solve_params.from_buffer_copy(prm)
+        prm_p.profile = 2
+        sq.sq_solve(ctx, spec["kappa"], spec["csw"], e, x, spec["n_rhs"], TOL, prm_p)
+        row = [r for r in sq.sq_get_profile(ctx) if r["name"] == "dslash_clover"]
+        if row and row[0]["ms"] > 0:
+            hbm, how = peaks()
+            gbs = sum(r["bytes"] for r in row) / (sum(r["ms"] for r in row) / 1000.0) / 1e9
+            out[name]["dslash_f16"] = {"us_per_launch": round(1000.0 * sum(r["ms"] for r in row) /
+                                                              max(1, sum(r["launches"] for r in row)), 2),
+                                       "GB/s": round(gbs, 1), "frac": round(gbs / hbm, 4),
+                                       "peak": hbm, "peak_kind": how}
         del e, x
         sq.sq_destroy(ctx)
     # 96 sources: 16^3x32 and 24^3x48 at kappa 0.118, 0.121, 0.124 in one batch

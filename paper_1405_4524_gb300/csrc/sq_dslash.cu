@@ -365,6 +365,11 @@ void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s) {
   }
 }
 
+bool dslash_tuned(const sq_ctx* c, int prec, int recon, int n) {
+  const long long key = ((long long)prec << 56) ^ ((long long)recon << 48) ^ ((long long)c->Vh << 12) ^ n;
+  return c->tuned.find(key) != c->tuned.end();
+}
+
 // Pick (sites, sources) per CTA by timing the candidates on the call's own
 // fields (no reduction). Results are cached per (precision, recon, Vh, n).
 Shape tune_dslash(sq_ctx* c, DslashCall d, cudaStream_t s) {

@@ -190,6 +190,7 @@ struct DslashCall {
 void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s);
 int dslash_nblk(const sq_ctx* c, Shape sh);
 Shape tune_dslash(sq_ctx* c, DslashCall d, cudaStream_t s);
+bool dslash_tuned(const sq_ctx* c, int prec, int recon, int n);
 
 // ---- solver (sq_solver.cu)
 sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, double* sol, int n,

@@ -982,7 +982,8 @@ static sq_status setup_problem(Prob& p, const sq_solve_params& prm) {
     tcall.in = w.p;
     tcall.p_out = 1;
     tcall.n = n;
-    cudaMemsetAsync(w.p.data, 0, field_bytes(c->Vh, inner, n), s);
+    // defined input for the trial launches (p is overwritten before use)
+    if (!dslash_tuned(c, tcall.prec, tcall.recon, n)) cudaMemsetAsync(w.p.data, 0, field_bytes(c->Vh, inner, n), s);
     p.sh = tune_dslash(c, tcall, s);
   }
   p.recon_in = inner == P64 ? 18 : (inner == P16 ? 12 : c->recon);
