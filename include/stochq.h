@@ -105,7 +105,8 @@ typedef struct sq_solve_params {
                           FP32 operator instead (a refresh; the Krylov
                           space is kept); below that level updates are FP64 */
   int max_iter;        /* inner iterations per source (default 20000)      */
-  int recon;           /* low-precision links: 12 or 18 (FP16 always 12)   */
+  int recon;           /* unused: the FP32 links (which FP16 solves also
+                          hop with) follow sq_load_gauge's recon          */
   int sites_per_block; /* dslash CTA shape; 0 = autotune                   */
   int rhs_per_block;   /* dslash sources per CTA; 0 = autotune             */
   int chunk;           /* iterations per CUDA-graph launch (default 16)    */
@@ -153,8 +154,8 @@ sq_status sq_create(sq_ctx **ctx, const int dims[4], int t_bc, void *cuda_stream
 sq_status sq_destroy(sq_ctx *ctx);
 
 /* Load the gauge field U (host or device, lexicographic FP64, see above).
- * Kept on the device as FP64 reconstruct-18, FP32 reconstruct-`recon`
- * and FP16 reconstruct-12, per-parity site-blocked (the analogue of the
+ * Kept on the device as FP64 reconstruct-18 and FP32 reconstruct-`recon`
+ * (used by the FP32 and the FP16 operator), per-parity site-blocked (the analogue of the
  * array reordering between the paper's host code and its GPU inverter,
  * Sec. "Stochastic propagators"). Drops cached clover terms.
  * Errors: SQ_ERR_ARG (recon not 12/18, NULL), SQ_ERR_NONFINITE,
@@ -164,8 +165,9 @@ sq_status sq_load_gauge(sq_ctx *ctx, const double *U, int recon, int where);
 /* Build the clover term A and its inverse for (kappa, c_sw) on the device
  * in FP64: clover-leaf Fhat (Sec. "Correlation function": c_SW = 1.0 is
  * the paper's tree-level value), A as two 6x6 Hermitian blocks per site in
- * the chiral basis, each inverted in FP64 (partial-pivot Gauss-Jordan);
- * FP32 and FP16 copies of A^{-1} feed the low-precision operator. Up to 8
+ * the chiral basis, each inverted in FP64 (LDL^H; partial-pivot
+ * Gauss-Jordan when a block is not safely positive definite);
+ * an FP32 copy of A^{-1} feeds the FP32 and FP16 operators. Up to 8
  * (kappa, c_sw) pairs are cached; a cached pair is reused.
  * Errors: SQ_ERR_STATE (no gauge), SQ_ERR_ARG (non-finite kappa/c_sw),
  * SQ_ERR_CLOVER (a block is singular: |pivot| < 1e-12 * block scale). */

@@ -81,7 +81,6 @@ static void free_clover(CloverSet& cs) {
   cudaFree(cs.A64);
   cudaFree(cs.Ainv64);
   cudaFree(cs.Ainv32);
-  cudaFree(cs.Ainv16);
   cs = CloverSet();
 }
 
@@ -115,7 +114,6 @@ sq_status find_clover(sq_ctx* c, double kappa, double csw, CloverSet** out) {
   if (!cs.A64) e = cudaMalloc((void**)&cs.A64, 2 * 36 * Vh * sizeof(double2));
   if (e == cudaSuccess && !cs.Ainv64) e = cudaMalloc((void**)&cs.Ainv64, 2 * 36 * Vh * sizeof(double2));
   if (e == cudaSuccess && !cs.Ainv32) e = cudaMalloc((void**)&cs.Ainv32, 2 * 18 * Vh * sizeof(float4));
-  if (e == cudaSuccess && !cs.Ainv16) e = cudaMalloc((void**)&cs.Ainv16, 2 * 9 * Vh * sizeof(uint4));
   if (e != cudaSuccess) {
     free_clover(cs);
     return cuda_check(c, e, "clover allocation");
@@ -211,7 +209,6 @@ sq_status sq_destroy(sq_ctx* c) {
   for (auto& cs : c->clover) free_clover(cs);
   cudaFree(c->U64);
   cudaFree(c->U32);
-  cudaFree(c->U16);
   cudaFree(c->d_err);
   cudaEventDestroy(c->ev);
   cudaStreamDestroy(c->stream);
@@ -239,7 +236,6 @@ sq_status sq_load_gauge(sq_ctx* c, const double* U, int recon, int where) {
   if (!c->U64) e = cudaMalloc((void**)&c->U64, 2 * 4 * 9 * Vh * sizeof(double2));
   if (e == cudaSuccess && !c->U32)
     e = cudaMalloc(&c->U32, recon == 12 ? 2 * 4 * 3 * Vh * sizeof(float4) : 2 * 4 * 9 * Vh * sizeof(float2));
-  if (e == cudaSuccess && !c->U16) e = cudaMalloc((void**)&c->U16, 2 * 4 * 3 * Vh * sizeof(uint2));
   if (e != cudaSuccess) return cuda_check(c, e, "gauge allocation");
   const size_t nd = (size_t)c->V * 4 * 18;
   const double* dU = U;
@@ -368,7 +364,7 @@ sq_status sq_dslash_eo(sq_ctx* c, void* out, const void* in, const void* x, int 
   d.x = make_field((void*)x, c->Vh, prec, n);
   d.p_out = out_parity;
   d.prec = prec;
-  d.recon = prec == SQ_F64 ? 18 : (prec == SQ_F16 ? 12 : c->recon);
+  d.recon = prec == SQ_F64 ? 18 : c->recon;  // FP16 fields use the FP32 links
   d.clover = (flags & SQ_DS_CLOVER_INV) ? 1 : 0;
   d.xpay = (flags & SQ_DS_XPAY) ? 1 : 0;
   d.a = a;

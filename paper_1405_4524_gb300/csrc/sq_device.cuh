@@ -239,7 +239,7 @@ struct SpinorIO<P16> {
 //   FP64 recon-18: double2 [p][mu][9][Vh]
 //   FP32 recon-12: float4  [p][mu][3][Vh]  (complex 2c, 2c+1 of rows 0,1)
 //   FP32 recon-18: float2  [p][mu][9][Vh]
-//   FP16 recon-12: uint2   [p][mu][3][Vh]  (2 x half2 = complex 2c, 2c+1)
+// (FP16 fields are hopped with the FP32 links.)
 // Row-major complex index a*3+b. Reconstruct-12 keeps rows 0 and 1 and
 // rebuilds row 2 = conj(row0 x row1), exact for SU(3).
 // ---------------------------------------------------------------------------
@@ -296,20 +296,6 @@ struct LinkIO<P32, 18> {
   }
 };
 
-template <>
-struct LinkIO<P16, 12> {
-  static __device__ __forceinline__ void load(const void* base, int Vh, int p, int mu, int cb, Link<float>& u) {
-    const uint2* q = (const uint2*)base + ((size_t)(p * 4 + mu) * 3) * Vh + cb;
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-      uint2 a = __ldg(q + (size_t)c * Vh);
-      float2 x = h2f(a.x), y = h2f(a.y);
-      u.e[2 * c] = mk(x.x, x.y);
-      u.e[2 * c + 1] = mk(y.x, y.y);
-    }
-    reconstruct_row2(u);
-  }
-};
 
 // ---------------------------------------------------------------------------
 // clover blocks: per site two 6x6 Hermitian blocks (chirality 0: spins 0,1;
@@ -317,7 +303,7 @@ struct LinkIO<P16, 12> {
 // reals per block: 6 real diagonals, then the 15 strictly-lower entries
 // (i>j, row by row: 10,20,21,30,31,32,40,...,54) as (re, im). 72 reals/site:
 //   FP64: double2 [p][36][Vh]   FP32: float4 [p][18][Vh]
-//   FP16: uint4 (8 halves) [p][9][Vh]
+// (FP16 fields use the FP32 blocks.)
 // ---------------------------------------------------------------------------
 template <int P>
 struct CloverIO;
@@ -352,32 +338,6 @@ struct CloverIO<P32> {
   }
 };
 
-template <>
-struct CloverIO<P16> {
-  // 36 halves per block: block 0 is words 0..17 of the site's 36 half2
-  // words (chunks 0..3 and the low half of chunk 4), block 1 words 18..35
-  template <int CH>
-  static __device__ __forceinline__ void load_block(const void* base, int Vh, int p, int cb, float a[36]) {
-    const uint4* q = (const uint4*)base + ((size_t)p * 9) * Vh + cb;
-    uint32_t w[20];
-    const int c0 = CH == 0 ? 0 : 4;
-#pragma unroll
-    for (int c = 0; c < 5; c++) {
-      uint4 v = __ldg(q + (size_t)(c0 + c) * Vh);
-      w[4 * c] = v.x;
-      w[4 * c + 1] = v.y;
-      w[4 * c + 2] = v.z;
-      w[4 * c + 3] = v.w;
-    }
-    const int off = CH == 0 ? 0 : 2;  // block 1 starts at lane 2 of chunk 4
-#pragma unroll
-    for (int i = 0; i < 18; i++) {
-      float2 f = h2f(w[off + i]);
-      a[2 * i] = f.x;
-      a[2 * i + 1] = f.y;
-    }
-  }
-};
 
 // off-diagonal packed index of (i, j), i > j
 __host__ __device__ constexpr int tri(int i, int j) { return i * (i - 1) / 2 + j; }

@@ -124,6 +124,11 @@ __device__ __forceinline__ void mv_dag(const Link<R>& u, const cx<R> h[6], cx<R>
     }
 }
 
+// precision of the links and clover blocks read by a dslash on fields of
+// precision P: FP16 fields use the FP32 gauge data (per site, shared by the
+// sources of a launch) and save the per-source half -> float conversions
+__host__ __device__ constexpr int gauge_prec(int P) { return P == P16 ? P32 : P; }
+
 template <int P, int RECON, int MU>
 __device__ __forceinline__ void hop_dir(const KArgs& a, int k, int cb, Coord c,
                                         cx<typename Real<P>::T> acc[12]) {
@@ -137,7 +142,7 @@ __device__ __forceinline__ void hop_dir(const KArgs& a, int k, int cb, Coord c,
     else SpinorIO<P>::load(a.in, k, ncb, v);
     project<MU, -1>(v, h);
     Link<R> u;
-    LinkIO<P, RECON>::load(a.links, a.g.Vh, a.p_out, MU, cb, u);
+    LinkIO<gauge_prec(P), RECON>::load(a.links, a.g.Vh, a.p_out, MU, cb, u);
     mv(u, h, w);
     if (P == P16) {  // site norm, and the time-boundary sign
       if (MU == 3 && c.t == a.g.T - 1) f *= (R)a.g.tbc;
@@ -159,7 +164,7 @@ __device__ __forceinline__ void hop_dir(const KArgs& a, int k, int cb, Coord c,
     else SpinorIO<P>::load(a.in, k, ncb, v);
     project<MU, +1>(v, h);
     Link<R> u;
-    LinkIO<P, RECON>::load(a.links, a.g.Vh, 1 - a.p_out, MU, ncb, u);
+    LinkIO<gauge_prec(P), RECON>::load(a.links, a.g.Vh, 1 - a.p_out, MU, ncb, u);
     mv_dag(u, h, w);
     if (P == P16) {  // site norm, and the time-boundary sign
       if (MU == 3 && c.t == 0) f *= (R)a.g.tbc;
@@ -210,11 +215,11 @@ __device__ __forceinline__ void dslash_pass(const KArgs& a, int sb, int slot0, i
     if (CLOV) {
       cx<R> w[6];
       R blk[36];
-      CloverIO<P>::template load_block<0>(a.clov, a.g.Vh, a.p_out, cb, blk);
+      CloverIO<gauge_prec(P)>::template load_block<0>(a.clov, a.g.Vh, a.p_out, cb, blk);
       herm6_apply(blk, acc, w);
 #pragma unroll
       for (int j = 0; j < 6; j++) acc[j] = w[j];
-      CloverIO<P>::template load_block<1>(a.clov, a.g.Vh, a.p_out, cb, blk);
+      CloverIO<gauge_prec(P)>::template load_block<1>(a.clov, a.g.Vh, a.p_out, cb, blk);
       herm6_apply(blk, acc + 6, w);
 #pragma unroll
       for (int j = 0; j < 6; j++) acc[6 + j] = w[j];
@@ -327,10 +332,9 @@ void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s) {
   a.ra = d.ra;
   a.clov = nullptr;
   if (d.clover && d.cs) {
-    a.clov = d.prec == P64 ? (const void*)d.cs->Ainv64
-           : d.prec == P32 ? (const void*)d.cs->Ainv32 : (const void*)d.cs->Ainv16;
+    a.clov = d.prec == P64 ? (const void*)d.cs->Ainv64 : (const void*)d.cs->Ainv32;
   }
-  a.links = d.prec == P64 ? (const void*)c->U64 : d.prec == P32 ? c->U32 : (const void*)c->U16;
+  a.links = d.prec == P64 ? (const void*)c->U64 : c->U32;
   dim3 block(d.shape.sx, d.shape.ry);
   a.nsb = (c->Vh + d.shape.sx - 1) / d.shape.sx;
   a.nrb = (d.n + d.shape.ry - 1) / d.shape.ry;
@@ -348,7 +352,7 @@ void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s) {
     ok = d.recon == 18 ? dispatch_mode<P32, 18>(d, a, grid, block, s)
                        : dispatch_mode<P32, 12>(d, a, grid, block, s);
   } else {
-    ok = dispatch_mode<P16, 12>(d, a, grid, block, s);
+    ok = d.recon == 18 ? dispatch_mode<P16, 18>(d, a, grid, block, s) : dispatch_mode<P16, 12>(d, a, grid, block, s);
   }
   if (!ok) fprintf(stderr, "libstochq: internal error: no dslash variant for this call\n");
   if (d.fin != FIN_NONE) {  // per-source sums and scalars

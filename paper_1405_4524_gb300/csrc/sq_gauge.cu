@@ -20,8 +20,7 @@ namespace sq {
 // ---------------------------------------------------------------------------
 // layout conversion
 // ---------------------------------------------------------------------------
-__global__ void k_gauge_convert(Geom g, const double* lex, double2* U64, void* U32, int recon,
-                                uint2* U16, int* err) {
+__global__ void k_gauge_convert(Geom g, const double* lex, double2* U64, void* U32, int recon, int* err) {
   const long long V = 2LL * g.Vh;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= V * 4) return;
@@ -80,20 +79,13 @@ __global__ void k_gauge_convert(Geom g, const double* lex, double2* U64, void* U
 #pragma unroll
     for (int e = 0; e < 9; e++) q[(base9 + e) * g.Vh + cb] = make_float2((float)u[e].x, (float)u[e].y);
   }
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    uint2 h;
-    h.x = f2h((float)u[2 * c].x, (float)u[2 * c].y);
-    h.y = f2h((float)u[2 * c + 1].x, (float)u[2 * c + 1].y);
-    U16[(base3 + c) * g.Vh + cb] = h;
-  }
 }
 
 sq_status gauge_convert(sq_ctx* c, const double* dev_lex) {
   Geom g = geom_of(c);
   long long n = (long long)c->V * 4;
   k_gauge_convert<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(g, dev_lex, c->U64, c->U32, c->recon,
-                                                                      c->U16, c->d_err);
+                                                                      c->d_err);
   return cuda_check(c, cudaGetLastError(), "gauge conversion launch");
 }
 
@@ -336,7 +328,7 @@ constexpr int kCloverSites = 32;
 
 __global__ void __launch_bounds__(3 * kCloverSites) k_clover(Geom g, const double2* U64, double kappa, double csw,
                                                              double2* A64, double2* Ainv64, float4* Ainv32,
-                                                             uint4* Ainv16, unsigned long long* abound, int* err) {
+                                                             unsigned long long* abound, int* err) {
   __shared__ M3 sG[kCloverSites][2][3];
   const int t = threadIdx.x;
   const int V = 2 * g.Vh;
@@ -434,15 +426,6 @@ __global__ void __launch_bounds__(3 * kCloverSites) k_clover(Geom g, const doubl
   for (int m = 0; m < 9; m++)
     Ainv32[((size_t)p * 18 + 9 * ch + m) * g.Vh + cb] =
         make_float4((float)pi[4 * m], (float)pi[4 * m + 1], (float)pi[4 * m + 2], (float)pi[4 * m + 3]);
-  // FP16: 18 half2 words per block; block 0 = words 0..17, block 1 = 18..35
-  // of the site's 36 words (4 words per uint4 chunk)
-  uint32_t* w16 = (uint32_t*)Ainv16;
-#pragma unroll
-  for (int m = 0; m < 18; m++) {
-    const int word = 18 * ch + m;
-    const size_t chunk = (size_t)p * 9 + (word >> 2);
-    w16[(chunk * g.Vh + cb) * 4 + (word & 3)] = f2h((float)pi[2 * m], (float)pi[2 * m + 1]);
-  }
 }
 
 sq_status clover_build(sq_ctx* c, CloverSet& cs, double kappa, double csw) {
@@ -452,7 +435,7 @@ sq_status clover_build(sq_ctx* c, CloverSet& cs, double kappa, double csw) {
   if (e != cudaSuccess) return cuda_check(c, e, "clover bound alloc");
   cudaMemsetAsync(d_bound, 0, sizeof(unsigned long long), c->stream);
   k_clover<<<(2 * c->Vh + kCloverSites - 1) / kCloverSites, 3 * kCloverSites, 0, c->stream>>>(
-      g, c->U64, kappa, csw, cs.A64, cs.Ainv64, cs.Ainv32, cs.Ainv16, d_bound, c->d_err);
+      g, c->U64, kappa, csw, cs.A64, cs.Ainv64, cs.Ainv32, d_bound, c->d_err);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_check(c, e, "clover launch");
   unsigned long long hb = 0;

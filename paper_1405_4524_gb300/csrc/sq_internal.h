@@ -21,7 +21,6 @@ struct CloverSet {
   double2* A64 = nullptr;     // [2][36][Vh] packed A (FP64)
   double2* Ainv64 = nullptr;  // [2][36][Vh] packed A^{-1} (FP64)
   float4* Ainv32 = nullptr;   // [2][18][Vh]
-  uint4* Ainv16 = nullptr;    // [2][9][Vh]
   double a_bound = 1.0;       // max over sites of a Gershgorin bound on ||A||_2
   int valid = 0;              // built for the current gauge field
   unsigned long long tick = 0;
@@ -125,7 +124,6 @@ struct sq_ctx {
   int su3 = 0;  // links passed the SU(3) check (needed by reconstruct-12)
   double2* U64 = nullptr;  // [2][4][9][Vh]
   void* U32 = nullptr;     // recon 12: float4 [2][4][3][Vh]; 18: float2 [2][4][9][Vh]
-  uint2* U16 = nullptr;    // [2][4][3][Vh]
   // clover cache
   std::vector<sq::CloverSet> clover;
   int cur_clover = -1;

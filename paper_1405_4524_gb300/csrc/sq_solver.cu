@@ -585,7 +585,7 @@ static void launch_iteration(sq_ctx* c, Workspace& w, const CloverSet& cs, doubl
   DslashCall d;
   memset(&d, 0, sizeof(d));
   d.prec = P;
-  d.recon = P == P64 ? 18 : (P == P16 ? 12 : c->recon);
+  d.recon = P == P64 ? 18 : c->recon;  // FP16 fields use the FP32 links
   d.cs = &cs;
   d.list = w.active_list;
   d.count = &w.ctl->n_active;
@@ -771,8 +771,10 @@ struct Cost {
 static Cost class_cost(int kc, int inner, int recon, double Vh, double na, double nu) {
   const double S = inner == P64 ? 192 : inner == P32 ? 96 : 52;  // spinor site
   const double SX = inner == P64 ? 192 : 96;                      // x accumulator
-  const double L = inner == P64 ? 144 : inner == P32 ? (recon == 12 ? 48 : 72) : 24;
-  const double Cl = inner == P64 ? 576 : inner == P32 ? 288 : 144;
+  // links and clover blocks: FP64 for the FP64 operator, FP32 otherwise
+  // (FP16 fields are hopped with the FP32 gauge data)
+  const double L = inner == P64 ? 144 : (recon == 12 ? 48 : 72);
+  const double Cl = inner == P64 ? 576 : 288;
   const double hop = 1320, clv = 504, xpay = 48;  // flops per site and source
   Cost r = {0, 0};
   switch (kc) {
@@ -975,7 +977,7 @@ static sq_status setup_problem(Prob& p, const sq_solve_params& prm) {
     DslashCall tcall;
     memset(&tcall, 0, sizeof(tcall));
     tcall.prec = inner;
-    tcall.recon = inner == P64 ? 18 : (inner == P16 ? 12 : c->recon);
+    tcall.recon = inner == P64 ? 18 : c->recon;
     tcall.cs = p.cs;
     tcall.clover = 1;
     tcall.out = w.to;
@@ -986,7 +988,7 @@ static sq_status setup_problem(Prob& p, const sq_solve_params& prm) {
     if (!dslash_tuned(c, tcall.prec, tcall.recon, n)) cudaMemsetAsync(w.p.data, 0, field_bytes(c->Vh, inner, n), s);
     p.sh = tune_dslash(c, tcall, s);
   }
-  p.recon_in = inner == P64 ? 18 : (inner == P16 ? 12 : c->recon);
+  p.recon_in = inner == P64 ? 18 : c->recon;
   fns_for(inner, &p.iter, &p.upd);
   return SQ_OK;
 }
@@ -1085,10 +1087,8 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
                                       (unsigned long long)p.sh.ry, (unsigned long long)p.sh.order,
                                       (unsigned long long)p.c->recon, (unsigned long long)(uintptr_t)p.w->base,
                                       (unsigned long long)(uintptr_t)p.c->U64, (unsigned long long)(uintptr_t)p.c->U32,
-                                      (unsigned long long)(uintptr_t)p.c->U16,
                                       (unsigned long long)(uintptr_t)p.cs->Ainv64,
                                       (unsigned long long)(uintptr_t)p.cs->Ainv32,
-                                      (unsigned long long)(uintptr_t)p.cs->Ainv16,
                                       (unsigned long long)(uintptr_t)p.w->hist,
                                       (unsigned long long)(uintptr_t)(p.w->pev.empty() ? nullptr : p.w->pev[0]),
                                       (unsigned long long)(uintptr_t)p.s, kb};
