@@ -348,7 +348,6 @@ sq_status sq_dslash_eo(sq_ctx* c, void* out, const void* in, const void* x, int 
   if ((flags & SQ_DS_XPAY) && !x) return set_error(c, SQ_ERR_ARG, "sq_dslash_eo: XPAY needs x");
   if (out == in) return set_error(c, SQ_ERR_ARG, "sq_dslash_eo: in must not alias out");
   if (!c->have_gauge) return set_error(c, SQ_ERR_STATE, "sq_dslash_eo: no gauge field loaded");
-  if (prec == SQ_F16 && !c->su3) return set_error(c, SQ_ERR_ARG, "sq_dslash_eo: FP16 links need SU(3) links");
   const CloverSet* cs = nullptr;
   if (flags & SQ_DS_CLOVER_INV) {
     if (c->cur_clover < 0 || c->cur_clover >= (int)c->clover.size() || !c->clover[c->cur_clover].valid)
@@ -488,8 +487,6 @@ sq_status sq_apply_M(sq_ctx* c, double* out, const double* in, int n, double kap
 sq_status sq_solve(sq_ctx* c, double kappa, double csw, const double* sources, double* solutions, int n,
                    double tol, const sq_solve_params* params, sq_solve_stats* stats) {
   if (!c) return SQ_ERR_ARG;
-  if (params && params->inner_prec == SQ_F16 && c->have_gauge && !c->su3)
-    return set_error(c, SQ_ERR_ARG, "sq_solve: FP16 inner solves need SU(3) links");
   sq_status s = enter_stream(c);
   if (s != SQ_OK) return s;
   s = solve_impl(c, kappa, csw, sources, solutions, n, tol, params, stats);

@@ -876,7 +876,6 @@ static sq_status setup_problem(Prob& p, const sq_solve_params& prm) {
   if (!std::isfinite(p.kappa) || !std::isfinite(p.csw))
     return set_error(c, SQ_ERR_ARG, "sq_solve: non-finite kappa/c_sw");
   if (!c->have_gauge) return set_error(c, SQ_ERR_STATE, "sq_solve: no gauge field loaded");
-  if (inner == P16 && !c->su3) return set_error(c, SQ_ERR_ARG, "sq_solve: FP16 inner solves need SU(3) links");
   sq_status st = find_clover(c, p.kappa, p.csw, &p.cs);
   if (st != SQ_OK) return st;
   st = alloc_ws(c, *p.w, p.n, inner);

@@ -1,6 +1,7 @@
-// Per-source solver state kept on the device, the deterministic
-// "last block finalises" reduction used by every reducing kernel, and the
-// BiCGStab scalar updates that run in those last blocks.
+// Per-source solver state kept on the device, the deterministic reductions
+// (per-warp partials added up by a finishing kernel in the inner loop; a
+// "last block finalises" scheme for the norms) and the BiCGStab scalar
+// updates that run where a source's sums are complete.
 //
 // BiCGStab (van der Vorst 1992) per source k, on the even-odd Schur system
 // Mhat x = bhat:  v = Mhat p; alpha = rho/<rhat,v>; s = r - alpha v;

@@ -221,6 +221,10 @@ def test_nonfinite_source_and_links(small):
 
 
 def test_not_su3_needs_recon18(small):
+    """Links that are not SU(3) are refused for reconstruct-12 and accepted
+    with reconstruct-18; the FP32 and FP16 operators (both hop with the
+    FP32 links) then solve the operator of those links, checked against the
+    oracle's solve on the same links."""
     s, spec, eta, ref = small
     sq = s.sq
     U = 1.01 * s.U
@@ -229,12 +233,15 @@ def test_not_su3_needs_recon18(small):
         with pytest.raises(sq.StochqError) as e:
             sq.sq_load_gauge(ctx, U, 12)
         assert e.value.status == sq.SQ_ERR_ARG
-        sq.sq_load_gauge(ctx, U, 18)  # allowed; FP16 inner is then refused
-        sol = np.zeros_like(eta[:1])
-        with pytest.raises(sq.StochqError) as e:
+        sq.sq_load_gauge(ctx, U, 18)
+        F = oracle.field_strength(U)
+        want, _, res = oracle.solve(U, eta[0], spec["kappa"], spec["csw"], -1.0, tol=1e-13, F=F)
+        assert res <= 1e-13
+        for inner in (1, 2):
+            sol = np.zeros_like(eta[:1])
             sq.sq_solve(ctx, spec["kappa"], spec["csw"], eta[:1], sol, 1, 1e-10,
-                        sq.sq_default_params(inner_prec=2))
-        assert e.value.status == sq.SQ_ERR_ARG
+                        sq.sq_default_params(inner_prec=inner))
+            assert rel(sol[0], want) <= 1e-9
     finally:
         sq.sq_destroy(ctx)
 
