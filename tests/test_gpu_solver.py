@@ -286,6 +286,39 @@ def test_state_and_argument_errors():
         sq.sq_destroy(ctx)
 
 
+@pytest.mark.parametrize("dims", [(2, 2, 2, 4), (2, 4, 2, 6)])
+def test_tiny_lattices(dims):
+    """Fewer sites per parity than a warp (8 and 48): partial warps in
+    every kernel and its reductions; FP32 and FP16 solves match the oracle."""
+    s = Setup(dims, 0.25, 1005)
+    try:
+        eta = inputs.make_z4(dims, 3, 2005)
+        refs = []
+        for k in range(3):
+            ref, _, res = oracle.solve(s.U, eta[k], 0.12, 1.0, -1.0, tol=1e-13, F=s.F)
+            assert res <= 1e-13
+            refs.append(ref)
+        for inner in (1, 2):
+            sol = np.zeros_like(eta)
+            s.sq.sq_solve(s.ctx, 0.12, 1.0, eta, sol, 3, 1e-10, s.sq.sq_default_params(inner_prec=inner))
+            for k in range(3):
+                assert rel(sol[k], refs[k]) <= 1e-9, (inner, k)
+    finally:
+        s.close()
+
+
+def test_empty_and_bad_batches(small):
+    s, spec, eta, ref = small
+    sq = s.sq
+    sol = np.zeros_like(eta)
+    with pytest.raises(sq.StochqError) as e:
+        sq.sq_solve(s.ctx, spec["kappa"], spec["csw"], eta, sol, 0, 1e-10)
+    assert e.value.status == sq.SQ_ERR_ARG
+    with pytest.raises(sq.StochqError) as e:
+        sq.sq_contract_pion(s.ctx, sol, 0)
+    assert e.value.status == sq.SQ_ERR_ARG
+
+
 def test_solve_batch_mixed_lattices_and_kappas():
     """Three problems in one batch: two kappas sharing one lattice and a
     second lattice; every source against the oracle, and the same
