@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "clover dslash HBM GB/s; noise-source solves/sec at 1e-10 rel. residual vs FP64"
+FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (FMA = 2 flops); the FP64 operator is bound by it
 WORKLOAD = "16x16x16x32"
 TOL = 1e-10
 UNIT = "sources/s"
@@ -460,6 +461,29 @@ def main():
             del sol2
         if "sources_per_s" in extras["fp64_solver"]:
             extras["speedup_vs_fp64_solver"] = round(value / world / extras["fp64_solver"]["sources_per_s"], 2)
+        # the FP64 operator alone (hop + A^-1 + xpay on all sources): bound
+        # by the FP64 pipe; CUDA events on the library's ordering stream
+        fb = sq.sq_field_bytes(ctx, sq.SQ_F64, n)
+        bi, bo, bx = (torch.zeros(fb, dtype=torch.uint8, device="cuda") for _ in range(3))
+        flags = sq.SQ_DS_CLOVER_INV | sq.SQ_DS_XPAY
+        for _ in range(2):
+            sq.sq_dslash_eo(ctx, bo, bi, bx, 0, sq.SQ_F64, n, flags, -kappa * kappa)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            sq.sq_dslash_eo(ctx, bo, bi, bx, 0, sq.SQ_F64, n, flags, -kappa * kappa)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / reps
+        vh = int(np.prod(dims)) // 2
+        tflops = n * vh * (1320 + 504 + 48) / (ms64 / 1000.0) / 1e12
+        extras["fp64_operator"] = {"bound": "alu", "achieved": round(tflops, 3), "peak": FP64_PEAK_TFLOPS,
+                                   "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                                   "us_per_launch": round(1000.0 * ms64, 1),
+                                   "flops_per_site_source": 1320 + 504 + 48,
+                                   "peak_kind": "GB300 nominal FP64 rate (an FMA-loop probe measured the same)"}
+        del bi, bo, bx
 
     if args.workloads and rank == 0:
         extras["workloads"] = other_workloads(sq)
