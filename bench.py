@@ -223,8 +223,7 @@ def other_workloads(sq):
         return time.perf_counter() - t0, st
 
     for name, prm in [("24x24x24x48", sq.sq_default_params(inner_prec=sq.SQ_F16)),
-                      ("32x32x32x64", sq.sq_default_params(inner_prec=sq.SQ_F16, outer=sq.SQ_OUTER_DEFECT,
-                                                           delta=1e-3))]:
+                      ("32x32x32x64", sq.sq_default_params(inner_prec=sq.SQ_F16, outer=sq.SQ_OUTER_DEFECT))]:
         spec, U, eta = inputs.workload(name)
         ctx = sq.sq_create(spec["dims"], -1)
         sq.sq_load_gauge(ctx, U, 12)

@@ -98,7 +98,8 @@ typedef struct sq_solve_params {
   double delta;        /* FP64 update when ||r|| < delta * max||r|| since the
                           last update (reliable) or < delta * ||r_start||
                           (defect correction); <= 0 picks the default for
-                          the inner precision (FP32 3e-6, FP16 3e-3);
+                          the inner precision (FP32 3e-6, FP16 3e-3, FP16
+                          with defect correction 1e-4);
                           ignored for SQ_F64. With SQ_F16 and reliable
                           updates, an update while ||r|| is more than 1e-6
                           of the first FP64 residual recomputes r with the

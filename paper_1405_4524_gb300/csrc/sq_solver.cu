@@ -852,10 +852,13 @@ static sq_status validate_params(sq_ctx* c, sq_solve_params& prm) {
   if (prm.io != SQ_HOST && prm.io != SQ_DEVICE) return set_error(c, SQ_ERR_ARG, "sq_solve: bad io");
   if (prm.max_iter <= 0) return set_error(c, SQ_ERR_ARG, "sq_solve: max_iter must be > 0");
   if (!(prm.delta < 1.0)) return set_error(c, SQ_ERR_ARG, "sq_solve: delta must be < 1");
-  // Defaults measured on GB300 (16^3x32, 16 sources): FP32 3e-6 (one FP64
-  // update mid-solve; the full-lattice FP64 check catches any drift of the
-  // iterated residual), FP16 3e-3 (11-bit mantissas drift sooner)
-  if (!(prm.delta > 0.0)) prm.delta = prm.inner_prec == P16 ? 3e-3 : 3e-6;
+  // Defaults measured on GB300: FP32 3e-6 (16^3x32: one FP64 update
+  // mid-solve; the full-lattice FP64 check catches any drift of the
+  // iterated residual), FP16 3e-3 (11-bit mantissas drift sooner; 24^3x48
+  // sweep 2e-3..5e-3), FP16 defect correction 1e-4 (32^3x64 sweep
+  // 1e-4..1e-2: fewest outer cycles for a few more inner iterations)
+  if (!(prm.delta > 0.0))
+    prm.delta = prm.inner_prec == P16 ? (prm.outer == SQ_OUTER_DEFECT ? 1e-4 : 3e-3) : 3e-6;
   if (prm.chunk <= 0) prm.chunk = 16;
   if (prm.chunk > 256) return set_error(c, SQ_ERR_ARG, "sq_solve: chunk must be <= 256");
   if (prm.sites_per_block > 0 || prm.rhs_per_block > 0) {
