@@ -25,6 +25,8 @@ from .dirac import (  # noqa: F401
     inner,
     parity_field,
     pion_correlator,
+    stochastic_operator,
+    stochastic_operator_correlator,
     plaquette_leaves,
     restrict,
     schur_apply,

@@ -40,7 +40,8 @@ and M^{-1} with antiperiodic time momenta, gamma5-hermiticity, gauge
 covariance, a constant abelian background (clover normalisation 1/8, leaf
 orientation, mu<nu bookkeeping), dense LU on tiny lattices (BiCGStab and the
 even-odd formulas), brute-force loops and the exact expectation value for
-the pion contraction. Parity unpinned: the overall sign of the clover term
+the pion contraction and for the stochastic-operator contraction O_ij(t)
+(with O_ii = 0 for X = eta as a special case). Parity unpinned: the overall sign of the clover term
 (+i kappa c_sw) is the Sheikholeslami-Wohlert / Luscher-Sint-Sommer-Weisz
 convention and is fixed by that citation only; no invariant above changes
 when it flips.
@@ -330,3 +331,34 @@ def pion_correlator(psi: np.ndarray, t_src: int = 0) -> np.ndarray:
     T = psi.shape[0]
     per_t = np.sum(np.abs(psi) ** 2, axis=(1, 2, 3, 4, 5))
     return np.array([per_t[(t_src + dt) % T] for dt in range(T)])
+
+
+def stochastic_operator(eta: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """O[t, i, j] = sum over the sites y of timeslice t of
+    eta_i(y)^dag gamma5 X_j(y), spin and colour contracted (Eq. stoop:
+    the operators of the L^3 rearrangement of the pion correlator in
+    Sec. "Stochastic propagators").
+
+    eta, X: (n, T, Z, Y, X, 4, 3) sources and solution vectors; returns a
+    complex (T, n, n) array.
+    """
+    g5X = _spin_all(GAMMA5, X)
+    return np.einsum("itzyxsc,jtzyxsc->tij", np.conj(eta), g5X)
+
+
+def _spin_all(G: np.ndarray, psi: np.ndarray) -> np.ndarray:
+    """(G psi)[..., s, c] = sum_s' G[s, s'] psi[..., s', c]."""
+    return np.einsum("ab,...bc->...ac", G, psi)
+
+
+def stochastic_operator_correlator(O: np.ndarray) -> np.ndarray:
+    """C(dt) = 1/(N_r^2 T) sum_t0 sum_ij O_ij((t0 + dt) mod T) O_ji(t0): the
+    correlator contraction of the operators (Sec. "Stochastic propagators",
+    the equation after Eq. stoop), averaged over the source timeslice t0
+    (every timeslice carries noise for undiluted sources). Complex (T,)."""
+    T, n, _ = O.shape
+    C = np.zeros(T, dtype=np.complex128)
+    for dt in range(T):
+        for t0 in range(T):
+            C[dt] += np.sum(O[(t0 + dt) % T] * O[t0].T)
+    return C / (n * n * T)

@@ -171,3 +171,38 @@ def test_pion_mutation_is_caught(monkeypatch):
     import oracle
     monkeypatch.setattr(oracle, "pion_correlator", _pion_off_by_one)
     assert not _run_pins(["test_pion_correlator_brute_force"])
+
+
+def _stoch_op_no_gamma5(eta, X):
+    return np.einsum("itzyxsc,jtzyxsc->tij", np.conj(eta), X)
+
+
+def _stoch_op_no_conj(eta, X):
+    return np.einsum("itzyxsc,jtzyxsc->tij", eta, dirac._spin_all(dirac.GAMMA5, X))
+
+
+def _stoch_corr_same_t(O):
+    T, n, _ = O.shape
+    C = np.zeros(T, dtype=np.complex128)
+    for dt in range(T):
+        for t0 in range(T):
+            C[dt] += np.sum(O[(t0 + dt) % T] * O[t0])  # O_ij O_ij instead of O_ij O_ji
+    return C / (n * n * T)
+
+
+STOCH_PINS = ["test_stochastic_operator_brute_force", "test_stochastic_operator_of_the_noise_itself",
+              "test_stochastic_operator_estimate_matches_exact"]
+
+
+@pytest.mark.parametrize("kind", ["no_gamma5", "transposed", "no_conj", "corr_same_t"])
+def test_stochastic_operator_mutation_is_caught(kind, monkeypatch):
+    import oracle
+
+    orig = dirac.stochastic_operator
+    attr, fn = {"no_gamma5": ("stochastic_operator", _stoch_op_no_gamma5),
+                "transposed": ("stochastic_operator", lambda e, x: np.transpose(orig(e, x), (0, 2, 1))),
+                "no_conj": ("stochastic_operator", _stoch_op_no_conj),
+                "corr_same_t": ("stochastic_operator_correlator", _stoch_corr_same_t)}[kind]
+    monkeypatch.setattr(dirac, attr, fn)
+    monkeypatch.setattr(oracle, attr, fn)
+    assert not _run_pins(STOCH_PINS), f"mutation not caught: {kind}"

@@ -342,3 +342,97 @@ def test_pion_stochastic_estimate_matches_exact():
     err = Cs.std(axis=0, ddof=1) / np.sqrt(n)
     z = np.abs(mean - exact) / err
     assert np.all(z < 4.0), z
+
+
+# ---------------------------------------------------------------------------
+# Stochastic-operator contraction (Eq. stoop)
+# ---------------------------------------------------------------------------
+
+def test_stochastic_operator_brute_force():
+    """O_ij(t) and its correlator against explicit loops, with gamma5 of the
+    DeGrand-Rossi basis written out as diag(1, 1, -1, -1)."""
+    dims = (2, 2, 2, 4)
+    X, Y, Z, T = dims
+    rng = np.random.default_rng(21)
+    n = 3
+    eta = np.stack([random_spinor(dims, rng) for _ in range(n)])
+    sol = np.stack([random_spinor(dims, rng) for _ in range(n)])
+    O = oracle.stochastic_operator(eta, sol)
+    g5 = [1.0, 1.0, -1.0, -1.0]
+    ref = np.zeros((T, n, n), dtype=np.complex128)
+    for t in range(T):
+        for i in range(n):
+            for j in range(n):
+                acc = 0j
+                for z in range(Z):
+                    for y in range(Y):
+                        for x in range(X):
+                            for s in range(4):
+                                for c in range(3):
+                                    acc += np.conj(eta[i, t, z, y, x, s, c]) * g5[s] * sol[j, t, z, y, x, s, c]
+                ref[t, i, j] = acc
+    assert np.max(np.abs(O - ref)) <= 1e-13 * np.max(np.abs(ref))
+    C = oracle.stochastic_operator_correlator(O)
+    for dt in range(T):
+        acc = 0j
+        for t0 in range(T):
+            for i in range(n):
+                for j in range(n):
+                    acc += ref[(t0 + dt) % T, i, j] * ref[t0, j, i]
+        assert abs(C[dt] - acc / (n * n * T)) <= 1e-13 * abs(acc / (n * n * T))
+
+
+def test_stochastic_operator_of_the_noise_itself():
+    """With X_j = eta_j and Z4 noise the diagonal O_ii(t) vanishes exactly
+    (|eta| = 1 everywhere and gamma5 is traceless over spin), and
+    O_ji(t) = conj(O_ij(t)) (gamma5 is Hermitian)."""
+    dims = (2, 2, 2, 4)
+    eta = inputs.make_z4(dims, 4, 33)
+    O = oracle.stochastic_operator(eta, eta)
+    assert np.all(np.abs(np.einsum("tii->ti", O)) == 0.0)
+    assert np.allclose(O, np.conj(np.transpose(O, (0, 2, 1))), rtol=0, atol=1e-14)
+
+
+def test_stochastic_operator_estimate_matches_exact():
+    """For Z4 noise the i != j terms of O_ij(t0 + dt) O_ji(t0) estimate
+    sum_{x in t0, y in t0+dt} |S(x, y)|_F^2 (gamma5-hermiticity), S = M^{-1}
+    from the dense LU inverse; averaged over t0."""
+    dims = (4, 2, 2, 4)
+    X, Y, Z, T = dims
+    U = inputs.make_links(dims, 0.25, 52)
+    F = oracle.field_strength(U)
+    kappa, csw = 0.12, 1.0
+    M = dense_M(U, F, kappa, csw, -1.0, dims)
+    S = np.linalg.inv(M)
+    nsite = T * Z * Y * X
+    B = np.abs(S.reshape(nsite, 12, nsite, 12)) ** 2
+    blk = B.sum(axis=(1, 3)).reshape(T, Z * Y * X, T, Z * Y * X).sum(axis=(1, 3))  # [t_x, t_y]
+    exact = np.array([np.mean([blk[t0, (t0 + dt) % T] for t0 in range(T)]) for dt in range(T)])
+    n = 40
+    eta = inputs.make_z4(dims, n, 600)
+    sol = (S @ eta.reshape(n, -1).T).T.reshape(eta.shape)
+    O = oracle.stochastic_operator(eta, sol)
+    # per pair (i < j) estimates, symmetrised, averaged over t0
+    est = []
+    for i in range(n):
+        for j in range(i + 1, n):
+            e = [np.mean([O[(t0 + dt) % T, i, j] * O[t0, j, i] + O[(t0 + dt) % T, j, i] * O[t0, i, j]
+                          for t0 in range(T)]) / 2 for dt in range(T)]
+            est.append(np.real(e))
+    est = np.array(est)
+    mean = est.mean(axis=0)
+    err = est.std(axis=0, ddof=1) / np.sqrt(len(est))
+    z = np.abs(mean - exact) / err
+    assert np.all(z < 5.0), (z, mean, exact)
+    # the correlator function (all pairs, i = j included as in the paper's
+    # sum) is the off-diagonal estimate plus the diagonal terms
+    C = oracle.stochastic_operator_correlator(O)
+    off = np.zeros(T, dtype=np.complex128)
+    diag = np.zeros(T, dtype=np.complex128)
+    for dt in range(T):
+        for t0 in range(T):
+            P = O[(t0 + dt) % T] * O[t0].T  # P_ij = O_ij(t0 + dt) O_ji(t0)
+            diag[dt] += np.trace(P) / T
+            off[dt] += (P.sum() - np.trace(P)) / T
+    assert np.allclose(np.real(off) / (n * (n - 1)), mean, rtol=1e-10, atol=0)
+    assert np.allclose(C * n * n, off + diag, rtol=1e-10, atol=0)
