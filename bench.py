@@ -483,6 +483,28 @@ def main():
                                    "flops_per_site_source": 1320 + 504 + 48,
                                    "peak_kind": "GB300 nominal FP64 rate (an FMA-loop probe measured the same)"}
         del bi, bo, bx
+        # the stochastic operators O_ij(t) of all source pairs and their
+        # correlator from the sources and the solutions (Eq. stoop): bound by
+        # the FP64 pipe, three FMAs per complex term (t, i, j, row)
+        O_dev = torch.zeros((T, n, n), dtype=torch.complex128, device="cuda")
+        Cs_dev = torch.zeros(T, dtype=torch.complex128, device="cuda")
+        for _ in range(2):
+            sq.sq_contract_stoch_op(ctx, eta_dev, sol_dev, n, O_dev, Cs_dev)
+        e0.record(stream)
+        for _ in range(reps):
+            sq.sq_contract_stoch_op(ctx, eta_dev, sol_dev, n, O_dev, Cs_dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_so = e0.elapsed_time(e1) / reps
+        terms = float(n) * n * int(np.prod(dims)) * 12
+        tflops = 6.0 * terms / (ms_so / 1000.0) / 1e12
+        extras["stoch_op"] = {"bound": "alu", "achieved": round(tflops, 3), "peak": FP64_PEAK_TFLOPS,
+                              "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                              "us_per_call": round(1000.0 * ms_so, 1), "pairs": n * n,
+                              "complex_terms_per_s": round(terms / (ms_so / 1000.0), 1),
+                              "flops_per_term": 6,
+                              "note": "device I/O, operators and correlator; 3 FP64 FMAs per complex term"}
+        del O_dev, Cs_dev
 
     if args.workloads and rank == 0:
         extras["workloads"] = other_workloads(sq)

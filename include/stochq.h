@@ -293,6 +293,25 @@ sq_status sq_solve_batch(const sq_problem *probs, int n_probs,
 sq_status sq_contract_pion(sq_ctx *ctx, const double *solutions, int n_rhs,
                            const int *src_tslice, double *C, int where);
 
+/* Stochastic operators of Eq. stoop (Sec. "Stochastic propagators"): for
+ * n_rhs noise sources eta_i and their solution vectors X_j = M^-1 eta_j,
+ *   O[t][i][j] = sum over sites y on timeslice t of eta_i(y)^+ gamma5 X_j(y)
+ * (spin and colour contracted, DeGrand-Rossi gamma5 = diag(1,1,-1,-1)),
+ * complex, stored as O[(t*n_rhs + i)*n_rhs + j] = (re, im), T*n_rhs^2
+ * pairs. If C is not NULL it also gets the correlator built from the
+ * operators, averaged over the source timeslice:
+ *   C[dt] = 1/(n_rhs^2 T) sum_t0 sum_{i,j} O_ij((t0+dt) mod T) O_ji(t0),
+ * complex, T pairs (the i = j terms are the biased same-noise products;
+ * they are kept, as in the formula). eta, X: lexicographic FP64 fields of
+ * n_rhs vectors as sq_solve takes them. eta, X, O and C are all host or
+ * all device memory per `where`; the caller owns them. FP64 throughout,
+ * summed in a fixed order (bitwise reproducible for the same inputs and
+ * device). Synchronises the context's stream before returning.
+ * Errors: SQ_ERR_ARG (NULL eta/X/O, n_rhs <= 0 or > 4080, bad where),
+ * SQ_ERR_CUDA. */
+sq_status sq_contract_stoch_op(sq_ctx *ctx, const double *eta, const double *X,
+                               int n_rhs, double *O, double *C, int where);
+
 /* Per kernel class of the solver's inner loop (profiling). */
 typedef struct sq_kernel_stat {
   char name[48];       /* kernel class, e.g. "dslash_clover"              */

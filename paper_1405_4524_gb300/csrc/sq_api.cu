@@ -525,6 +525,50 @@ sq_status sq_contract_pion(sq_ctx* c, const double* sol, int n, const int* tsl, 
   return leave_stream(c);
 }
 
+sq_status sq_contract_stoch_op(sq_ctx* c, const double* eta, const double* X, int n, double* O, double* C,
+                               int where) {
+  if (!c) return SQ_ERR_ARG;
+  if (!eta || !X || !O || n <= 0 || n > 4080 || (where != SQ_HOST && where != SQ_DEVICE))
+    return set_error(c, SQ_ERR_ARG, "sq_contract_stoch_op: bad argument");
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  const double *deta, *dX;
+  double *teta, *tX = nullptr;
+  s = stage_in(c, eta, n, where, &deta, &teta);
+  if (s == SQ_OK) s = stage_in(c, X, n, where, &dX, &tX);
+  if (s != SQ_OK) {
+    if (teta) cudaFreeAsync(teta, c->stream);
+    return s;
+  }
+  const int T = c->dims[3];
+  const int nkg = stoch_groups(c, n);
+  const size_t ob = (size_t)T * n * n * 2 * sizeof(double), cb = (size_t)T * 2 * sizeof(double);
+  double *part = nullptr, *dO = O, *dC = C;
+  cudaError_t e = cudaMallocAsync((void**)&part, ob * nkg, c->stream);
+  if (e == cudaSuccess && where == SQ_HOST) e = cudaMallocAsync((void**)&dO, ob, c->stream);
+  if (e == cudaSuccess && where == SQ_HOST && C) e = cudaMallocAsync((void**)&dC, cb, c->stream);
+  if (e == cudaSuccess) {
+    launch_stoch_op(c, deta, dX, n, dO, dC, part, nkg, c->stream);
+    c->launches += C ? 3 : 2;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && where == SQ_HOST) {
+    e = cudaMemcpyAsync(O, dO, ob, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && C) e = cudaMemcpyAsync(C, dC, cb, cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (part) cudaFreeAsync(part, c->stream);
+  if (where == SQ_HOST) {
+    if (dO) cudaFreeAsync(dO, c->stream);
+    if (C && dC) cudaFreeAsync(dC, c->stream);
+  }
+  if (teta) cudaFreeAsync(teta, c->stream);
+  if (tX) cudaFreeAsync(tX, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  s = cuda_check(c, e, "sq_contract_stoch_op");
+  if (s != SQ_OK) return s;
+  return leave_stream(c);
+}
+
 sq_status sq_get_profile(const sq_ctx* c, sq_kernel_stat* out, int max, int* n) {
   static const char* names[KC_N] = {
       "dslash_clover",         "dslash_clover_xpay_alpha", "blas_s_update",

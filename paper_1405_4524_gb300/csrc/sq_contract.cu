@@ -42,4 +42,146 @@ void launch_pion(const sq_ctx* c, const double* lex, int n, const int* tsl, doub
   k_pion<<<grid, 256, 0, s>>>((const double2*)lex, slice2, T, tsl, C);
 }
 
+// ---------------------------------------------------------------------------
+// Stochastic-operator contraction (Eq. stoop): per timeslice t the complex
+// n x n matrix O(t) = H(t)^+ G(t), H = [eta_1 .. eta_n], G = gamma5 [X_1 ..
+// X_n], K = X*Y*Z*12 rows (the sites of the slice times spin-colour). With
+// a = eta_i(y), b = (gamma5 X_j)(y), every term conj(a) b is formed from three
+// real products (the three-multiplication form of a complex product):
+//   P1 += ar br,  P2 += ai bi,  P3 += (ar - ai)(br + bi),
+//   Re O = P1 + P2,  Im O = P3 - P1 + P2,
+// so the contraction costs 3 FP64 FMAs per term instead of 4; the sums
+// ar - ai and br + bi are formed once per row element when it is staged,
+// shared by the 16 pairs of a tile row. GB300's FP64 rate bounds it.
+//
+// k_stoch_partial: CTA (t, kg, tile) sums the rows of its K-range for a
+// 16 x 16 tile of (i, j) pairs, one pair per thread. The K-range is walked
+// in chunks of kStochChunk rows (whole sites, so the gamma5 sign of a row
+// position is fixed: spins 0, 1 are rows 0..5 of a site, spins 2, 3 rows
+// 6..11; the sign is applied to b when it is staged). The K-group partials
+// are added in a fixed order by k_stoch_sum (bitwise reproducible).
+// ---------------------------------------------------------------------------
+constexpr int kStochTile = 16;
+constexpr int kStochChunk = 48;            // rows per chunk: 4 sites x 12
+constexpr int kStochPitch = kStochChunk + 1;  // odd pitch: the 16 rows of a tile fall in 16 banks
+
+__global__ void __launch_bounds__(256) k_stoch_partial(const double2* eta, const double2* X, int n, int T,
+                                                       long long slice2, int nkg, double2* part) {
+  __shared__ double a_r[kStochTile][kStochPitch], a_i[kStochTile][kStochPitch], a_d[kStochTile][kStochPitch];
+  __shared__ double b_r[kStochTile][kStochPitch], b_i[kStochTile][kStochPitch], b_s[kStochTile][kStochPitch];
+  const int t = blockIdx.x, kg = blockIdx.y;
+  const int ntile = (n + kStochTile - 1) / kStochTile;
+  const int ti = blockIdx.z / ntile, tj = blockIdx.z - ti * ntile;
+  const int li = threadIdx.x / kStochTile, lj = threadIdx.x - li * kStochTile;
+  const int i = ti * kStochTile + li, j = tj * kStochTile + lj;
+  const long long nchunk = (slice2 + kStochChunk - 1) / kStochChunk;
+  const long long c0 = nchunk * kg / nkg, c1 = nchunk * (kg + 1) / nkg;
+  double P1 = 0, P2 = 0, P3 = 0;
+  for (long long c = c0; c < c1; c++) {
+    const long long r0 = c * kStochChunk;
+    __syncthreads();
+    for (int e = threadIdx.x; e < 2 * kStochTile * kStochChunk; e += blockDim.x) {
+      const int which = e / (kStochTile * kStochChunk);
+      const int rem = e - which * kStochTile * kStochChunk;
+      const int row = rem / kStochChunk, q = rem - row * kStochChunk;
+      const int src = (which == 0 ? ti : tj) * kStochTile + row;
+      double2 v = make_double2(0.0, 0.0);
+      if (src < n && r0 + q < slice2) v = (which == 0 ? eta : X)[((long long)src * T + t) * slice2 + r0 + q];
+      if (which == 0) {
+        a_r[row][q] = v.x;
+        a_i[row][q] = v.y;
+        a_d[row][q] = v.x - v.y;
+      } else {
+        if ((q % 12) >= 6) v = make_double2(-v.x, -v.y);  // gamma5 on spins 2, 3
+        b_r[row][q] = v.x;
+        b_i[row][q] = v.y;
+        b_s[row][q] = v.x + v.y;
+      }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int q = 0; q < kStochChunk; q++) {
+      P1 = fma(a_r[li][q], b_r[lj][q], P1);
+      P2 = fma(a_i[li][q], b_i[lj][q], P2);
+      P3 = fma(a_d[li][q], b_s[lj][q], P3);
+    }
+  }
+  if (i < n && j < n) part[(((long long)t * nkg + kg) * n + i) * n + j] = make_double2(P1 + P2, P3 - P1 + P2);
+}
+
+// O[t][i][j] = sum over K-groups in order
+__global__ void k_stoch_sum(const double2* part, int n, int T, int nkg, double2* O) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)T * n * n;
+  if (idx >= total) return;
+  const long long t = idx / ((long long)n * n), ij = idx - t * n * n;
+  double re = 0, im = 0;
+  for (int kg = 0; kg < nkg; kg++) {
+    const double2 v = part[(t * nkg + kg) * n * n + ij];
+    re += v.x;
+    im += v.y;
+  }
+  O[idx] = make_double2(re, im);
+}
+
+// C[dt] = 1/(n^2 T) sum_t0 sum_ij O_ij((t0 + dt) mod T) O_ji(t0); one CTA per
+// dt, fixed-order tree
+__global__ void __launch_bounds__(256) k_stoch_corr(const double2* O, int n, int T, double2* C) {
+  const int dt = blockIdx.x;
+  double re = 0, im = 0;
+  const long long nn = (long long)n * n;
+  for (long long e = threadIdx.x; e < (long long)T * nn; e += blockDim.x) {
+    const int t0 = (int)(e / nn);
+    const long long ij = e - (long long)t0 * nn;
+    const int i = (int)(ij / n), j = (int)(ij - (long long)i * n);
+    const double2 a = O[((long long)((t0 + dt) % T)) * nn + (long long)i * n + j];
+    const double2 b = O[(long long)t0 * nn + (long long)j * n + i];
+    re += a.x * b.x - a.y * b.y;
+    im += a.x * b.y + a.y * b.x;
+  }
+  __shared__ double sr[8], si[8];
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if ((threadIdx.x & 31) == 0) {
+    sr[threadIdx.x >> 5] = re;
+    si[threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      a += sr[w];
+      b += si[w];
+    }
+    const double f = 1.0 / ((double)n * n * T);
+    C[dt] = make_double2(a * f, b * f);
+  }
+}
+
+// K-groups per timeslice: enough CTAs to fill the GPU about four times
+int stoch_groups(const sq_ctx* c, int n) {
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const int T = c->dims[3];
+  const int ntile = (n + kStochTile - 1) / kStochTile;
+  const long long slice2 = (long long)c->dims[0] * c->dims[1] * c->dims[2] * 12;
+  const long long nchunk = (slice2 + kStochChunk - 1) / kStochChunk;
+  long long g = (4LL * sms + (long long)T * ntile * ntile - 1) / ((long long)T * ntile * ntile);
+  if (g < 1) g = 1;
+  if (g > nchunk) g = nchunk;
+  return (int)g;
+}
+
+void launch_stoch_op(const sq_ctx* c, const double* eta, const double* X, int n, double* O, double* C, double* part,
+                     int nkg, cudaStream_t s) {
+  const int T = c->dims[3];
+  const long long slice2 = (long long)c->dims[0] * c->dims[1] * c->dims[2] * 12;
+  const int ntile = (n + kStochTile - 1) / kStochTile;
+  k_stoch_partial<<<dim3(T, nkg, ntile * ntile), 256, 0, s>>>((const double2*)eta, (const double2*)X, n, T, slice2,
+                                                              nkg, (double2*)part);
+  const long long total = (long long)T * n * n;
+  k_stoch_sum<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((const double2*)part, n, T, nkg, (double2*)O);
+  if (C) k_stoch_corr<<<T, 256, 0, s>>>((const double2*)O, n, T, (double2*)C);
+}
+
 }  // namespace sq

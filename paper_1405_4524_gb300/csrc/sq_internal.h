@@ -200,5 +200,8 @@ void release_workspace(sq_ctx* c);
 
 // ---- contraction (sq_contract.cu)
 void launch_pion(const sq_ctx* c, const double* lex, int n, const int* tsl, double* C, cudaStream_t s);
+int stoch_groups(const sq_ctx* c, int n);
+void launch_stoch_op(const sq_ctx* c, const double* eta, const double* X, int n, double* O, double* C, double* part,
+                     int nkg, cudaStream_t s);
 
 }  // namespace sq

@@ -97,6 +97,7 @@ _SIG = {
     "sq_solve_batch": (_i, [C.POINTER(sq_problem), _i, C.POINTER(sq_solve_params),
                             C.POINTER(sq_solve_stats)]),
     "sq_contract_pion": (_i, [_vp, _vp, _i, _vp, _vp, _i]),
+    "sq_contract_stoch_op": (_i, [_vp, _vp, _vp, _i, _vp, _vp, _i]),
     "sq_get_profile": (_i, [_vp, C.POINTER(sq_kernel_stat), _i, C.POINTER(_i)]),
     "sq_kernel_launches": (_i, [_vp, C.POINTER(C.c_longlong)]),
     "sq_status_string": (C.c_char_p, [_i]),
@@ -324,6 +325,37 @@ def sq_contract_pion(ctx, solutions, n_rhs: int, src_tslice=None) -> np.ndarray:
     _check(ctx, _lib.sq_contract_pion(ctx, _ptr(solutions), int(n_rhs), _ptr(ts), _ptr(Cout),
                                       _where(solutions)))
     return Cout
+
+
+def sq_contract_stoch_op(ctx, eta, X, n_rhs: int, O=None, C=None, correlator: bool = True):
+    """Operators O (T, n, n) complex128 and, if correlator, C (T,) complex128.
+
+    eta, X: (n, T, Z, Y, X, 4, 3) float64 (or complex128 with the last axis
+    folded) arrays, both on the host or both CUDA tensors. Outputs are
+    allocated like the inputs when not given."""
+    where = _where(eta)
+    if _where(X) != where:
+        raise ValueError("eta and X must both be host arrays or both device tensors")
+    T = int(eta.shape[1])
+    n = int(n_rhs)
+    if where == SQ_HOST:
+        if O is None:
+            O = np.zeros((T, n, n), dtype=np.complex128)
+        if correlator and C is None:
+            C = np.zeros(T, dtype=np.complex128)
+    else:
+        import torch
+        if O is None:
+            O = torch.zeros((T, n, n), dtype=torch.complex128, device=eta.device)
+        if correlator and C is None:
+            C = torch.zeros(T, dtype=torch.complex128, device=eta.device)
+    if not correlator:
+        C = None
+    for a in (O, C):
+        if a is not None and _where(a) != where:
+            raise ValueError("O and C must live where eta and X do")
+    _check(ctx, _lib.sq_contract_stoch_op(ctx, _ptr(eta), _ptr(X), n, _ptr(O), _ptr(C), where))
+    return O, C
 
 
 def sq_get_profile(ctx):
