@@ -306,7 +306,10 @@ sq_status sq_contract_pion(sq_ctx *ctx, const double *solutions, int n_rhs,
  * n_rhs vectors as sq_solve takes them. eta, X, O and C are all host or
  * all device memory per `where`; the caller owns them. FP64 throughout,
  * summed in a fixed order (bitwise reproducible for the same inputs and
- * device). Synchronises the context's stream before returning.
+ * device). Host memory: returns when O and C are written. Device memory:
+ * ordered after the caller's stream and returns without waiting. The
+ * context keeps a partial-sum buffer of T * n_rhs^2 * 16 bytes times the
+ * number of K-groups (at most 4 CTAs per SM) between calls.
  * Errors: SQ_ERR_ARG (NULL eta/X/O, n_rhs <= 0 or > 4080, bad where),
  * SQ_ERR_CUDA. */
 sq_status sq_contract_stoch_op(sq_ctx *ctx, const double *eta, const double *X,

@@ -210,6 +210,7 @@ sq_status sq_destroy(sq_ctx* c) {
   cudaFree(c->U64);
   cudaFree(c->U32);
   cudaFree(c->d_err);
+  cudaFree(c->stoch_part);
   cudaEventDestroy(c->ev);
   cudaStreamDestroy(c->stream);
   delete c;
@@ -532,6 +533,22 @@ sq_status sq_contract_stoch_op(sq_ctx* c, const double* eta, const double* X, in
     return set_error(c, SQ_ERR_ARG, "sq_contract_stoch_op: bad argument");
   sq_status s = enter_stream(c);
   if (s != SQ_OK) return s;
+  const int T = c->dims[3];
+  const int nkg = stoch_groups(c, n);
+  const size_t ob = (size_t)T * n * n * 2 * sizeof(double), cb = (size_t)T * 2 * sizeof(double);
+  // the partials live in a context buffer kept between calls (grown on demand)
+  cudaError_t e = cudaSuccess;
+  if (c->stoch_cap < ob * nkg) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) {
+      cudaFree(c->stoch_part);
+      c->stoch_part = nullptr;
+      c->stoch_cap = 0;
+      e = cudaMalloc(&c->stoch_part, ob * nkg);
+      if (e == cudaSuccess) c->stoch_cap = ob * nkg;
+    }
+    if (e != cudaSuccess) return cuda_check(c, e, "sq_contract_stoch_op scratch");
+  }
   const double *deta, *dX;
   double *teta, *tX = nullptr;
   s = stage_in(c, eta, n, where, &deta, &teta);
@@ -540,30 +557,25 @@ sq_status sq_contract_stoch_op(sq_ctx* c, const double* eta, const double* X, in
     if (teta) cudaFreeAsync(teta, c->stream);
     return s;
   }
-  const int T = c->dims[3];
-  const int nkg = stoch_groups(c, n);
-  const size_t ob = (size_t)T * n * n * 2 * sizeof(double), cb = (size_t)T * 2 * sizeof(double);
-  double *part = nullptr, *dO = O, *dC = C;
-  cudaError_t e = cudaMallocAsync((void**)&part, ob * nkg, c->stream);
-  if (e == cudaSuccess && where == SQ_HOST) e = cudaMallocAsync((void**)&dO, ob, c->stream);
-  if (e == cudaSuccess && where == SQ_HOST && C) e = cudaMallocAsync((void**)&dC, cb, c->stream);
+  double *dO = O, *dC = C;
+  if (where == SQ_HOST) {
+    e = cudaMallocAsync((void**)&dO, ob, c->stream);
+    if (e == cudaSuccess && C) e = cudaMallocAsync((void**)&dC, cb, c->stream);
+  }
   if (e == cudaSuccess) {
-    launch_stoch_op(c, deta, dX, n, dO, dC, part, nkg, c->stream);
+    launch_stoch_op(c, deta, dX, n, dO, dC, (double*)c->stoch_part, nkg, c->stream);
     c->launches += C ? 3 : 2;
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess && where == SQ_HOST) {
-    e = cudaMemcpyAsync(O, dO, ob, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess && C) e = cudaMemcpyAsync(C, dC, cb, cudaMemcpyDeviceToHost, c->stream);
-  }
-  if (part) cudaFreeAsync(part, c->stream);
   if (where == SQ_HOST) {
-    if (dO) cudaFreeAsync(dO, c->stream);
-    if (C && dC) cudaFreeAsync(dC, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(O, dO, ob, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && C) e = cudaMemcpyAsync(C, dC, cb, cudaMemcpyDeviceToHost, c->stream);
+    if (dO && dO != O) cudaFreeAsync(dO, c->stream);
+    if (C && dC && dC != C) cudaFreeAsync(dC, c->stream);
+    if (teta) cudaFreeAsync(teta, c->stream);
+    if (tX) cudaFreeAsync(tX, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   }
-  if (teta) cudaFreeAsync(teta, c->stream);
-  if (tX) cudaFreeAsync(tX, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   s = cuda_check(c, e, "sq_contract_stoch_op");
   if (s != SQ_OK) return s;
   return leave_stream(c);

@@ -65,8 +65,30 @@ constexpr int kStochTile = 16;
 constexpr int kStochChunk = 48;            // rows per chunk: 4 sites x 12
 constexpr int kStochPitch = kStochChunk + 1;  // odd pitch: the 16 rows of a tile fall in 16 banks
 
-__global__ void __launch_bounds__(256) k_stoch_partial(const double2* eta, const double2* X, int n, int T,
-                                                       long long slice2, int nkg, double2* part) {
+__device__ __forceinline__ double flip_sign(double v) {
+  return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ULL);
+}
+
+// The 2 x 16 x 48 elements of a chunk's tile rows, 6 per thread: element
+// k < 3 is an eta row entry, k >= 3 the X row entry at the same tile
+// position. ea / xa point at the tile's first row in chunk r0 = 0, stride is
+// the distance between sources, ne / nx the number of rows of the tiles
+// that exist. A slice holds X*Y*Z*12 rows, a multiple of 96 for even
+// extents, so a chunk never runs past its slice.
+__device__ __forceinline__ void stoch_fetch(double2 (&v)[6], const double2* ea, const double2* xa, long long stride,
+                                            int ne, int nx, long long r0) {
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const int rem = (int)threadIdx.x + 256 * k;
+    const int row = rem / kStochChunk, q = rem - row * kStochChunk;
+    const long long o = row * stride + r0 + q;
+    v[k] = row < ne ? ea[o] : make_double2(0.0, 0.0);
+    v[k + 3] = row < nx ? xa[o] : make_double2(0.0, 0.0);
+  }
+}
+
+__global__ void __launch_bounds__(256, 4) k_stoch_partial(const double2* eta, const double2* X, int n, int T,
+                                                          long long slice2, int nkg, double2* part) {
   __shared__ double a_r[kStochTile][kStochPitch], a_i[kStochTile][kStochPitch], a_d[kStochTile][kStochPitch];
   __shared__ double b_r[kStochTile][kStochPitch], b_i[kStochTile][kStochPitch], b_s[kStochTile][kStochPitch];
   const int t = blockIdx.x, kg = blockIdx.y;
@@ -77,28 +99,33 @@ __global__ void __launch_bounds__(256) k_stoch_partial(const double2* eta, const
   const long long nchunk = (slice2 + kStochChunk - 1) / kStochChunk;
   const long long c0 = nchunk * kg / nkg, c1 = nchunk * (kg + 1) / nkg;
   double P1 = 0, P2 = 0, P3 = 0;
+  const long long stride = (long long)T * slice2;
+  const double2* ea = eta + (long long)ti * kStochTile * stride + (long long)t * slice2;
+  const double2* xa = X + (long long)tj * kStochTile * stride + (long long)t * slice2;
+  const int ne = min(kStochTile, n - ti * kStochTile), nx = min(kStochTile, n - tj * kStochTile);
+  double2 v[6];
+  if (c0 < c1) stoch_fetch(v, ea, xa, stride, ne, nx, c0 * kStochChunk);
   for (long long c = c0; c < c1; c++) {
-    const long long r0 = c * kStochChunk;
-    __syncthreads();
-    for (int e = threadIdx.x; e < 2 * kStochTile * kStochChunk; e += blockDim.x) {
-      const int which = e / (kStochTile * kStochChunk);
-      const int rem = e - which * kStochTile * kStochChunk;
+    __syncthreads();  // the previous chunk's products are done
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const int rem = (int)threadIdx.x + 256 * (k % 3);
       const int row = rem / kStochChunk, q = rem - row * kStochChunk;
-      const int src = (which == 0 ? ti : tj) * kStochTile + row;
-      double2 v = make_double2(0.0, 0.0);
-      if (src < n && r0 + q < slice2) v = (which == 0 ? eta : X)[((long long)src * T + t) * slice2 + r0 + q];
-      if (which == 0) {
-        a_r[row][q] = v.x;
-        a_i[row][q] = v.y;
-        a_d[row][q] = v.x - v.y;
+      if (k < 3) {
+        a_r[row][q] = v[k].x;
+        a_i[row][q] = v[k].y;
+        a_d[row][q] = v[k].x - v[k].y;
       } else {
-        if ((q % 12) >= 6) v = make_double2(-v.x, -v.y);  // gamma5 on spins 2, 3
-        b_r[row][q] = v.x;
-        b_i[row][q] = v.y;
-        b_s[row][q] = v.x + v.y;
+        const double sum = v[k].x + v[k].y;
+        const bool lower = (q % 12) >= 6;  // gamma5 = -1 on spins 2, 3
+        b_r[row][q] = lower ? flip_sign(v[k].x) : v[k].x;
+        b_i[row][q] = lower ? flip_sign(v[k].y) : v[k].y;
+        b_s[row][q] = lower ? flip_sign(sum) : sum;
       }
     }
     __syncthreads();
+    // the next chunk's loads are in flight during this chunk's products
+    if (c + 1 < c1) stoch_fetch(v, ea, xa, stride, ne, nx, (c + 1) * kStochChunk);
 #pragma unroll 8
     for (int q = 0; q < kStochChunk; q++) {
       P1 = fma(a_r[li][q], b_r[lj][q], P1);
@@ -130,14 +157,15 @@ __global__ void __launch_bounds__(256) k_stoch_corr(const double2* O, int n, int
   const int dt = blockIdx.x;
   double re = 0, im = 0;
   const long long nn = (long long)n * n;
-  for (long long e = threadIdx.x; e < (long long)T * nn; e += blockDim.x) {
-    const int t0 = (int)(e / nn);
-    const long long ij = e - (long long)t0 * nn;
+  for (long long ij = threadIdx.x; ij < nn; ij += blockDim.x) {
     const int i = (int)(ij / n), j = (int)(ij - (long long)i * n);
-    const double2 a = O[((long long)((t0 + dt) % T)) * nn + (long long)i * n + j];
-    const double2 b = O[(long long)t0 * nn + (long long)j * n + i];
-    re += a.x * b.x - a.y * b.y;
-    im += a.x * b.y + a.y * b.x;
+    const long long ji = (long long)j * n + i;
+    for (int t0 = 0, t1 = dt; t0 < T; t0++, t1 = (t1 + 1 == T ? 0 : t1 + 1)) {
+      const double2 a = O[t1 * nn + ij];
+      const double2 b = O[t0 * nn + ji];
+      re += a.x * b.x - a.y * b.y;
+      im += a.x * b.y + a.y * b.x;
+    }
   }
   __shared__ double sr[8], si[8];
   re = warp_sum(re);

@@ -139,6 +139,8 @@ struct sq_ctx {
   int prof_valid = 0;
   int prof_inner = 0;
   sq::KStat prof[sq::KC_N];        // per-class totals of the last profiled solve
+  void* stoch_part = nullptr;      // K-group partials of the stochastic operators
+  size_t stoch_cap = 0;            // bytes held by stoch_part
 };
 
 namespace sq {
