@@ -504,7 +504,27 @@ def main():
                               "complex_terms_per_s": round(terms / (ms_so / 1000.0), 1),
                               "flops_per_term": 6,
                               "note": "device I/O, operators and correlator; 3 FP64 FMAs per complex term"}
-        del O_dev, Cs_dev
+        # the trace of the filled stochastic propagators (Eq. Sfill, Table Lcomp's
+        # sum_x sum_z tr S S^dag for every source and sink timeslice) through
+        # two Gram matrices per timeslice instead of the fill: FP64-pipe bound
+        Cp_dev = torch.zeros((T, T), dtype=torch.complex128, device="cuda")
+        for _ in range(2):
+            sq.sq_contract_prop_trace(ctx, eta_dev, sol_dev, n, C=Cp_dev)
+        e0.record(stream)
+        for _ in range(reps):
+            sq.sq_contract_prop_trace(ctx, eta_dev, sol_dev, n, C=Cp_dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_pt = e0.elapsed_time(e1) / reps
+        tflops = 2 * 6.0 * terms / (ms_pt / 1000.0) / 1e12
+        fill_cmul = 144.0 * (int(np.prod(dims[:3])) ** 2) * T * T * n  # complex multiplies of the fill route
+        extras["prop_trace"] = {"bound": "alu", "achieved": round(tflops, 3), "peak": FP64_PEAK_TFLOPS,
+                                "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                                "us_per_call": round(1000.0 * ms_pt, 1), "source_sets": 1,
+                                "fill_route_complex_multiplies": fill_cmul,
+                                "note": "device I/O; C[t0][t] for all T^2 pairs from two Gram matrices per "
+                                        "timeslice, 3 FP64 FMAs per complex term"}
+        del O_dev, Cs_dev, Cp_dev
 
     if args.workloads and rank == 0:
         extras["workloads"] = other_workloads(sq)

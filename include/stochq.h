@@ -315,6 +315,29 @@ sq_status sq_contract_pion(sq_ctx *ctx, const double *solutions, int n_rhs,
 sq_status sq_contract_stoch_op(sq_ctx *ctx, const double *eta, const double *X,
                                int n_rhs, double *O, double *C, int where);
 
+/* Traces of filled stochastic propagators without the fill (Eq. Sfill and
+ * the "sum_x sum_z tr S_s S_s^+" entry of Table Lcomp, Sec. "Stochastic
+ * propagators"): with S_A(t,z; t0,x) = (1/n_rhs) sum_i XA_i(t,z) etaA_i(t0,x)^+
+ * and S_B likewise from the second set (etaB, XB),
+ *   C[t0][t] = sum over source sites x on timeslice t0 and sink sites z on
+ *              timeslice t of tr[S_A(t,z; t0,x) S_B(t,z; t0,x)^+]
+ * (spin-colour trace), complex, T*T pairs, C[(t0*T + t)] = (re, im).
+ * Computed as (1/n_rhs^2) tr[P(t) Q(t0)] with the Gram matrices
+ * P_ji(t) = sum_{z in t} XB_j(z)^+ XA_i(z) and Q_ij(t0) = sum_{x in t0}
+ * etaA_i(x)^+ etaB_j(x), so S (12*12*T*V_3^2 entries per t0) is never
+ * formed. etaB = XB = NULL uses one set for both propagators (the paper's
+ * correlated option; the i = j terms are kept as the formula has them).
+ * Fields: lexicographic FP64, n_rhs vectors each, as sq_solve takes them;
+ * all inputs and C host or all device memory per `where`; the caller owns
+ * them. FP64, fixed summation order. Host memory: returns when C is
+ * written; device memory: ordered after the caller's stream, no wait. Uses
+ * the context's contraction buffer (2 + K-groups) * T * n_rhs^2 * 16 bytes.
+ * Errors: SQ_ERR_ARG (NULL etaA/XA/C, only one of etaB/XB given,
+ * n_rhs <= 0 or > 4080, bad where), SQ_ERR_CUDA. */
+sq_status sq_contract_prop_trace(sq_ctx *ctx, const double *etaA, const double *XA,
+                                 const double *etaB, const double *XB, int n_rhs,
+                                 double *C, int where);
+
 /* Per kernel class of the solver's inner loop (profiling). */
 typedef struct sq_kernel_stat {
   char name[48];       /* kernel class, e.g. "dslash_clover"              */

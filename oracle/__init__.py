@@ -25,8 +25,11 @@ from .dirac import (  # noqa: F401
     inner,
     parity_field,
     pion_correlator,
+    propagator_trace,
     stochastic_operator,
     stochastic_operator_correlator,
+    stochastic_propagator,
+    stochastic_propagator_trace,
     plaquette_leaves,
     restrict,
     schur_apply,

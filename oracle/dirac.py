@@ -41,7 +41,9 @@ covariance, a constant abelian background (clover normalisation 1/8, leaf
 orientation, mu<nu bookkeeping), dense LU on tiny lattices (BiCGStab and the
 even-odd formulas), brute-force loops and the exact expectation value for
 the pion contraction and for the stochastic-operator contraction O_ij(t)
-(with O_ii = 0 for X = eta as a special case). Parity unpinned: the overall sign of the clover term
+(with O_ii = 0 for X = eta as a special case); brute-force loops, the
+point-source limit and the exact expectation value for the traces of
+filled stochastic propagators. Parity unpinned: the overall sign of the clover term
 (+i kappa c_sw) is the Sheikholeslami-Wohlert / Luscher-Sint-Sommer-Weisz
 convention and is fixed by that citation only; no invariant above changes
 when it flips.
@@ -362,3 +364,35 @@ def stochastic_operator_correlator(O: np.ndarray) -> np.ndarray:
         for t0 in range(T):
             C[dt] += np.sum(O[(t0 + dt) % T] * O[t0].T)
     return C / (n * n * T)
+
+
+def stochastic_propagator(eta: np.ndarray, X: np.ndarray, t0: int) -> np.ndarray:
+    """The filled stochastic propagator of Eq. Sfill from the source
+    timeslice t0 to every sink site:
+        S(t, z; t0, x)_{ab} = (1/N_r) sum_i X_i(t, z)_a eta_i(t0, x)_b^*,
+    a = (spin, colour) at the sink, b at the source (Sec. "Stochastic
+    propagators"). Returns a complex array indexed
+    [t, z, y, x (sink), z', y', x' (source on t0), s, c, s', c']."""
+    n = eta.shape[0]
+    return np.einsum("itzyxsc,iwvuSC->tzyxwvuscSC", X, np.conj(eta[:, t0])) / n
+
+
+def propagator_trace(SA: np.ndarray, SB: np.ndarray) -> np.ndarray:
+    """sum over every source site x and sink site z of the sink timeslice t
+    of tr[SA(t, z; x) SB(t, z; x)^dag], the spin-colour trace of Table Lcomp's
+    "sum_x sum_z tr S_s S_s^dag"; complex (T,)."""
+    return np.einsum("tzyxwvuscSC,tzyxwvuscSC->t", SA, np.conj(SB))
+
+
+def stochastic_propagator_trace(etaA, XA, etaB=None, XB=None) -> np.ndarray:
+    """C[t0, t] = propagator_trace of the propagators filled from source
+    timeslice t0 with set A (S) and set B (S^dag); one set (B = A) when
+    etaB, XB are None, as in the paper's correlated option. Fills S for
+    every t0 (the L^7 route the paper measured); complex (T, T)."""
+    T = etaA.shape[1]
+    C = np.zeros((T, T), dtype=np.complex128)
+    for t0 in range(T):
+        SA = stochastic_propagator(etaA, XA, t0)
+        SB = SA if etaB is None else stochastic_propagator(etaB, XB, t0)
+        C[t0] = propagator_trace(SA, SB)
+    return C

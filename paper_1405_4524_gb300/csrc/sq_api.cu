@@ -526,6 +526,21 @@ sq_status sq_contract_pion(sq_ctx* c, const double* sol, int n, const int* tsl, 
   return leave_stream(c);
 }
 
+// Scratch of the pair contractions (K-group partials and operator
+// matrices), kept in the context between calls and grown on demand.
+static sq_status grow_contract_scratch(sq_ctx* c, size_t bytes) {
+  if (c->stoch_cap >= bytes) return SQ_OK;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) {
+    cudaFree(c->stoch_part);
+    c->stoch_part = nullptr;
+    c->stoch_cap = 0;
+    e = cudaMalloc(&c->stoch_part, bytes);
+    if (e == cudaSuccess) c->stoch_cap = bytes;
+  }
+  return cuda_check(c, e, "contraction scratch");
+}
+
 sq_status sq_contract_stoch_op(sq_ctx* c, const double* eta, const double* X, int n, double* O, double* C,
                                int where) {
   if (!c) return SQ_ERR_ARG;
@@ -536,19 +551,9 @@ sq_status sq_contract_stoch_op(sq_ctx* c, const double* eta, const double* X, in
   const int T = c->dims[3];
   const int nkg = stoch_groups(c, n);
   const size_t ob = (size_t)T * n * n * 2 * sizeof(double), cb = (size_t)T * 2 * sizeof(double);
-  // the partials live in a context buffer kept between calls (grown on demand)
+  s = grow_contract_scratch(c, ob * nkg);
+  if (s != SQ_OK) return s;
   cudaError_t e = cudaSuccess;
-  if (c->stoch_cap < ob * nkg) {
-    e = cudaStreamSynchronize(c->stream);
-    if (e == cudaSuccess) {
-      cudaFree(c->stoch_part);
-      c->stoch_part = nullptr;
-      c->stoch_cap = 0;
-      e = cudaMalloc(&c->stoch_part, ob * nkg);
-      if (e == cudaSuccess) c->stoch_cap = ob * nkg;
-    }
-    if (e != cudaSuccess) return cuda_check(c, e, "sq_contract_stoch_op scratch");
-  }
   const double *deta, *dX;
   double *teta, *tX = nullptr;
   s = stage_in(c, eta, n, where, &deta, &teta);
@@ -577,6 +582,49 @@ sq_status sq_contract_stoch_op(sq_ctx* c, const double* eta, const double* X, in
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   }
   s = cuda_check(c, e, "sq_contract_stoch_op");
+  if (s != SQ_OK) return s;
+  return leave_stream(c);
+}
+
+sq_status sq_contract_prop_trace(sq_ctx* c, const double* etaA, const double* XA, const double* etaB,
+                                 const double* XB, int n, double* C, int where) {
+  if (!c) return SQ_ERR_ARG;
+  if (!etaA || !XA || !C || n <= 0 || n > 4080 || (!etaB) != (!XB) || (where != SQ_HOST && where != SQ_DEVICE))
+    return set_error(c, SQ_ERR_ARG, "sq_contract_prop_trace: bad argument");
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  const int T = c->dims[3];
+  const int nkg = stoch_groups(c, n);
+  const size_t ob = (size_t)T * n * n * 2 * sizeof(double), cb = (size_t)T * T * 2 * sizeof(double);
+  s = grow_contract_scratch(c, ob * (nkg + 2));
+  if (s != SQ_OK) return s;
+  double* part = (double*)c->stoch_part;
+  double* P = part + (size_t)T * n * n * 2 * nkg;
+  double* Q = P + (size_t)T * n * n * 2;
+  const double* in[4] = {etaA, XA, etaB ? etaB : etaA, XB ? XB : XA};
+  const double* dev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
+  const int nin = etaB ? 4 : 2;
+  for (int k = 0; k < nin && s == SQ_OK; k++) s = stage_in(c, in[k], n, where, &dev[k], &tmp[k]);
+  if (nin == 2) {
+    dev[2] = dev[0];
+    dev[3] = dev[1];
+  }
+  cudaError_t e = cudaSuccess;
+  double* dC = C;
+  if (s == SQ_OK && where == SQ_HOST) e = cudaMallocAsync((void**)&dC, cb, c->stream);
+  if (s == SQ_OK && e == cudaSuccess) {
+    launch_prop_trace(c, dev[0], dev[1], dev[2], dev[3], n, P, Q, dC, part, nkg, c->stream);
+    c->launches += 5;
+    e = cudaGetLastError();
+    if (e == cudaSuccess && where == SQ_HOST) e = cudaMemcpyAsync(C, dC, cb, cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (where == SQ_HOST && dC && dC != C) cudaFreeAsync(dC, c->stream);
+  for (int k = 0; k < 4; k++)
+    if (tmp[k]) cudaFreeAsync(tmp[k], c->stream);
+  if (s != SQ_OK) return s;
+  if (e == cudaSuccess && where == SQ_HOST) e = cudaStreamSynchronize(c->stream);
+  s = cuda_check(c, e, "sq_contract_prop_trace");
   if (s != SQ_OK) return s;
   return leave_stream(c);
 }

@@ -54,7 +54,11 @@ void launch_pion(const sq_ctx* c, const double* lex, int n, const int* tsl, doub
 // ar - ai and br + bi are formed once per row element when it is staged,
 // shared by the 16 pairs of a tile row. GB300's FP64 rate bounds it.
 //
-// k_stoch_partial: CTA (t, kg, tile) sums the rows of its K-range for a
+// The same kernel without gamma5 gives the Gram matrices Sum_y F_k(y)^+ G_l(y)
+// of two fields per timeslice (G5 = false), from which the traces of
+// products of filled stochastic propagators follow (Eq. Sfill).
+//
+// k_pair_partial: CTA (t, kg, tile) sums the rows of its K-range for a
 // 16 x 16 tile of (i, j) pairs, one pair per thread. The K-range is walked
 // in chunks of kStochChunk rows (whole sites, so the gamma5 sign of a row
 // position is fixed: spins 0, 1 are rows 0..5 of a site, spins 2, 3 rows
@@ -87,8 +91,9 @@ __device__ __forceinline__ void stoch_fetch(double2 (&v)[6], const double2* ea, 
   }
 }
 
-__global__ void __launch_bounds__(256, 4) k_stoch_partial(const double2* eta, const double2* X, int n, int T,
-                                                          long long slice2, int nkg, double2* part) {
+template <bool G5>
+__global__ void __launch_bounds__(256, 4) k_pair_partial(const double2* eta, const double2* X, int n, int T,
+                                                         long long slice2, int nkg, double2* part) {
   __shared__ double a_r[kStochTile][kStochPitch], a_i[kStochTile][kStochPitch], a_d[kStochTile][kStochPitch];
   __shared__ double b_r[kStochTile][kStochPitch], b_i[kStochTile][kStochPitch], b_s[kStochTile][kStochPitch];
   const int t = blockIdx.x, kg = blockIdx.y;
@@ -117,7 +122,7 @@ __global__ void __launch_bounds__(256, 4) k_stoch_partial(const double2* eta, co
         a_d[row][q] = v[k].x - v[k].y;
       } else {
         const double sum = v[k].x + v[k].y;
-        const bool lower = (q % 12) >= 6;  // gamma5 = -1 on spins 2, 3
+        const bool lower = G5 && (q % 12) >= 6;  // gamma5 = -1 on spins 2, 3
         b_r[row][q] = lower ? flip_sign(v[k].x) : v[k].x;
         b_i[row][q] = lower ? flip_sign(v[k].y) : v[k].y;
         b_s[row][q] = lower ? flip_sign(sum) : sum;
@@ -187,6 +192,39 @@ __global__ void __launch_bounds__(256) k_stoch_corr(const double2* O, int n, int
 }
 
 // K-groups per timeslice: enough CTAs to fill the GPU about four times
+// C[t0][t] = 1/n^2 sum_ij P_ji(t) Q_ij(t0) = tr[P(t) Q(t0)] / n^2; one CTA per
+// (t0, t), fixed-order tree
+__global__ void __launch_bounds__(256) k_prop_trace(const double2* P, const double2* Q, int n, int T, double2* C) {
+  const int t0 = blockIdx.x / T, t = blockIdx.x - t0 * T;
+  const long long nn = (long long)n * n;
+  double re = 0, im = 0;
+  for (long long ij = threadIdx.x; ij < nn; ij += blockDim.x) {
+    const int i = (int)(ij / n), j = (int)(ij - (long long)i * n);
+    const double2 a = P[t * nn + (long long)j * n + i];
+    const double2 b = Q[t0 * nn + ij];
+    re += a.x * b.x - a.y * b.y;
+    im += a.x * b.y + a.y * b.x;
+  }
+  __shared__ double sr[8], si[8];
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if ((threadIdx.x & 31) == 0) {
+    sr[threadIdx.x >> 5] = re;
+    si[threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      a += sr[w];
+      b += si[w];
+    }
+    const double f = 1.0 / ((double)n * n);
+    C[blockIdx.x] = make_double2(a * f, b * f);
+  }
+}
+
+// K-groups per timeslice: about four CTAs per SM in one wave
 int stoch_groups(const sq_ctx* c, int n) {
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -194,22 +232,39 @@ int stoch_groups(const sq_ctx* c, int n) {
   const int ntile = (n + kStochTile - 1) / kStochTile;
   const long long slice2 = (long long)c->dims[0] * c->dims[1] * c->dims[2] * 12;
   const long long nchunk = (slice2 + kStochChunk - 1) / kStochChunk;
-  long long g = (4LL * sms + (long long)T * ntile * ntile - 1) / ((long long)T * ntile * ntile);
+  long long g = 4LL * sms / ((long long)T * ntile * ntile);
   if (g < 1) g = 1;
   if (g > nchunk) g = nchunk;
   return (int)g;
 }
 
-void launch_stoch_op(const sq_ctx* c, const double* eta, const double* X, int n, double* O, double* C, double* part,
-                     int nkg, cudaStream_t s) {
+// out[t][k][l] = sum over timeslice t of F_k^+ (gamma5) G_l
+static void launch_pairs(const sq_ctx* c, bool g5, const double* F, const double* G, int n, double* out, double* part,
+                         int nkg, cudaStream_t s) {
   const int T = c->dims[3];
   const long long slice2 = (long long)c->dims[0] * c->dims[1] * c->dims[2] * 12;
   const int ntile = (n + kStochTile - 1) / kStochTile;
-  k_stoch_partial<<<dim3(T, nkg, ntile * ntile), 256, 0, s>>>((const double2*)eta, (const double2*)X, n, T, slice2,
-                                                              nkg, (double2*)part);
+  const dim3 grid(T, nkg, ntile * ntile);
+  if (g5)
+    k_pair_partial<true><<<grid, 256, 0, s>>>((const double2*)F, (const double2*)G, n, T, slice2, nkg, (double2*)part);
+  else
+    k_pair_partial<false><<<grid, 256, 0, s>>>((const double2*)F, (const double2*)G, n, T, slice2, nkg, (double2*)part);
   const long long total = (long long)T * n * n;
-  k_stoch_sum<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((const double2*)part, n, T, nkg, (double2*)O);
-  if (C) k_stoch_corr<<<T, 256, 0, s>>>((const double2*)O, n, T, (double2*)C);
+  k_stoch_sum<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((const double2*)part, n, T, nkg, (double2*)out);
+}
+
+void launch_stoch_op(const sq_ctx* c, const double* eta, const double* X, int n, double* O, double* C, double* part,
+                     int nkg, cudaStream_t s) {
+  launch_pairs(c, true, eta, X, n, O, part, nkg, s);
+  if (C) k_stoch_corr<<<c->dims[3], 256, 0, s>>>((const double2*)O, n, c->dims[3], (double2*)C);
+}
+
+void launch_prop_trace(const sq_ctx* c, const double* etaA, const double* XA, const double* etaB, const double* XB,
+                       int n, double* P, double* Q, double* C, double* part, int nkg, cudaStream_t s) {
+  const int T = c->dims[3];
+  launch_pairs(c, false, XB, XA, n, P, part, nkg, s);     // P_ji(t) = sum_z XB_j^+ XA_i
+  launch_pairs(c, false, etaA, etaB, n, Q, part, nkg, s);  // Q_ij(t0) = sum_x etaA_i^+ etaB_j
+  k_prop_trace<<<T * T, 256, 0, s>>>((const double2*)P, (const double2*)Q, n, T, (double2*)C);
 }
 
 }  // namespace sq

@@ -205,5 +205,7 @@ void launch_pion(const sq_ctx* c, const double* lex, int n, const int* tsl, doub
 int stoch_groups(const sq_ctx* c, int n);
 void launch_stoch_op(const sq_ctx* c, const double* eta, const double* X, int n, double* O, double* C, double* part,
                      int nkg, cudaStream_t s);
+void launch_prop_trace(const sq_ctx* c, const double* etaA, const double* XA, const double* etaB, const double* XB,
+                       int n, double* P, double* Q, double* C, double* part, int nkg, cudaStream_t s);
 
 }  // namespace sq

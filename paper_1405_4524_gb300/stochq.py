@@ -98,6 +98,7 @@ _SIG = {
                             C.POINTER(sq_solve_stats)]),
     "sq_contract_pion": (_i, [_vp, _vp, _i, _vp, _vp, _i]),
     "sq_contract_stoch_op": (_i, [_vp, _vp, _vp, _i, _vp, _vp, _i]),
+    "sq_contract_prop_trace": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp, _i]),
     "sq_get_profile": (_i, [_vp, C.POINTER(sq_kernel_stat), _i, C.POINTER(_i)]),
     "sq_kernel_launches": (_i, [_vp, C.POINTER(C.c_longlong)]),
     "sq_status_string": (C.c_char_p, [_i]),
@@ -356,6 +357,31 @@ def sq_contract_stoch_op(ctx, eta, X, n_rhs: int, O=None, C=None, correlator: bo
             raise ValueError("O and C must live where eta and X do")
     _check(ctx, _lib.sq_contract_stoch_op(ctx, _ptr(eta), _ptr(X), n, _ptr(O), _ptr(C), where))
     return O, C
+
+
+def sq_contract_prop_trace(ctx, etaA, XA, n_rhs: int, etaB=None, XB=None, C=None):
+    """C (T, T) complex128: C[t0, t] = sum_{x in t0, z in t} tr[S_A S_B^dag].
+
+    One source set when etaB and XB are None. Inputs all host arrays or all
+    CUDA tensors; C is allocated like them when not given."""
+    if (etaB is None) != (XB is None):
+        raise ValueError("give both etaB and XB, or neither")
+    fields = [f for f in (etaA, XA, etaB, XB) if f is not None]
+    where = _where(etaA)
+    if any(_where(f) != where for f in fields):
+        raise ValueError("all fields must be host arrays or all device tensors")
+    T = int(etaA.shape[1])
+    if C is None:
+        if where == SQ_HOST:
+            C = np.zeros((T, T), dtype=np.complex128)
+        else:
+            import torch
+            C = torch.zeros((T, T), dtype=torch.complex128, device=etaA.device)
+    elif _where(C) != where:
+        raise ValueError("C must live where the fields do")
+    _check(ctx, _lib.sq_contract_prop_trace(ctx, _ptr(etaA), _ptr(XA), _ptr(etaB), _ptr(XB), int(n_rhs),
+                                            _ptr(C), where))
+    return C
 
 
 def sq_get_profile(ctx):

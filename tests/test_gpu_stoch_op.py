@@ -129,3 +129,75 @@ def test_errors(sq):
         assert close(O, oracle.stochastic_operator(eta, eta))
     finally:
         sq.sq_destroy(ctx)
+
+
+# ---------------------------------------------------------------------------
+# traces of filled stochastic propagators (Eq. Sfill) without the fill
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,n,two", [((4, 4, 4, 8), 4, True), ((4, 4, 4, 8), 4, False),
+                                        ((2, 2, 4, 6), 19, True), ((2, 2, 2, 4), 1, False)])
+def test_prop_trace_matches_oracle_fill(sq, dims, n, two):
+    """Against the oracle's explicit fill of S for every source timeslice."""
+    ctx = sq.sq_create(dims, -1)
+    try:
+        eA = inputs.make_z4(dims, n, 5101)
+        xA = random_spinors(dims, n, 5102)
+        eB = inputs.make_z4(dims, n, 5201 + 100) if two else None
+        xB = random_spinors(dims, n, 5202) if two else None
+        C = sq.sq_contract_prop_trace(ctx, eA, xA, n, eB, xB)
+        want = oracle.stochastic_propagator_trace(eA, xA, eB, xB)
+        assert C.shape == want.shape
+        assert close(C, want)
+    finally:
+        sq.sq_destroy(ctx)
+
+
+def gram_form(eA, xA, eB, xB):
+    """(1/n^2) tr[P(t) Q(t0)] in numpy: the identity pinned against the
+    oracle's fill in the oracle pins, for sizes where the fill cannot be
+    stored."""
+    n = eA.shape[0]
+    P = np.einsum("jtzyxsc,itzyxsc->tji", np.conj(xB), xA)
+    Q = np.einsum("itzyxsc,jtzyxsc->tij", np.conj(eA), eB)
+    return np.einsum("tji,sij->st", P, Q) / n**2
+
+
+def test_prop_trace_full_size(sq):
+    dims, n = (16, 16, 16, 32), 16
+    ctx = sq.sq_create(dims, -1)
+    try:
+        eA = inputs.make_z4(dims, n, 5301)
+        xA = random_spinors(dims, n, 5302)
+        eB = inputs.make_z4(dims, n, 5401)
+        xB = random_spinors(dims, n, 5402)
+        C = sq.sq_contract_prop_trace(ctx, eA, xA, n, eB, xB)
+        assert close(C, gram_form(eA, xA, eB, xB))
+    finally:
+        sq.sq_destroy(ctx)
+
+
+def test_prop_trace_device_io_and_errors(sq):
+    import torch
+
+    dims, n = (4, 4, 4, 8), 3
+    ctx = sq.sq_create(dims, -1)
+    try:
+        eA = inputs.make_z4(dims, n, 5501)
+        xA = random_spinors(dims, n, 5502)
+        C = sq.sq_contract_prop_trace(ctx, eA, xA, n)
+        Cd = sq.sq_contract_prop_trace(ctx, torch.from_numpy(eA).cuda(), torch.from_numpy(xA).cuda(), n)
+        assert Cd.is_cuda and np.array_equal(Cd.cpu().numpy(), C)
+        # one set: C[t0, t] is a sum of |.|^2, real and non-negative
+        assert np.all(np.abs(C.imag) <= 1e-12 * np.abs(C).max()) and np.all(C.real >= 0)
+        with pytest.raises(ValueError):
+            sq.sq_contract_prop_trace(ctx, eA, xA, n, eA, None)
+        out = np.zeros((8, 8), dtype=np.complex128)
+        st = sq._lib.sq_contract_prop_trace(ctx, eA.ctypes.data, xA.ctypes.data, eA.ctypes.data, None, n,
+                                            out.ctypes.data, sq.SQ_HOST)
+        assert st == sq.SQ_ERR_ARG
+        with pytest.raises(sq.StochqError):
+            sq.sq_contract_prop_trace(ctx, eA, xA, 0)
+        assert np.array_equal(sq.sq_contract_prop_trace(ctx, eA, xA, n), C)
+    finally:
+        sq.sq_destroy(ctx)

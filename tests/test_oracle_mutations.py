@@ -206,3 +206,37 @@ def test_stochastic_operator_mutation_is_caught(kind, monkeypatch):
     monkeypatch.setattr(dirac, attr, fn)
     monkeypatch.setattr(oracle, attr, fn)
     assert not _run_pins(STOCH_PINS), f"mutation not caught: {kind}"
+
+
+def _fill_no_conj(eta, X, t0):
+    n = eta.shape[0]
+    return np.einsum("itzyxsc,iwvuSC->tzyxwvuscSC", X, eta[:, t0]) / n
+
+
+def _fill_no_norm(eta, X, t0):
+    return np.einsum("itzyxsc,iwvuSC->tzyxwvuscSC", X, np.conj(eta[:, t0]))
+
+
+def _trace_no_dagger(SA, SB):
+    return np.einsum("tzyxwvuscSC,tzyxwvuscSC->t", SA, SB)
+
+
+def _trace_transposed(SA, SB):
+    return np.einsum("tzyxwvuscSC,tzyxwvuSCsc->t", SA, np.conj(SB))
+
+
+FILL_PINS = ["test_propagator_trace_brute_force", "test_propagator_trace_point_source_limit",
+             "test_propagator_trace_estimate_matches_exact"]
+
+
+@pytest.mark.parametrize("kind", ["no_conj", "no_norm", "no_dagger", "transposed"])
+def test_propagator_trace_mutation_is_caught(kind, monkeypatch):
+    import oracle
+
+    attr, fn = {"no_conj": ("stochastic_propagator", _fill_no_conj),
+                "no_norm": ("stochastic_propagator", _fill_no_norm),
+                "no_dagger": ("propagator_trace", _trace_no_dagger),
+                "transposed": ("propagator_trace", _trace_transposed)}[kind]
+    monkeypatch.setattr(dirac, attr, fn)
+    monkeypatch.setattr(oracle, attr, fn)
+    assert not _run_pins(FILL_PINS), f"mutation not caught: {kind}"
