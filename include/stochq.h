@@ -315,6 +315,26 @@ sq_status sq_contract_pion(sq_ctx *ctx, const double *solutions, int n_rhs,
 sq_status sq_contract_stoch_op(sq_ctx *ctx, const double *eta, const double *X,
                                int n_rhs, double *O, double *C, int where);
 
+/* The operators of sq_contract_stoch_op (same O and C, same layouts) on the
+ * tensor cores, for sources whose real and imaginary components are all
+ * 0 or +-1 (Z2 and Z4 noise, diluted or not). gamma5 X is cut per source,
+ * timeslice and block of 4096 rows into a 55-bit fixed-point integer
+ * relative to the block's largest component and split into five 11-bit
+ * digits; each digit's products with the sources are summed on the tensor
+ * cores in FP16 x FP16 -> FP32, exactly (every partial sum is an integer
+ * below 2^24), and the digits are combined in FP64 with power-of-two
+ * weights. The result differs from sq_contract_stoch_op by the truncation
+ * of X below 2^-55 of each block's largest component and by FP64 rounding
+ * order. Always synchronises the context's stream (it reports the source
+ * check). The context keeps a workspace of the packed operands (up to
+ * 8 GiB; larger problems run in timeslice batches). Worth it for n_rhs of
+ * about 128 and more (the tensor tiles hold 128 x 16 sources).
+ * Errors: SQ_ERR_ARG (as sq_contract_stoch_op, or a source component not
+ * 0 or +-1), SQ_ERR_NONFINITE (X), SQ_ERR_TIMEOUT (a bounded wait of the
+ * kernel ran out; nothing hangs), SQ_ERR_CUDA. */
+sq_status sq_contract_stoch_op_z4(sq_ctx *ctx, const double *eta, const double *X,
+                                  int n_rhs, double *O, double *C, int where);
+
 /* Traces of filled stochastic propagators without the fill (Eq. Sfill and
  * the "sum_x sum_z tr S_s S_s^+" entry of Table Lcomp, Sec. "Stochastic
  * propagators"): with S_A(t,z; t0,x) = (1/n_rhs) sum_i XA_i(t,z) etaA_i(t0,x)^+

@@ -586,6 +586,65 @@ sq_status sq_contract_stoch_op(sq_ctx* c, const double* eta, const double* X, in
   return leave_stream(c);
 }
 
+sq_status sq_contract_stoch_op_z4(sq_ctx* c, const double* eta, const double* X, int n, double* O, double* C,
+                                  int where) {
+  if (!c) return SQ_ERR_ARG;
+  if (!eta || !X || !O || n <= 0 || n > 4080 || (where != SQ_HOST && where != SQ_DEVICE))
+    return set_error(c, SQ_ERR_ARG, "sq_contract_stoch_op_z4: bad argument");
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  const TcPlan p = tc_plan(c, n, (size_t)8 << 30);
+  s = grow_contract_scratch(c, p.bytes);
+  if (s != SQ_OK) return s;
+  const int T = c->dims[3];
+  const size_t ob = (size_t)T * n * n * 2 * sizeof(double), cb = (size_t)T * 2 * sizeof(double);
+  const double *deta, *dX;
+  double *teta, *tX = nullptr;
+  s = stage_in(c, eta, n, where, &deta, &teta);
+  if (s == SQ_OK) s = stage_in(c, X, n, where, &dX, &tX);
+  if (s != SQ_OK) {
+    if (teta) cudaFreeAsync(teta, c->stream);
+    return s;
+  }
+  double *dO = O, *dC = C;
+  cudaError_t e = cudaSuccess;
+  if (where == SQ_HOST) {
+    e = cudaMallocAsync((void**)&dO, ob, c->stream);
+    if (e == cudaSuccess && C) e = cudaMallocAsync((void**)&dC, cb, c->stream);
+  }
+  int* flag = reinterpret_cast<int*>(static_cast<char*>(c->stoch_part) + p.bytes - 256);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = launch_stoch_tc(c, p, deta, dX, n, dO, c->stoch_part, c->d_err, c->stream);
+  if (e == cudaSuccess) {
+    c->launches += 3LL * ((T + p.Tb - 1) / p.Tb);
+    if (C) {
+      launch_stoch_corr(c, dO, n, dC, c->stream);
+      c->launches += 1;
+      e = cudaGetLastError();
+    }
+  }
+  int hflag = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (where == SQ_HOST) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(O, dO, ob, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && C) e = cudaMemcpyAsync(C, dC, cb, cudaMemcpyDeviceToHost, c->stream);
+    if (dO && dO != O) cudaFreeAsync(dO, c->stream);
+    if (C && dC && dC != C) cudaFreeAsync(dC, c->stream);
+  }
+  if (teta) cudaFreeAsync(teta, c->stream);
+  if (tX) cudaFreeAsync(tX, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  s = cuda_check(c, e, "sq_contract_stoch_op_z4");
+  if (s != SQ_OK) return s;
+  int bits = 0;
+  s = read_error_word(c, &bits);
+  if (s != SQ_OK) return s;
+  if (bits & ERRBIT_TIMEOUT) return set_error(c, SQ_ERR_TIMEOUT, "sq_contract_stoch_op_z4: a tensor-core wait timed out");
+  if (hflag & 1) return set_error(c, SQ_ERR_ARG, "sq_contract_stoch_op_z4: a source component is not 0 or +-1");
+  if (hflag & 2) return set_error(c, SQ_ERR_NONFINITE, "sq_contract_stoch_op_z4: X is not finite");
+  return leave_stream(c);
+}
+
 sq_status sq_contract_prop_trace(sq_ctx* c, const double* etaA, const double* XA, const double* etaB,
                                  const double* XB, int n, double* C, int where) {
   if (!c) return SQ_ERR_ARG;

@@ -259,6 +259,10 @@ void launch_stoch_op(const sq_ctx* c, const double* eta, const double* X, int n,
   if (C) k_stoch_corr<<<c->dims[3], 256, 0, s>>>((const double2*)O, n, c->dims[3], (double2*)C);
 }
 
+void launch_stoch_corr(const sq_ctx* c, const double* O, int n, double* C, cudaStream_t s) {
+  k_stoch_corr<<<c->dims[3], 256, 0, s>>>((const double2*)O, n, c->dims[3], (double2*)C);
+}
+
 void launch_prop_trace(const sq_ctx* c, const double* etaA, const double* XA, const double* etaB, const double* XB,
                        int n, double* P, double* Q, double* C, double* part, int nkg, cudaStream_t s) {
   const int T = c->dims[3];

@@ -205,6 +205,17 @@ void launch_pion(const sq_ctx* c, const double* lex, int n, const int* tsl, doub
 int stoch_groups(const sq_ctx* c, int n);
 void launch_stoch_op(const sq_ctx* c, const double* eta, const double* X, int n, double* O, double* C, double* part,
                      int nkg, cudaStream_t s);
+// Tensor-core stochastic operators (sq_stoch_tc.cu): tile counts and the
+// packed-operand workspace of a batch of Tb timeslices.
+struct TcPlan {
+  int T = 0, Tb = 0, nkt = 0, nch = 0, nit = 0, njt = 0;
+  long long K = 0;
+  size_t a_per_t = 0, b_per_t = 0, e_per_t = 0, bytes = 0;
+};
+TcPlan tc_plan(const sq_ctx* c, int n, size_t cap_bytes);
+cudaError_t launch_stoch_tc(const sq_ctx* c, const TcPlan& p, const double* eta, const double* X, int n, double* O,
+                            void* ws, int* err, cudaStream_t s);
+void launch_stoch_corr(const sq_ctx* c, const double* O, int n, double* C, cudaStream_t s);
 void launch_prop_trace(const sq_ctx* c, const double* etaA, const double* XA, const double* etaB, const double* XB,
                        int n, double* P, double* Q, double* C, double* part, int nkg, cudaStream_t s);
 

@@ -1,0 +1,461 @@
+// Stochastic operators O_ij(t) (Eq. stoop) on the fifth-generation tensor
+// cores, for sources whose real and imaginary components are all 0 or +-1
+// (Z2 and Z4 noise and their dilutions).
+//
+// Exactness. With such sources O_ij(t) is a sum of signed components of
+// gamma5 X_j. Every component x of gamma5 X_j is cut, per source, timeslice
+// and chunk of 4096 complex rows, into a 55-bit fixed-point integer relative
+// to the chunk's largest component (|x| < 2^e):  m = trunc(x 2^(55-e)),
+// split into five signed 11-bit digits d_s (m = sum_s d_s 2^(11(4-s))), each
+// exact in FP16. One FP16 x FP16 -> FP32 tensor-core product per digit then
+// sums at most 8192 terms of magnitude <= 2047, so every partial sum is an
+// integer below 2^24 and exact in FP32, whatever order the hardware adds in.
+// The digits are combined in FP64 with exact power-of-two weights
+// 2^(e - 55 + 11(4-s)), chunk by chunk in a fixed order. The only
+// approximation is the truncation of x below 2^(e-55) (relative 2^-55 of the
+// chunk's largest component) and the FP64 roundings of that combination.
+//
+// Real form. K' = 2K columns per timeslice (K = 12 * X*Y*Z complex rows;
+// column 2k is the real part of row k, 2k+1 the imaginary part):
+//   A (M side, 128 sources i per tile):  a(i, 2k) = Re eta_i(k), a(i, 2k+1) = Im eta_i(k)
+//   B (N side, 16 sources j per tile, 10 rows each, row (s*2 + c)*16 + j):
+//     c = 0:  b(2k) = d_s(Re y_j(k)),  b(2k+1) = d_s(Im y_j(k))     -> Re O_ij
+//     c = 1:  b(2k) = d_s(Im y_j(k)),  b(2k+1) = -d_s(Re y_j(k))    -> Im O_ij
+//   with y = gamma5 X. D = A B^T accumulates in tensor memory (128 lanes =
+// sources i, 160 columns = (digit, part, j)).
+//
+// Layout. Operand tiles of 64 columns are stored in global memory already
+// in the tensor core's K-major no-swizzle shared-memory layout: 8-row x
+// 16-byte core matrices, the core matrix of row group g and column group q
+// at byte ((q * R/8) + g) * 128 (R = 128 rows for A, 160 for B), so that one
+// bulk copy moves a tile and the matrix descriptors use a leading (column
+// group) stride of R*16 bytes and a stride (row group) of 128 bytes.
+//
+// Kernel. One CTA per (16-source j tile, 128-source i tile, timeslice):
+// warp 4 streams the tiles through a 4-stage shared-memory ring with
+// cp.async.bulk, warp 5 issues tcgen05.mma (4 per tile, K = 16 each) into
+// one of two tensor-memory accumulators (one per chunk of 128 tiles, so the
+// epilogue of a chunk overlaps the products of the next), warps 0-3 read
+// the accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31) and add the
+// digits into FP64 registers. Every wait is bounded; on a timeout the CTA
+// records ERRBIT_TIMEOUT, lets its copies and products drain, frees its
+// tensor memory and returns.
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "sq_internal.h"
+
+namespace sq {
+
+constexpr int kTcM = 128;                  // i rows per tile
+constexpr int kTcJ = 16;                   // j sources per tile
+constexpr int kTcN = 10 * kTcJ;            // B rows per tile
+constexpr int kTcK = 64;                   // K' columns per tile (32 complex rows)
+constexpr int kTcStages = 4;
+constexpr int kTcChunkTiles = 128;         // tiles per exact chunk (8192 columns)
+constexpr int kTcChunkRows = kTcChunkTiles * kTcK / 2;  // complex rows per chunk
+constexpr int kTcABytes = kTcM * kTcK * 2;  // 16384
+constexpr int kTcBBytes = kTcN * kTcK * 2;  // 20480
+constexpr int kTcStageBytes = kTcABytes + kTcBBytes;
+constexpr int kTcTmemCols = 512;           // two accumulators of 160 columns at 0 and 256
+constexpr int kTcThreads = 192;
+// dynamic shared memory: the ring, then the barriers; the rest is slack that
+// keeps every address a descriptor can form inside the allocation
+constexpr int kTcBarOffset = kTcStages * kTcStageBytes;  // 147456
+constexpr int kTcSmemBytes = 200 * 1024;
+constexpr long long kTcWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+// ---- PTX wrappers ----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major, no swizzle: start address,
+// leading byte offset (between column groups), stride byte offset (between
+// 8-row groups), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
+         ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, FP16 A and B, both
+// K-major, N = kTcN, M = kTcM.
+constexpr uint32_t kTcIdesc = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+
+// Wait, as a whole warp (uniform result), for the phase of parity `parity`
+// of barrier `bar`; false after about 2 s (ERRBIT_TIMEOUT, abort set) or,
+// if watch_abort, when another role has aborted.
+__device__ bool tc_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* err, bool watch_abort) {
+  const long long t0 = clock64();
+  while (true) {
+    const bool ready = mbar_try(bar, parity);
+    if (__all_sync(0xffffffffu, ready)) return true;
+    const bool timed_out = clock64() - t0 > kTcWaitCycles;
+    const bool stop = timed_out || (watch_abort && *abort);
+    if (__any_sync(0xffffffffu, stop)) {
+      if (__any_sync(0xffffffffu, timed_out) && (threadIdx.x & 31) == 0) {
+        *abort = 1;
+        atomicOr(err, ERRBIT_TIMEOUT);
+      }
+      return false;
+    }
+  }
+}
+
+// ---- operand packing -------------------------------------------------------
+// byte offset of element (row r, column k) inside a tile of R rows
+__host__ __device__ constexpr int tile_offset(int R, int r, int k) {
+  return (((k >> 3) * (R >> 3)) + (r >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+  uint4 u;
+  __half2 h;
+  h = __floats2half2_rn(f[0], f[1]);
+  u.x = *reinterpret_cast<uint32_t*>(&h);
+  h = __floats2half2_rn(f[2], f[3]);
+  u.y = *reinterpret_cast<uint32_t*>(&h);
+  h = __floats2half2_rn(f[4], f[5]);
+  u.z = *reinterpret_cast<uint32_t*>(&h);
+  h = __floats2half2_rn(f[6], f[7]);
+  u.w = *reinterpret_cast<uint32_t*>(&h);
+  return u;
+}
+
+// A tiles of timeslices t0 .. t0 + Tb - 1: grid (nkt, n_itiles, Tb), 256 threads.
+// Sets bit 1 of *flag if a component is not 0 or +-1.
+__global__ void __launch_bounds__(256) k_tc_pack_eta(const double2* eta, int n, int T, int t0, long long K,
+                                                     int nkt, int nit, uint4* A, int* flag) {
+  const int kt = blockIdx.x, it = blockIdx.y, tb = blockIdx.z;
+  char* blk = reinterpret_cast<char*>(A) + (((long long)tb * nit + it) * nkt + kt) * kTcABytes;
+  for (int v = threadIdx.x; v < kTcM * 8; v += blockDim.x) {
+    const int r = v >> 3, q = v & 7;  // row, group of 8 columns = 4 complex rows
+    const int i = it * kTcM + r;
+    float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (i < n) {
+      const double2* src = eta + ((long long)i * T + t0 + tb) * K + (long long)kt * (kTcK / 2) + q * 4;
+      bool ok = true;
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        const double2 d = src[c];
+        ok = ok && (d.x == 0.0 || d.x == 1.0 || d.x == -1.0) && (d.y == 0.0 || d.y == 1.0 || d.y == -1.0);
+        f[2 * c] = (float)d.x;
+        f[2 * c + 1] = (float)d.y;
+      }
+      if (!ok) atomicOr(flag, 1);
+    }
+    *reinterpret_cast<uint4*>(blk + tile_offset(kTcM, r, q * 8)) = pack8(f);
+  }
+}
+
+// trunc(x 2^(55-e)) for |x| < 2^e, from the bits of x (integer pipe only)
+__device__ __forceinline__ long long fixed55(double x, int e) {
+  const long long b = __double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7ff);
+  if (E == 0) return 0;  // zero or subnormal
+  const long long mant = (b & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+  const int sh = E - 1075 + 55 - e;
+  const long long m = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0LL);
+  return b < 0 ? -m : m;
+}
+
+__device__ __forceinline__ float digit(long long m, int s) {
+  const long long a = m < 0 ? -m : m;
+  const int d = (int)((a >> (11 * (4 - s))) & 2047);
+  return (float)(m < 0 ? -d : d);
+}
+
+// B tiles and chunk exponents of timeslices t0 .. t0 + Tb - 1: grid (nch,
+// n_jtiles * 16, Tb), 256 threads. Sets bit 2 of *flag on a non-finite x.
+__global__ void __launch_bounds__(256) k_tc_pack_x(const double2* X, int n, int T, int t0, long long K, int nkt,
+                                                   int njt, int nch, uint4* B, int* exps, int* flag) {
+  const int ch = blockIdx.x, j = blockIdx.y, tb = blockIdx.z;
+  const long long r0 = (long long)ch * kTcChunkRows;
+  const long long r1 = min(K, r0 + kTcChunkRows);
+  const double2* src = X + ((long long)j * T + t0 + tb) * K;
+  // largest |component| of the chunk (as bits: order-preserving for |x|)
+  unsigned long long mx = 0;
+  if (j < n)
+    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+      const double2 d = src[r];
+      mx = max(mx, (unsigned long long)__double_as_longlong(d.x) & 0x7FFFFFFFFFFFFFFFULL);
+      mx = max(mx, (unsigned long long)__double_as_longlong(d.y) & 0x7FFFFFFFFFFFFFFFULL);
+    }
+  __shared__ unsigned long long smx[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) smx[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = smx[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); w++) mx = max(mx, smx[w]);
+  const int Eb = (int)(mx >> 52);
+  if (Eb == 0x7ff) {
+    if (threadIdx.x == 0) atomicOr(flag, 2);
+    return;
+  }
+  const int e = mx == 0 ? 0 : Eb - 1023 + 1;  // |x| < 2^e
+  if (threadIdx.x == 0) exps[((long long)tb * njt * kTcJ + j) * nch + ch] = e;
+  const int jt = j / kTcJ, jl = j - jt * kTcJ;
+  const int kt0 = ch * kTcChunkTiles, kt1 = min(nkt, kt0 + kTcChunkTiles);
+  for (int v = threadIdx.x; v < (kt1 - kt0) * 8; v += blockDim.x) {
+    const int kt = kt0 + (v >> 3), q = v & 7;
+    const long long row = (long long)kt * (kTcK / 2) + q * 4;
+    long long mr[4], mi[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+      double2 d = make_double2(0.0, 0.0);
+      if (j < n) d = src[row + c];
+      mr[c] = fixed55(d.x, e);
+      mi[c] = fixed55(d.y, e);
+      if (((row + c) % 12) >= 6) {  // gamma5 = -1 on spins 2, 3
+        mr[c] = -mr[c];
+        mi[c] = -mi[c];
+      }
+    }
+    char* blk = reinterpret_cast<char*>(B) + (((long long)tb * njt + jt) * nkt + kt) * kTcBBytes;
+#pragma unroll
+    for (int s = 0; s < 5; s++) {
+      float fr[8], fi[8];
+#pragma unroll
+      for (int c = 0; c < 4; c++) {
+        fr[2 * c] = digit(mr[c], s);
+        fr[2 * c + 1] = digit(mi[c], s);
+        fi[2 * c] = digit(mi[c], s);
+        fi[2 * c + 1] = -digit(mr[c], s);
+      }
+      *reinterpret_cast<uint4*>(blk + tile_offset(kTcN, (s * 2 + 0) * kTcJ + jl, q * 8)) = pack8(fr);
+      *reinterpret_cast<uint4*>(blk + tile_offset(kTcN, (s * 2 + 1) * kTcJ + jl, q * 8)) = pack8(fi);
+    }
+  }
+}
+
+// ---- the product -----------------------------------------------------------
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_stoch_tc(const uint4* A, const uint4* B, const int* exps, int n, int t0, int nkt, int nit, int njt, int nch,
+               double2* O, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int jt = blockIdx.x, it = blockIdx.y, tb = blockIdx.z;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kTcBarOffset);
+  // bars: full[4], empty[4], accf[2], acce[2], done
+  const uint32_t full0 = smem_addr(bars), empty0 = full0 + 8 * kTcStages;
+  const uint32_t accf0 = empty0 + 8 * kTcStages, acce0 = accf0 + 16, done = acce0 + 16;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kTcBarOffset + 8 * (2 * kTcStages + 5));
+  volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+
+  // a timeout anywhere in this launch stops the CTAs that have not started
+  if (threadIdx.x == 0) tslot[1] = *(volatile int*)err & ERRBIT_TIMEOUT;
+  __syncthreads();
+  if (tslot[1]) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; s++) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; b++) {
+      mbar_init(accf0 + 8 * b, 1);
+      mbar_init(acce0 + 8 * b, 128);
+    }
+    mbar_init(done, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                 "r"(kTcTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  const char* Ablk = reinterpret_cast<const char*>(A) + ((long long)tb * nit + it) * nkt * (long long)kTcABytes;
+  const char* Bblk = reinterpret_cast<const char*>(B) + ((long long)tb * njt + jt) * nkt * (long long)kTcBBytes;
+  const uint32_t ring = smem_addr(smem);
+
+  if (warp == 4) {
+    // producer: tile kt into stage kt % 4 once the products of tile kt - 4
+    // are done (the whole warp waits, lane 0 issues)
+    int kt = 0;
+    for (; kt < nkt; kt++) {
+      const int s = kt % kTcStages;
+      if (kt >= kTcStages && !tc_wait(empty0 + 8 * s, ((kt / kTcStages) - 1) & 1, abort, err, true)) break;
+      if (lane == 0) {
+        mbar_expect_tx(full0 + 8 * s, kTcStageBytes);
+        bulk_load(ring + s * kTcStageBytes, Ablk + (long long)kt * kTcABytes, kTcABytes, full0 + 8 * s);
+        bulk_load(ring + s * kTcStageBytes + kTcABytes, Bblk + (long long)kt * kTcBBytes, kTcBBytes, full0 + 8 * s);
+      }
+      __syncwarp();
+    }
+    // every copy issued has landed before the CTA can leave
+    for (int k = max(0, kt - kTcStages); k < kt; k++)
+      tc_wait(full0 + 8 * (k % kTcStages), (k / kTcStages) & 1, abort, err, false);
+  } else if (warp == 5) {
+    // products (the whole warp waits, lane 0 issues): chunk c accumulates
+    // in tensor columns (c & 1) * 256
+    for (int kt = 0; kt < nkt; kt++) {
+      const int s = kt % kTcStages, c = kt / kTcChunkTiles, buf = c & 1;
+      const bool first = (kt % kTcChunkTiles) == 0;
+      if (first && c >= 2 && !tc_wait(acce0 + 8 * buf, ((c - 2) >> 1) & 1, abort, err, true)) break;
+      if (!tc_wait(full0 + 8 * s, (kt / kTcStages) & 1, abort, err, true)) break;
+      tc_fence_after();
+      if (lane == 0) {
+        const uint32_t a0 = ring + s * kTcStageBytes, b0 = a0 + kTcABytes;
+#pragma unroll
+        for (int ks = 0; ks < kTcK / 16; ks++) {
+          const uint64_t ad = smem_desc(a0 + ks * 2 * (kTcM * 16), kTcM * 16, 128);
+          const uint64_t bd = smem_desc(b0 + ks * 2 * (kTcN * 16), kTcN * 16, 128);
+          tc_mma(tmem + buf * 256, ad, bd, kTcIdesc, (first && ks == 0) ? 0u : 1u);
+        }
+        tc_commit(empty0 + 8 * s);
+        if ((kt % kTcChunkTiles) == kTcChunkTiles - 1 || kt == nkt - 1) tc_commit(accf0 + 8 * buf);
+      }
+      __syncwarp();
+    }
+    // all products issued by lane 0 have finished
+    if (lane == 0) tc_commit(done);
+    __syncwarp();
+    tc_wait(done, 0, abort, err, false);
+  } else if (warp < 4) {
+    double re[kTcJ], im[kTcJ];
+#pragma unroll
+    for (int q = 0; q < kTcJ; q++) re[q] = im[q] = 0.0;
+    const int* ex = exps + ((long long)tb * njt * kTcJ + jt * kTcJ) * nch;
+    for (int c = 0; c < nch; c++) {
+      const int buf = c & 1;
+      if (!tc_wait(accf0 + 8 * buf, (c >> 1) & 1, abort, err, true)) break;
+      tc_fence_after();
+      int e[kTcJ];
+#pragma unroll
+      for (int q = 0; q < kTcJ; q++) e[q] = ex[q * nch + c];
+      const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16) + buf * 256;
+#pragma unroll 1
+      for (int s = 0; s < 5; s++) {
+        uint32_t vr[16], vi[16];
+        tc_ld16(tbase + (s * 2 + 0) * kTcJ, vr);
+        tc_ld16(tbase + (s * 2 + 1) * kTcJ, vi);
+        tc_wait_ld();
+#pragma unroll
+        for (int q = 0; q < kTcJ; q++) {
+          const double w = __longlong_as_double((long long)(1023 + e[q] - 55 + 11 * (4 - s)) << 52);
+          re[q] = fma((double)__uint_as_float(vr[q]), w, re[q]);
+          im[q] = fma((double)__uint_as_float(vi[q]), w, im[q]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(acce0 + 8 * buf);
+    }
+    const int i = it * kTcM + warp * 32 + lane;
+    if (i < n && !*abort) {
+      double2* o = O + ((long long)(t0 + tb) * n + i) * n + jt * kTcJ;
+#pragma unroll
+      for (int q = 0; q < kTcJ; q++)
+        if (jt * kTcJ + q < n) o[q] = make_double2(re[q], im[q]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+  }
+}
+
+// ---- host side -------------------------------------------------------------
+TcPlan tc_plan(const sq_ctx* c, int n, size_t cap_bytes) {
+  TcPlan p;
+  const long long K = (long long)c->dims[0] * c->dims[1] * c->dims[2] * 12;
+  p.T = c->dims[3];
+  p.K = K;
+  p.nkt = (int)(2 * K / kTcK);
+  p.nch = (p.nkt + kTcChunkTiles - 1) / kTcChunkTiles;
+  p.nit = (n + kTcM - 1) / kTcM;
+  p.njt = (n + kTcJ - 1) / kTcJ;
+  p.a_per_t = (size_t)p.nit * p.nkt * kTcABytes;
+  p.b_per_t = (size_t)p.njt * p.nkt * kTcBBytes;
+  p.e_per_t = (size_t)p.njt * kTcJ * p.nch * sizeof(int);
+  const size_t per_t = p.a_per_t + p.b_per_t + ((p.e_per_t + 255) & ~(size_t)255);
+  long long tb = (long long)(cap_bytes / per_t);
+  if (tb < 1) tb = 1;
+  if (tb > p.T) tb = p.T;
+  p.Tb = (int)tb;
+  p.bytes = per_t * p.Tb + 256;
+  return p;
+}
+
+// The packed tiles, the exponents and the flag live in ws (p.bytes); the
+// flag word (bits 1: eta not 0/+-1, 2: X not finite) is at the end.
+cudaError_t launch_stoch_tc(const sq_ctx* c, const TcPlan& p, const double* eta, const double* X, int n, double* O,
+                            void* ws, int* err, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_stoch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  char* base = static_cast<char*>(ws);
+  uint4* A = reinterpret_cast<uint4*>(base);
+  uint4* B = reinterpret_cast<uint4*>(base + p.a_per_t * p.Tb);
+  int* exps = reinterpret_cast<int*>(base + (p.a_per_t + p.b_per_t) * p.Tb);
+  int* flag = reinterpret_cast<int*>(base + p.bytes - 256);
+  for (int t0 = 0; t0 < p.T; t0 += p.Tb) {
+    const int tb = min(p.Tb, p.T - t0);
+    k_tc_pack_eta<<<dim3(p.nkt, p.nit, tb), 256, 0, s>>>((const double2*)eta, n, p.T, t0, p.K, p.nkt, p.nit, A,
+                                                          flag);
+    k_tc_pack_x<<<dim3(p.nch, p.njt * kTcJ, tb), 256, 0, s>>>((const double2*)X, n, p.T, t0, p.K, p.nkt, p.njt,
+                                                               p.nch, B, exps, flag);
+    k_stoch_tc<<<dim3(p.njt, p.nit, tb), kTcThreads, kTcSmemBytes, s>>>(A, B, exps, n, t0, p.nkt, p.nit, p.njt,
+                                                                         p.nch, (double2*)O, err);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace sq

@@ -99,6 +99,7 @@ _SIG = {
     "sq_contract_pion": (_i, [_vp, _vp, _i, _vp, _vp, _i]),
     "sq_contract_stoch_op": (_i, [_vp, _vp, _vp, _i, _vp, _vp, _i]),
     "sq_contract_prop_trace": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp, _i]),
+    "sq_contract_stoch_op_z4": (_i, [_vp, _vp, _vp, _i, _vp, _vp, _i]),
     "sq_get_profile": (_i, [_vp, C.POINTER(sq_kernel_stat), _i, C.POINTER(_i)]),
     "sq_kernel_launches": (_i, [_vp, C.POINTER(C.c_longlong)]),
     "sq_status_string": (C.c_char_p, [_i]),
@@ -328,12 +329,15 @@ def sq_contract_pion(ctx, solutions, n_rhs: int, src_tslice=None) -> np.ndarray:
     return Cout
 
 
-def sq_contract_stoch_op(ctx, eta, X, n_rhs: int, O=None, C=None, correlator: bool = True):
+def sq_contract_stoch_op(ctx, eta, X, n_rhs: int, O=None, C=None, correlator: bool = True,
+                         tensor_cores: bool = False):
     """Operators O (T, n, n) complex128 and, if correlator, C (T,) complex128.
 
     eta, X: (n, T, Z, Y, X, 4, 3) float64 (or complex128 with the last axis
     folded) arrays, both on the host or both CUDA tensors. Outputs are
-    allocated like the inputs when not given."""
+    allocated like the inputs when not given. tensor_cores: the exact
+    digit-split tensor-core route (sq_contract_stoch_op_z4), for sources with
+    components 0 or +-1."""
     where = _where(eta)
     if _where(X) != where:
         raise ValueError("eta and X must both be host arrays or both device tensors")
@@ -355,8 +359,14 @@ def sq_contract_stoch_op(ctx, eta, X, n_rhs: int, O=None, C=None, correlator: bo
     for a in (O, C):
         if a is not None and _where(a) != where:
             raise ValueError("O and C must live where eta and X do")
-    _check(ctx, _lib.sq_contract_stoch_op(ctx, _ptr(eta), _ptr(X), n, _ptr(O), _ptr(C), where))
+    fn = _lib.sq_contract_stoch_op_z4 if tensor_cores else _lib.sq_contract_stoch_op
+    _check(ctx, fn(ctx, _ptr(eta), _ptr(X), n, _ptr(O), _ptr(C), where))
     return O, C
+
+
+def sq_contract_stoch_op_z4(ctx, eta, X, n_rhs: int, O=None, C=None, correlator: bool = True):
+    """sq_contract_stoch_op on the tensor cores (sources with components 0 or +-1)."""
+    return sq_contract_stoch_op(ctx, eta, X, n_rhs, O, C, correlator, tensor_cores=True)
 
 
 def sq_contract_prop_trace(ctx, etaA, XA, n_rhs: int, etaB=None, XB=None, C=None):

@@ -1,0 +1,119 @@
+"""GPU parity of the tensor-core stochastic operators (sq_contract_stoch_op_z4,
+Eq. stoop) against the FP64 oracle, through the C ABI.
+
+Bar: every element of O and C within 1e-12 of the largest element's
+magnitude, as for the FP64 route. The route is exact up to the truncation
+of gamma5 X to 55 bits below each 4096-row block's largest component and
+FP64 rounding, so the bar holds with a wide margin even when the sources'
+magnitudes differ by e^16 (the inputs below scale each source and
+timeslice by a random factor in [e^-8, e^8]).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import random_spinors
+from paper_1405_4524_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+BAR = 1e-12
+
+
+def close(got, want, bar=BAR):
+    return float(np.max(np.abs(got - want))) <= bar * float(np.max(np.abs(want)))
+
+
+@pytest.fixture(scope="module")
+def sq():
+    from paper_1405_4524_gb300 import stochq
+
+    return stochq
+
+
+def scaled_spinors(dims, n, seed):
+    X = random_spinors(dims, n, seed)
+    rng = np.random.default_rng(seed + 1)
+    f = np.exp(rng.uniform(-8.0, 8.0, (n, dims[3])))
+    return X * f[:, :, None, None, None, None, None]
+
+
+@pytest.mark.parametrize("dims,n", [((2, 2, 2, 2), 3), ((4, 4, 4, 8), 20), ((8, 8, 8, 2), 5),
+                                    ((2, 2, 2, 4), 130)])
+def test_tensor_core_operators_match_oracle(sq, dims, n):
+    """One CTA; two j tiles; two exact chunks of 8192 columns (8^3 slice);
+    two i tiles and nine j tiles with ragged edges (130 sources)."""
+    ctx = sq.sq_create(dims, -1)
+    try:
+        eta = inputs.make_z4(dims, n, 6101 + n)
+        X = scaled_spinors(dims, n, 6201 + n)
+        O, C = sq.sq_contract_stoch_op(ctx, eta, X, n, tensor_cores=True)
+        Ow = oracle.stochastic_operator(eta, X)
+        assert close(O, Ow), float(np.max(np.abs(O - Ow)) / np.max(np.abs(Ow)))
+        assert close(C, oracle.stochastic_operator_correlator(Ow))
+    finally:
+        sq.sq_destroy(ctx)
+
+
+def test_tensor_core_full_size_and_fp64_route(sq):
+    """16^3 x 32 with 16 sources (twelve exact chunks per slice): against the
+    oracle and against the FP64-pipe route."""
+    dims, n = (16, 16, 16, 32), 16
+    ctx = sq.sq_create(dims, -1)
+    try:
+        eta = inputs.make_z4(dims, n, 6301)
+        X = scaled_spinors(dims, n, 6302)
+        O, C = sq.sq_contract_stoch_op(ctx, eta, X, n, tensor_cores=True)
+        Ow = oracle.stochastic_operator(eta, X)
+        assert close(O, Ow)
+        assert close(C, oracle.stochastic_operator_correlator(Ow))
+        O64, _ = sq.sq_contract_stoch_op(ctx, eta, X, n)
+        assert close(O, O64, 1e-13)
+    finally:
+        sq.sq_destroy(ctx)
+
+
+def test_tensor_core_diluted_sources_device_io(sq):
+    """Time-diluted Z4 sources (zero off their timeslice), device I/O equal
+    bitwise to host I/O, repeated calls equal bitwise."""
+    import torch
+
+    dims, n = (4, 4, 4, 8), 8
+    ctx = sq.sq_create(dims, -1)
+    try:
+        eta = inputs.make_z4(dims, n, 6401, [k % 8 for k in range(n)])
+        X = scaled_spinors(dims, n, 6402)
+        O, C = sq.sq_contract_stoch_op(ctx, eta, X, n, tensor_cores=True)
+        Ow = oracle.stochastic_operator(eta, X)
+        assert close(O, Ow)
+        Od, Cd = sq.sq_contract_stoch_op(ctx, torch.from_numpy(eta).cuda(), torch.from_numpy(X).cuda(), n,
+                                         tensor_cores=True)
+        assert np.array_equal(Od.cpu().numpy(), O) and np.array_equal(Cd.cpu().numpy(), C)
+        O2, _ = sq.sq_contract_stoch_op(ctx, eta, X, n, tensor_cores=True)
+        assert np.array_equal(O2, O)
+    finally:
+        sq.sq_destroy(ctx)
+
+
+def test_tensor_core_rejects_general_sources(sq):
+    dims, n = (2, 2, 2, 4), 2
+    ctx = sq.sq_create(dims, -1)
+    try:
+        X = random_spinors(dims, n, 6501)
+        eta = inputs.make_z4(dims, n, 6502)
+        eta[1, 2, 0, 1, 1, 3, 2] = 0.5
+        with pytest.raises(sq.StochqError) as ex:
+            sq.sq_contract_stoch_op(ctx, eta, X, n, tensor_cores=True)
+        assert ex.value.status == sq.SQ_ERR_ARG
+        X[0, 0, 0, 0, 0, 0, 0] = np.inf
+        with pytest.raises(sq.StochqError) as ex:
+            sq.sq_contract_stoch_op(ctx, inputs.make_z4(dims, n, 6502), X, n, tensor_cores=True)
+        assert ex.value.status == sq.SQ_ERR_NONFINITE
+        # the context still works
+        X = random_spinors(dims, n, 6503)
+        eta = inputs.make_z4(dims, n, 6504)
+        O, _ = sq.sq_contract_stoch_op(ctx, eta, X, n, tensor_cores=True)
+        assert close(O, oracle.stochastic_operator(eta, X))
+    finally:
+        sq.sq_destroy(ctx)
