@@ -83,6 +83,15 @@ def job_throughput(n_local: int, world: int, max_ms: float) -> float:
     return n_local * world / (max_ms / 1000.0)
 
 
+def tensor_peak():
+    """Dense bf16 burst TFLOP/s of MEASURED_PEAKS.json (FP16 runs at the same
+    nominal rate), else the fallback measurement."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["bf16_tflops"])
+    return 1900.0
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -524,7 +533,54 @@ def main():
                                 "fill_route_complex_multiplies": fill_cmul,
                                 "note": "device I/O; C[t0][t] for all T^2 pairs from two Gram matrices per "
                                         "timeslice, 3 FP64 FMAs per complex term"}
-        del O_dev, Cs_dev, Cp_dev
+        # the same operators on the tensor cores (exact digit split, sources
+        # with components 0 or +-1) at the bench size, and at the paper's
+        # N_r = 10^3 regime (Sec. "Stochastic propagators": 10^3 noise sources
+        # on the L = 8 lattice): 8^3 x 16 with 1024 Z4 sources, Gaussian X
+        # (the time does not depend on the values)
+        O_dev = torch.zeros((T, n, n), dtype=torch.complex128, device="cuda")
+        sq.sq_contract_stoch_op(ctx, eta_dev, sol_dev, n, O_dev, Cs_dev, tensor_cores=True)
+        e0.record(stream)
+        for _ in range(reps):
+            sq.sq_contract_stoch_op(ctx, eta_dev, sol_dev, n, O_dev, Cs_dev, tensor_cores=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        extras["stoch_op"]["tensor_core_route_us_per_call"] = round(1000.0 * e0.elapsed_time(e1) / reps, 1)
+        dims_tc, n_tc = (8, 8, 8, 16), 1024
+        T_tc = dims_tc[3]
+        ctx_tc = sq.sq_create(dims_tc, -1, stream)
+        eta_tc = torch.from_numpy(inputs.make_z4(dims_tc, n_tc, 7001)).cuda()
+        X_tc = torch.from_numpy(inputs.make_gaussian_spinors(dims_tc, n_tc, 8001)).cuda()
+        O_tc = torch.zeros((T_tc, n_tc, n_tc), dtype=torch.complex128, device="cuda")
+        C_tc = torch.zeros(T_tc, dtype=torch.complex128, device="cuda")
+        sq.sq_contract_stoch_op(ctx_tc, eta_tc, X_tc, n_tc, O_tc, C_tc, tensor_cores=True)
+        e0.record(stream)
+        for _ in range(reps):
+            sq.sq_contract_stoch_op(ctx_tc, eta_tc, X_tc, n_tc, O_tc, C_tc, tensor_cores=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_tc = e0.elapsed_time(e1) / reps
+        e0.record(stream)
+        sq.sq_contract_stoch_op(ctx_tc, eta_tc, X_tc, n_tc, O_tc, C_tc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_tc64 = e0.elapsed_time(e1)
+        terms_tc = float(n_tc) * n_tc * int(np.prod(dims_tc)) * 12
+        bf16_peak = tensor_peak()
+        tflops = 40.0 * terms_tc / (ms_tc / 1000.0) / 1e12
+        extras["stoch_op_tc"] = {"bound": "tensor", "achieved": round(tflops, 1), "peak": bf16_peak,
+                                 "unit": "TFLOP/s", "frac": round(tflops / bf16_peak, 4),
+                                 "workload": "8x8x8x16, 1024 Z4 sources, operators + correlator, device I/O",
+                                 "ms_per_call": round(ms_tc, 3), "fp64_route_ms": round(ms_tc64, 2),
+                                 "speedup_vs_fp64_route": round(ms_tc64 / ms_tc, 1),
+                                 "complex_terms_per_s": round(terms_tc / (ms_tc / 1000.0), 1),
+                                 "flops_per_term": 40,
+                                 "note": "FP16 x FP16 -> FP32 tcgen05 products of 5 exact 11-bit digits of "
+                                         "gamma5 X (real and imaginary rows) against ternary sources; whole "
+                                         "call (packing, products, FP64 digit sums, correlator) against the "
+                                         "measured dense bf16 burst peak (FP16 has the same nominal rate)"}
+        sq.sq_destroy(ctx_tc)
+        del O_dev, Cs_dev, Cp_dev, eta_tc, X_tc, O_tc, C_tc
 
     if args.workloads and rank == 0:
         extras["workloads"] = other_workloads(sq)

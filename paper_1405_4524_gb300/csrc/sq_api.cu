@@ -1,6 +1,7 @@
 // The extern "C" boundary of libstochq (declared in include/stochq.h):
 // argument validation, context and stream handling, host <-> device
 // staging, and dispatch to the kernels of the other translation units.
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cmath>
@@ -551,7 +552,7 @@ sq_status sq_contract_stoch_op(sq_ctx* c, const double* eta, const double* X, in
   const int T = c->dims[3];
   const int nkg = stoch_groups(c, n);
   const size_t ob = (size_t)T * n * n * 2 * sizeof(double), cb = (size_t)T * 2 * sizeof(double);
-  s = grow_contract_scratch(c, ob * nkg);
+  s = grow_contract_scratch(c, std::max(ob * nkg, corr_scratch_bytes(c, n)));
   if (s != SQ_OK) return s;
   cudaError_t e = cudaSuccess;
   const double *deta, *dX;
@@ -569,7 +570,7 @@ sq_status sq_contract_stoch_op(sq_ctx* c, const double* eta, const double* X, in
   }
   if (e == cudaSuccess) {
     launch_stoch_op(c, deta, dX, n, dO, dC, (double*)c->stoch_part, nkg, c->stream);
-    c->launches += C ? 3 : 2;
+    c->launches += C ? 4 : 2;
     e = cudaGetLastError();
   }
   if (where == SQ_HOST) {
@@ -594,9 +595,9 @@ sq_status sq_contract_stoch_op_z4(sq_ctx* c, const double* eta, const double* X,
   sq_status s = enter_stream(c);
   if (s != SQ_OK) return s;
   const TcPlan p = tc_plan(c, n, (size_t)8 << 30);
-  s = grow_contract_scratch(c, p.bytes);
-  if (s != SQ_OK) return s;
   const int T = c->dims[3];
+  s = grow_contract_scratch(c, p.bytes + corr_scratch_bytes(c, n));
+  if (s != SQ_OK) return s;
   const size_t ob = (size_t)T * n * n * 2 * sizeof(double), cb = (size_t)T * 2 * sizeof(double);
   const double *deta, *dX;
   double *teta, *tX = nullptr;
@@ -618,8 +619,9 @@ sq_status sq_contract_stoch_op_z4(sq_ctx* c, const double* eta, const double* X,
   if (e == cudaSuccess) {
     c->launches += 3LL * ((T + p.Tb - 1) / p.Tb);
     if (C) {
-      launch_stoch_corr(c, dO, n, dC, c->stream);
-      c->launches += 1;
+      launch_stoch_corr(c, dO, n, dC, reinterpret_cast<double*>(static_cast<char*>(c->stoch_part) + p.bytes),
+                        c->stream);
+      c->launches += 2;
       e = cudaGetLastError();
     }
   }

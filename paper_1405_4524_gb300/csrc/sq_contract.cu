@@ -156,20 +156,40 @@ __global__ void k_stoch_sum(const double2* part, int n, int T, int nkg, double2*
   O[idx] = make_double2(re, im);
 }
 
-// C[dt] = 1/(n^2 T) sum_t0 sum_ij O_ij((t0 + dt) mod T) O_ji(t0); one CTA per
-// dt, fixed-order tree
-__global__ void __launch_bounds__(256) k_stoch_corr(const double2* O, int n, int T, double2* C) {
-  const int dt = blockIdx.x;
-  double re = 0, im = 0;
+// C[dt] = 1/(n^2 T) sum_t0 S((t0 + dt) mod T, t0), S(ta, tb) = sum_ij
+// O_ij(ta) O_ji(tb). S is symmetric (swap i and j), so only ta >= tb is
+// formed: k_stoch_corr_pairs, grid (pair, group), walks 32 x 32 tiles of
+// O(ta) and the transposed tiles of O(tb) through shared memory (both read
+// along rows), one partial per (pair, group); k_stoch_corr_sum adds the
+// groups and then the timeslices in a fixed order.
+__global__ void __launch_bounds__(256) k_stoch_corr_pairs(const double2* O, int n, int T, int G, double2* part) {
+  const int p = blockIdx.x, g = blockIdx.y;
+  int ta = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
+  while (ta * (ta + 1) / 2 > p) ta--;
+  while ((ta + 1) * (ta + 2) / 2 <= p) ta++;
+  const int tb = p - ta * (ta + 1) / 2;
+  __shared__ double2 sa[32][33], sb[32][33];
   const long long nn = (long long)n * n;
-  for (long long ij = threadIdx.x; ij < nn; ij += blockDim.x) {
-    const int i = (int)(ij / n), j = (int)(ij - (long long)i * n);
-    const long long ji = (long long)j * n + i;
-    for (int t0 = 0, t1 = dt; t0 < T; t0++, t1 = (t1 + 1 == T ? 0 : t1 + 1)) {
-      const double2 a = O[t1 * nn + ij];
-      const double2 b = O[t0 * nn + ji];
-      re += a.x * b.x - a.y * b.y;
-      im += a.x * b.y + a.y * b.x;
+  const int nt = (n + 31) / 32;
+  double re = 0, im = 0;
+  for (int tile = g; tile < nt * nt; tile += G) {
+    const int I = tile / nt, J = tile - (tile / nt) * nt;
+    __syncthreads();
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+      const int r = e >> 5, c = e & 31;
+      const int ia = I * 32 + r, ja = J * 32 + c;  // O(ta)[ia][ja]
+      const int jb = J * 32 + r, ib = I * 32 + c;  // O(tb)[jb][ib]
+      sa[r][c] = (ia < n && ja < n) ? O[ta * nn + (long long)ia * n + ja] : make_double2(0.0, 0.0);
+      sb[r][c] = (jb < n && ib < n) ? O[tb * nn + (long long)jb * n + ib] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+      const int r = e >> 5, c = e & 31;  // i = I*32 + r, j = J*32 + c
+      const double2 a = sa[r][c], b = sb[c][r];
+      re = fma(a.x, b.x, re);
+      re = fma(-a.y, b.y, re);
+      im = fma(a.x, b.y, im);
+      im = fma(a.y, b.x, im);
     }
   }
   __shared__ double sr[8], si[8];
@@ -186,12 +206,47 @@ __global__ void __launch_bounds__(256) k_stoch_corr(const double2* O, int n, int
       a += sr[w];
       b += si[w];
     }
-    const double f = 1.0 / ((double)n * n * T);
-    C[dt] = make_double2(a * f, b * f);
+    part[(long long)p * G + g] = make_double2(a, b);
   }
 }
 
-// K-groups per timeslice: enough CTAs to fill the GPU about four times
+__global__ void k_stoch_corr_sum(const double2* part, int n, int T, int G, double2* C) {
+  const int dt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (dt >= T) return;
+  double a = 0, b = 0;
+  for (int t0 = 0; t0 < T; t0++) {
+    const int t1 = (t0 + dt) % T;
+    const int ta = max(t0, t1), tb = min(t0, t1);
+    const long long p = (long long)ta * (ta + 1) / 2 + tb;
+    double pa = 0, pb = 0;
+    for (int g = 0; g < G; g++) {
+      pa += part[p * G + g].x;
+      pb += part[p * G + g].y;
+    }
+    a += pa;
+    b += pb;
+  }
+  const double f = 1.0 / ((double)n * n * T);
+  C[dt] = make_double2(a * f, b * f);
+}
+
+// groups per timeslice pair of the correlator: about 4 CTAs per SM in all
+int corr_groups(const sq_ctx* c, int n) {
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  const long long T = c->dims[3], pairs = T * (T + 1) / 2;
+  const long long nt = (n + 31) / 32;
+  long long g = (4LL * sms + pairs - 1) / pairs;
+  if (g > nt * nt) g = nt * nt;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+size_t corr_scratch_bytes(const sq_ctx* c, int n) {
+  const long long T = c->dims[3];
+  return (size_t)(T * (T + 1) / 2) * corr_groups(c, n) * 2 * sizeof(double);
+}
+
 // C[t0][t] = 1/n^2 sum_ij P_ji(t) Q_ij(t0) = tr[P(t) Q(t0)] / n^2; one CTA per
 // (t0, t), fixed-order tree
 __global__ void __launch_bounds__(256) k_prop_trace(const double2* P, const double2* Q, int n, int T, double2* C) {
@@ -256,11 +311,13 @@ static void launch_pairs(const sq_ctx* c, bool g5, const double* F, const double
 void launch_stoch_op(const sq_ctx* c, const double* eta, const double* X, int n, double* O, double* C, double* part,
                      int nkg, cudaStream_t s) {
   launch_pairs(c, true, eta, X, n, O, part, nkg, s);
-  if (C) k_stoch_corr<<<c->dims[3], 256, 0, s>>>((const double2*)O, n, c->dims[3], (double2*)C);
+  if (C) launch_stoch_corr(c, O, n, C, part, s);
 }
 
-void launch_stoch_corr(const sq_ctx* c, const double* O, int n, double* C, cudaStream_t s) {
-  k_stoch_corr<<<c->dims[3], 256, 0, s>>>((const double2*)O, n, c->dims[3], (double2*)C);
+void launch_stoch_corr(const sq_ctx* c, const double* O, int n, double* C, double* part, cudaStream_t s) {
+  const int T = c->dims[3], G = corr_groups(c, n);
+  k_stoch_corr_pairs<<<dim3(T * (T + 1) / 2, G), 256, 0, s>>>((const double2*)O, n, T, G, (double2*)part);
+  k_stoch_corr_sum<<<(T + 127) / 128, 128, 0, s>>>((const double2*)part, n, T, G, (double2*)C);
 }
 
 void launch_prop_trace(const sq_ctx* c, const double* etaA, const double* XA, const double* etaB, const double* XB,

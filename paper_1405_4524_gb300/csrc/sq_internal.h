@@ -215,7 +215,8 @@ struct TcPlan {
 TcPlan tc_plan(const sq_ctx* c, int n, size_t cap_bytes);
 cudaError_t launch_stoch_tc(const sq_ctx* c, const TcPlan& p, const double* eta, const double* X, int n, double* O,
                             void* ws, int* err, cudaStream_t s);
-void launch_stoch_corr(const sq_ctx* c, const double* O, int n, double* C, cudaStream_t s);
+void launch_stoch_corr(const sq_ctx* c, const double* O, int n, double* C, double* part, cudaStream_t s);
+size_t corr_scratch_bytes(const sq_ctx* c, int n);
 void launch_prop_trace(const sq_ctx* c, const double* etaA, const double* XA, const double* etaB, const double* XB,
                        int n, double* P, double* Q, double* C, double* part, int nkg, cudaStream_t s);
 

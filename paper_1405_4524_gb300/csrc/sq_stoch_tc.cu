@@ -33,11 +33,12 @@
 //
 // Kernel. One CTA per (16-source j tile, 128-source i tile, timeslice):
 // warp 4 streams the tiles through a 4-stage shared-memory ring with
-// cp.async.bulk, warp 5 issues tcgen05.mma (4 per tile, K = 16 each) into
-// one of two tensor-memory accumulators (one per chunk of 128 tiles, so the
-// epilogue of a chunk overlaps the products of the next), warps 0-3 read
-// the accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31) and add the
-// digits into FP64 registers. Every wait is bounded; on a timeout the CTA
+// cp.async.bulk, warp 5 issues tcgen05.mma (4 per tile, K = 16 each) into a
+// tensor-memory accumulator (one chunk of 128 tiles at a time), warps 0-3
+// read the accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31)
+// and add the digits into FP64 registers. Two CTAs share an SM (3-stage ring, 256 tensor-memory columns
+// each), so one CTA's epilogue overlaps the other's products. Every wait is
+// bounded; on a timeout the CTA
 // records ERRBIT_TIMEOUT, lets its copies and products drain, frees its
 // tensor memory and returns.
 
@@ -52,18 +53,17 @@ constexpr int kTcM = 128;                  // i rows per tile
 constexpr int kTcJ = 16;                   // j sources per tile
 constexpr int kTcN = 10 * kTcJ;            // B rows per tile
 constexpr int kTcK = 64;                   // K' columns per tile (32 complex rows)
-constexpr int kTcStages = 4;
+constexpr int kTcStages = 3;
 constexpr int kTcChunkTiles = 128;         // tiles per exact chunk (8192 columns)
 constexpr int kTcChunkRows = kTcChunkTiles * kTcK / 2;  // complex rows per chunk
 constexpr int kTcABytes = kTcM * kTcK * 2;  // 16384
 constexpr int kTcBBytes = kTcN * kTcK * 2;  // 20480
 constexpr int kTcStageBytes = kTcABytes + kTcBBytes;
-constexpr int kTcTmemCols = 512;           // two accumulators of 160 columns at 0 and 256
+constexpr int kTcTmemCols = 256;           // one accumulator of 160 columns
 constexpr int kTcThreads = 192;
-// dynamic shared memory: the ring, then the barriers; the rest is slack that
-// keeps every address a descriptor can form inside the allocation
-constexpr int kTcBarOffset = kTcStages * kTcStageBytes;  // 147456
-constexpr int kTcSmemBytes = 200 * 1024;
+// dynamic shared memory: the ring, then the barriers; two CTAs per SM
+constexpr int kTcBarOffset = kTcStages * kTcStageBytes;  // 110592
+constexpr int kTcSmemBytes = kTcBarOffset + 256;
 constexpr long long kTcWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
 // ---- PTX wrappers ----------------------------------------------------------
@@ -167,6 +167,16 @@ __device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
   return u;
 }
 
+// FP16 bits of v in {0, +1, -1} from its FP64 bits (integer pipe only);
+// clears ok for any other value (NaN included)
+__device__ __forceinline__ uint32_t ternary_half(double v, bool& ok) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFULL;
+  ok = ok && (mag == 0 || mag == 0x3FF0000000000000ULL);
+  const uint32_t sign = (uint32_t)(b >> 63) << 15;
+  return mag == 0 ? 0u : (sign | 0x3C00u);
+}
+
 // A tiles of timeslices t0 .. t0 + Tb - 1: grid (nkt, n_itiles, Tb), 256 threads.
 // Sets bit 1 of *flag if a component is not 0 or +-1.
 __global__ void __launch_bounds__(256) k_tc_pack_eta(const double2* eta, int n, int T, int t0, long long K,
@@ -174,22 +184,22 @@ __global__ void __launch_bounds__(256) k_tc_pack_eta(const double2* eta, int n, 
   const int kt = blockIdx.x, it = blockIdx.y, tb = blockIdx.z;
   char* blk = reinterpret_cast<char*>(A) + (((long long)tb * nit + it) * nkt + kt) * kTcABytes;
   for (int v = threadIdx.x; v < kTcM * 8; v += blockDim.x) {
-    const int r = v >> 3, q = v & 7;  // row, group of 8 columns = 4 complex rows
+    // row fastest: eight threads fill one 128-byte core matrix
+    const int r = v & (kTcM - 1), q = v >> 7;  // row, group of 8 columns = 4 complex rows
     const int i = it * kTcM + r;
-    float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    uint32_t h[4] = {0, 0, 0, 0};
     if (i < n) {
       const double2* src = eta + ((long long)i * T + t0 + tb) * K + (long long)kt * (kTcK / 2) + q * 4;
       bool ok = true;
 #pragma unroll
       for (int c = 0; c < 4; c++) {
         const double2 d = src[c];
-        ok = ok && (d.x == 0.0 || d.x == 1.0 || d.x == -1.0) && (d.y == 0.0 || d.y == 1.0 || d.y == -1.0);
-        f[2 * c] = (float)d.x;
-        f[2 * c + 1] = (float)d.y;
+        const uint32_t lo = ternary_half(d.x, ok), hi = ternary_half(d.y, ok);
+        h[c] = lo | (hi << 16);
       }
       if (!ok) atomicOr(flag, 1);
     }
-    *reinterpret_cast<uint4*>(blk + tile_offset(kTcM, r, q * 8)) = pack8(f);
+    *reinterpret_cast<uint4*>(blk + tile_offset(kTcM, r, q * 8)) = make_uint4(h[0], h[1], h[2], h[3]);
   }
 }
 
@@ -211,45 +221,56 @@ __device__ __forceinline__ float digit(long long m, int s) {
 }
 
 // B tiles and chunk exponents of timeslices t0 .. t0 + Tb - 1: grid (nch,
-// n_jtiles * 16, Tb), 256 threads. Sets bit 2 of *flag on a non-finite x.
+// njt, Tb), 256 threads; a CTA handles the 16 sources of a j tile so that
+// 16 consecutive threads fill two adjacent core matrices. Sets bit 2 of
+// *flag on a non-finite x.
 __global__ void __launch_bounds__(256) k_tc_pack_x(const double2* X, int n, int T, int t0, long long K, int nkt,
                                                    int njt, int nch, uint4* B, int* exps, int* flag) {
-  const int ch = blockIdx.x, j = blockIdx.y, tb = blockIdx.z;
+  const int ch = blockIdx.x, jt = blockIdx.y, tb = blockIdx.z;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long r0 = (long long)ch * kTcChunkRows;
   const long long r1 = min(K, r0 + kTcChunkRows);
-  const double2* src = X + ((long long)j * T + t0 + tb) * K;
-  // largest |component| of the chunk (as bits: order-preserving for |x|)
-  unsigned long long mx = 0;
-  if (j < n)
-    for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-      const double2 d = src[r];
-      mx = max(mx, (unsigned long long)__double_as_longlong(d.x) & 0x7FFFFFFFFFFFFFFFULL);
-      mx = max(mx, (unsigned long long)__double_as_longlong(d.y) & 0x7FFFFFFFFFFFFFFFULL);
-    }
-  __shared__ unsigned long long smx[8];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) smx[threadIdx.x >> 5] = mx;
+  __shared__ int se[kTcJ];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
   __syncthreads();
-  mx = smx[0];
-  for (int w = 1; w < (int)(blockDim.x >> 5); w++) mx = max(mx, smx[w]);
-  const int Eb = (int)(mx >> 52);
-  if (Eb == 0x7ff) {
+  // largest |component| of the chunk per source (bits order |x| for x >= 0)
+  for (int jl = warp; jl < kTcJ; jl += blockDim.x >> 5) {
+    const int j = jt * kTcJ + jl;
+    unsigned long long mx = 0;
+    if (j < n) {
+      const double2* src = X + ((long long)j * T + t0 + tb) * K;
+      for (long long r = r0 + lane; r < r1; r += 32) {
+        const double2 d = src[r];
+        mx = max(mx, (unsigned long long)__double_as_longlong(d.x) & 0x7FFFFFFFFFFFFFFFULL);
+        mx = max(mx, (unsigned long long)__double_as_longlong(d.y) & 0x7FFFFFFFFFFFFFFFULL);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) {
+      const int Eb = (int)(mx >> 52);
+      if (Eb == 0x7ff) bad = 1;
+      const int e = mx == 0 ? 0 : Eb - 1023 + 1;  // |x| < 2^e
+      se[jl] = e;
+      exps[((long long)tb * njt * kTcJ + jt * kTcJ + jl) * nch + ch] = e;
+    }
+  }
+  __syncthreads();
+  if (bad) {
     if (threadIdx.x == 0) atomicOr(flag, 2);
     return;
   }
-  const int e = mx == 0 ? 0 : Eb - 1023 + 1;  // |x| < 2^e
-  if (threadIdx.x == 0) exps[((long long)tb * njt * kTcJ + j) * nch + ch] = e;
-  const int jt = j / kTcJ, jl = j - jt * kTcJ;
   const int kt0 = ch * kTcChunkTiles, kt1 = min(nkt, kt0 + kTcChunkTiles);
-  for (int v = threadIdx.x; v < (kt1 - kt0) * 8; v += blockDim.x) {
-    const int kt = kt0 + (v >> 3), q = v & 7;
+  for (int v = threadIdx.x; v < (kt1 - kt0) * 8 * kTcJ; v += blockDim.x) {
+    const int jl = v & (kTcJ - 1), q = (v >> 4) & 7, kt = kt0 + (v >> 7);
+    const int j = jt * kTcJ + jl, e = se[jl];
     const long long row = (long long)kt * (kTcK / 2) + q * 4;
     long long mr[4], mi[4];
 #pragma unroll
     for (int c = 0; c < 4; c++) {
       double2 d = make_double2(0.0, 0.0);
-      if (j < n) d = src[row + c];
+      if (j < n) d = X[((long long)j * T + t0 + tb) * K + row + c];
       mr[c] = fixed55(d.x, e);
       mi[c] = fixed55(d.y, e);
       if (((row + c) % 12) >= 6) {  // gamma5 = -1 on spins 2, 3
@@ -275,17 +296,17 @@ __global__ void __launch_bounds__(256) k_tc_pack_x(const double2* X, int n, int 
 }
 
 // ---- the product -----------------------------------------------------------
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 2)
     k_stoch_tc(const uint4* A, const uint4* B, const int* exps, int n, int t0, int nkt, int nit, int njt, int nch,
                double2* O, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int jt = blockIdx.x, it = blockIdx.y, tb = blockIdx.z;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kTcBarOffset);
-  // bars: full[4], empty[4], accf[2], acce[2], done
+  // bars: full[stages], empty[stages], accf, acce, done
   const uint32_t full0 = smem_addr(bars), empty0 = full0 + 8 * kTcStages;
-  const uint32_t accf0 = empty0 + 8 * kTcStages, acce0 = accf0 + 16, done = acce0 + 16;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kTcBarOffset + 8 * (2 * kTcStages + 5));
+  const uint32_t accf = empty0 + 8 * kTcStages, acce = accf + 8, done = acce + 8;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kTcBarOffset + 8 * (2 * kTcStages + 3));
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
 
   // a timeout anywhere in this launch stops the CTAs that have not started
@@ -298,10 +319,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    for (int b = 0; b < 2; b++) {
-      mbar_init(accf0 + 8 * b, 1);
-      mbar_init(acce0 + 8 * b, 128);
-    }
+    mbar_init(accf, 1);
+    mbar_init(acce, 128);
     mbar_init(done, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -322,8 +341,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t ring = smem_addr(smem);
 
   if (warp == 4) {
-    // producer: tile kt into stage kt % 4 once the products of tile kt - 4
-    // are done (the whole warp waits, lane 0 issues)
+    // producer: tile kt into stage kt % stages once the products of the
+    // tile before it in that stage are done (the whole warp waits, lane 0
+    // issues)
     int kt = 0;
     for (; kt < nkt; kt++) {
       const int s = kt % kTcStages;
@@ -339,12 +359,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int k = max(0, kt - kTcStages); k < kt; k++)
       tc_wait(full0 + 8 * (k % kTcStages), (k / kTcStages) & 1, abort, err, false);
   } else if (warp == 5) {
-    // products (the whole warp waits, lane 0 issues): chunk c accumulates
-    // in tensor columns (c & 1) * 256
+    // products (the whole warp waits, lane 0 issues); chunk c starts once
+    // the epilogue has read chunk c - 1
     for (int kt = 0; kt < nkt; kt++) {
-      const int s = kt % kTcStages, c = kt / kTcChunkTiles, buf = c & 1;
+      const int s = kt % kTcStages, c = kt / kTcChunkTiles;
       const bool first = (kt % kTcChunkTiles) == 0;
-      if (first && c >= 2 && !tc_wait(acce0 + 8 * buf, ((c - 2) >> 1) & 1, abort, err, true)) break;
+      if (first && c >= 1 && !tc_wait(acce, (c - 1) & 1, abort, err, true)) break;
       if (!tc_wait(full0 + 8 * s, (kt / kTcStages) & 1, abort, err, true)) break;
       tc_fence_after();
       if (lane == 0) {
@@ -353,10 +373,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int ks = 0; ks < kTcK / 16; ks++) {
           const uint64_t ad = smem_desc(a0 + ks * 2 * (kTcM * 16), kTcM * 16, 128);
           const uint64_t bd = smem_desc(b0 + ks * 2 * (kTcN * 16), kTcN * 16, 128);
-          tc_mma(tmem + buf * 256, ad, bd, kTcIdesc, (first && ks == 0) ? 0u : 1u);
+          tc_mma(tmem, ad, bd, kTcIdesc, (first && ks == 0) ? 0u : 1u);
         }
         tc_commit(empty0 + 8 * s);
-        if ((kt % kTcChunkTiles) == kTcChunkTiles - 1 || kt == nkt - 1) tc_commit(accf0 + 8 * buf);
+        if ((kt % kTcChunkTiles) == kTcChunkTiles - 1 || kt == nkt - 1) tc_commit(accf);
       }
       __syncwarp();
     }
@@ -370,13 +390,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int q = 0; q < kTcJ; q++) re[q] = im[q] = 0.0;
     const int* ex = exps + ((long long)tb * njt * kTcJ + jt * kTcJ) * nch;
     for (int c = 0; c < nch; c++) {
-      const int buf = c & 1;
-      if (!tc_wait(accf0 + 8 * buf, (c >> 1) & 1, abort, err, true)) break;
+      if (!tc_wait(accf, c & 1, abort, err, true)) break;
       tc_fence_after();
       int e[kTcJ];
 #pragma unroll
       for (int q = 0; q < kTcJ; q++) e[q] = ex[q * nch + c];
-      const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16) + buf * 256;
+      const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
 #pragma unroll 1
       for (int s = 0; s < 5; s++) {
         uint32_t vr[16], vi[16];
@@ -391,7 +410,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
       }
       tc_fence_before();
-      mbar_arrive(acce0 + 8 * buf);
+      mbar_arrive(acce);
     }
     const int i = it * kTcM + warp * 32 + lane;
     if (i < n && !*abort) {
@@ -450,7 +469,7 @@ cudaError_t launch_stoch_tc(const sq_ctx* c, const TcPlan& p, const double* eta,
     const int tb = min(p.Tb, p.T - t0);
     k_tc_pack_eta<<<dim3(p.nkt, p.nit, tb), 256, 0, s>>>((const double2*)eta, n, p.T, t0, p.K, p.nkt, p.nit, A,
                                                           flag);
-    k_tc_pack_x<<<dim3(p.nch, p.njt * kTcJ, tb), 256, 0, s>>>((const double2*)X, n, p.T, t0, p.K, p.nkt, p.njt,
+    k_tc_pack_x<<<dim3(p.nch, p.njt, tb), 256, 0, s>>>((const double2*)X, n, p.T, t0, p.K, p.nkt, p.njt,
                                                                p.nch, B, exps, flag);
     k_stoch_tc<<<dim3(p.njt, p.nit, tb), kTcThreads, kTcSmemBytes, s>>>(A, B, exps, n, t0, p.nkt, p.nit, p.njt,
                                                                          p.nch, (double2*)O, err);

@@ -27,6 +27,7 @@ import numpy as np
 
 __all__ = [
     "WORKLOADS",
+    "make_gaussian_spinors",
     "make_links",
     "make_z4",
     "reunitarize",
@@ -90,6 +91,19 @@ def make_z4(dims, n: int, seed: int, tslices=None) -> np.ndarray:
             keep = np.zeros(T, dtype=bool)
             keep[int(tslices[k]) % T] = True
             out[k, ~keep] = 0.0
+    return out
+
+
+def make_gaussian_spinors(dims, n: int, seed: int) -> np.ndarray:
+    """``n`` spinor fields with iid standard normal real and imaginary parts;
+    field k draws from ``default_rng(seed + k)`` (real parts, then imaginary
+    parts, C order)."""
+    X, Y, Z, T = (int(d) for d in dims)
+    out = np.empty((n, T, Z, Y, X, 4, 3), dtype=np.complex128)
+    for k in range(n):
+        rng = np.random.default_rng(seed + k)
+        re = rng.standard_normal((T, Z, Y, X, 4, 3))
+        out[k] = re + 1j * rng.standard_normal((T, Z, Y, X, 4, 3))
     return out
 
 

@@ -117,3 +117,25 @@ def test_tensor_core_rejects_general_sources(sq):
         assert close(O, oracle.stochastic_operator(eta, X))
     finally:
         sq.sq_destroy(ctx)
+
+
+def test_tensor_core_many_sources(sq):
+    """256 sources on 8^3 x 16 (2 i tiles x 16 j tiles per timeslice, two
+    exact chunks): sampled pairs against the oracle, every element against
+    the FP64-pipe route."""
+    dims, n = (8, 8, 8, 16), 256
+    ctx = sq.sq_create(dims, -1)
+    try:
+        eta = inputs.make_z4(dims, n, 6601)
+        X = inputs.make_gaussian_spinors(dims, n, 6701)
+        O, C = sq.sq_contract_stoch_op(ctx, eta, X, n, tensor_cores=True)
+        rng = np.random.default_rng(6801)
+        scale = float(np.max(np.abs(O)))
+        for i, j in zip(rng.integers(0, n, 12), rng.integers(0, n, 12)):
+            want = oracle.stochastic_operator(eta[[i]], X[[j]])[:, 0, 0]
+            assert float(np.max(np.abs(O[:, i, j] - want))) <= BAR * scale
+        O64, C64 = sq.sq_contract_stoch_op(ctx, eta, X, n)
+        assert close(O, O64, 1e-13)
+        assert close(C, C64, 1e-12)
+    finally:
+        sq.sq_destroy(ctx)
