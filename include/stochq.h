@@ -283,6 +283,26 @@ typedef struct sq_problem {
 sq_status sq_solve_batch(const sq_problem *probs, int n_probs,
                          const sq_solve_params *params, sq_solve_stats *stats);
 
+/* Dilution schemes of sq_dilute (Sec. "Stochastic propagators": the
+ * paper's time-spin-colour dilution). */
+enum { SQ_DILUTE_TIME = 1, SQ_DILUTE_SPIN_COLOUR = 2, SQ_DILUTE_FULL = 3 };
+
+/* Diluted sources from noise vectors: D = T (time), 12 (spin-colour) or 12*T
+ * (full) sources per noise vector, source k*D + d keeping noise vector k on
+ * timeslice t = d (time), spin-colour component a = d = 3*spin + colour
+ * (spin-colour) or t = d / 12 and a = d % 12 (full), zero elsewhere. The
+ * sources of one noise vector sum to it and have disjoint supports. A noise
+ * vector equal to 1 on the twelve components of one site and 0 elsewhere
+ * gives, with SQ_DILUTE_SPIN_COLOUR, the twelve point sources of the point
+ * propagator at that site. noise: n_noise lexicographic FP64 fields; out:
+ * n_noise * D fields, same layout; both host or both device memory per
+ * `where`, owned by the caller. Host memory: returns when out is written;
+ * device memory: ordered after the caller's stream, no wait.
+ * Errors: SQ_ERR_ARG (NULL, n_noise <= 0, unknown scheme, bad where),
+ * SQ_ERR_CUDA. */
+sq_status sq_dilute(sq_ctx *ctx, const double *noise, int n_noise, int scheme,
+                    double *out, int where);
+
 /* Pion correlator of each solution vector (the zero-momentum contraction
  * sum_{x in t} sum_y tr S S^+ of Sec. "Stochastic propagators", estimated
  * per source):  C[k][dt] = sum over sites x on timeslice (t_k + dt) mod T

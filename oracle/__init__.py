@@ -19,6 +19,7 @@ from .dirac import (  # noqa: F401
     clover_apply,
     clover_matrices,
     dagger,
+    dilute,
     field_strength,
     hopping,
     hopping_eo,

@@ -43,7 +43,8 @@ even-odd formulas), brute-force loops and the exact expectation value for
 the pion contraction and for the stochastic-operator contraction O_ij(t)
 (with O_ii = 0 for X = eta as a special case); brute-force loops, the
 point-source limit and the exact expectation value for the traces of
-filled stochastic propagators. Parity unpinned: the overall sign of the clover term
+filled stochastic propagators; completeness, disjoint supports and the
+exact point propagator from a one-site noise vector for the dilution. Parity unpinned: the overall sign of the clover term
 (+i kappa c_sw) is the Sheikholeslami-Wohlert / Luscher-Sint-Sommer-Weisz
 convention and is fixed by that citation only; no invariant above changes
 when it flips.
@@ -364,6 +365,36 @@ def stochastic_operator_correlator(O: np.ndarray) -> np.ndarray:
         for t0 in range(T):
             C[dt] += np.sum(O[(t0 + dt) % T] * O[t0].T)
     return C / (n * n * T)
+
+
+def dilute(noise: np.ndarray, scheme: str) -> np.ndarray:
+    """Time, spin-colour or full (time-spin-colour) dilution of noise vectors
+    (Sec. "Stochastic propagators"): for each noise vector, one source per
+    timeslice t ("time"), per spin-colour component a = 3*spin + colour
+    ("spin_colour") or per pair (t, a) in the order 12*t + a ("full"), equal
+    to the noise on that part and zero elsewhere. noise: (n, T, Z, Y, X, 4, 3);
+    returns (n * D, T, Z, Y, X, 4, 3)."""
+    n, T = noise.shape[0], noise.shape[1]
+    parts = []
+    if scheme == "time":
+        parts = [(t, None) for t in range(T)]
+    elif scheme == "spin_colour":
+        parts = [(None, a) for a in range(12)]
+    elif scheme == "full":
+        parts = [(t, a) for t in range(T) for a in range(12)]
+    else:
+        raise ValueError(scheme)
+    out = []
+    for k in range(n):
+        for t, a in parts:
+            mask = np.zeros(noise.shape[1:], dtype=bool)
+            tt = slice(None) if t is None else t
+            if a is None:
+                mask[tt] = True
+            else:
+                mask[tt, :, :, :, a // 3, a % 3] = True
+            out.append(np.where(mask, noise[k], 0.0))
+    return np.array(out)
 
 
 def stochastic_propagator(eta: np.ndarray, X: np.ndarray, t0: int) -> np.ndarray:

@@ -496,6 +496,37 @@ sq_status sq_solve(sq_ctx* c, double kappa, double csw, const double* sources, d
   return s != SQ_OK ? s : s2;
 }
 
+sq_status sq_dilute(sq_ctx* c, const double* noise, int n_noise, int scheme, double* out, int where) {
+  if (!c) return SQ_ERR_ARG;
+  const int D = dilution_count(c, scheme);
+  if (!noise || !out || n_noise <= 0 || D == 0 || (where != SQ_HOST && where != SQ_DEVICE))
+    return set_error(c, SQ_ERR_ARG, "sq_dilute: bad argument");
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  const double* dev;
+  double* tmp;
+  s = stage_in(c, noise, n_noise, where, &dev, &tmp);
+  if (s != SQ_OK) return s;
+  const size_t ob = (size_t)n_noise * D * c->V * 24 * sizeof(double);
+  double* dout = out;
+  cudaError_t e = cudaSuccess;
+  if (where == SQ_HOST) e = cudaMallocAsync((void**)&dout, ob, c->stream);
+  if (e == cudaSuccess) {
+    launch_dilute(c, dev, n_noise, scheme, dout, c->stream);
+    c->launches += 1;
+    e = cudaGetLastError();
+  }
+  if (where == SQ_HOST) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, ob, cudaMemcpyDeviceToHost, c->stream);
+    if (dout && dout != out) cudaFreeAsync(dout, c->stream);
+  }
+  if (tmp) cudaFreeAsync(tmp, c->stream);
+  if (e == cudaSuccess && where == SQ_HOST) e = cudaStreamSynchronize(c->stream);
+  s = cuda_check(c, e, "sq_dilute");
+  if (s != SQ_OK) return s;
+  return leave_stream(c);
+}
+
 sq_status sq_contract_pion(sq_ctx* c, const double* sol, int n, const int* tsl, double* C, int where) {
   if (!c) return SQ_ERR_ARG;
   if (!sol || !C || n <= 0 || (where != SQ_HOST && where != SQ_DEVICE))

@@ -200,6 +200,10 @@ sq_status solve_batch_impl(const sq_problem* probs, int n_probs, const sq_solve_
 
 void release_workspace(sq_ctx* c);
 
+// ---- dilution (sq_dilute.cu)
+int dilution_count(const sq_ctx* c, int scheme);  // sources per noise vector, 0 if scheme is unknown
+void launch_dilute(const sq_ctx* c, const double* noise, int n_noise, int scheme, double* out, cudaStream_t s);
+
 // ---- contraction (sq_contract.cu)
 void launch_pion(const sq_ctx* c, const double* lex, int n, const int* tsl, double* C, cudaStream_t s);
 int stoch_groups(const sq_ctx* c, int n);

@@ -23,6 +23,7 @@ SQ_F64, SQ_F32, SQ_F16 = 0, 1, 2
 SQ_HOST, SQ_DEVICE = 0, 1
 SQ_DS_CLOVER_INV, SQ_DS_XPAY, SQ_DS_SYNC = 1, 2, 4
 SQ_OUTER_RELIABLE, SQ_OUTER_DEFECT = 0, 1
+SQ_DILUTE_TIME, SQ_DILUTE_SPIN_COLOUR, SQ_DILUTE_FULL = 1, 2, 3
 
 STATUS = {
     0: "SQ_OK", 1: "SQ_ERR_ARG", 2: "SQ_ERR_CUDA", 3: "SQ_ERR_OOM",
@@ -100,6 +101,7 @@ _SIG = {
     "sq_contract_stoch_op": (_i, [_vp, _vp, _vp, _i, _vp, _vp, _i]),
     "sq_contract_prop_trace": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp, _i]),
     "sq_contract_stoch_op_z4": (_i, [_vp, _vp, _vp, _i, _vp, _vp, _i]),
+    "sq_dilute": (_i, [_vp, _vp, _i, _i, _vp, _i]),
     "sq_get_profile": (_i, [_vp, C.POINTER(sq_kernel_stat), _i, C.POINTER(_i)]),
     "sq_kernel_launches": (_i, [_vp, C.POINTER(C.c_longlong)]),
     "sq_status_string": (C.c_char_p, [_i]),
@@ -312,6 +314,26 @@ def sq_solve_batch(problems, params: sq_solve_params | None = None, raise_on_err
     if raise_on_error and st != 0:
         raise StochqError(st, sq_last_error(problems[0]["ctx"]), out)
     return st, out
+
+
+def sq_dilute(ctx, noise, n_noise: int, scheme: int, out=None):
+    """Diluted sources (n_noise * D, T, Z, Y, X, 4, 3), D = T, 12 or 12 T for
+    SQ_DILUTE_TIME, SQ_DILUTE_SPIN_COLOUR, SQ_DILUTE_FULL; allocated like
+    ``noise`` (host array or CUDA tensor) when not given."""
+    where = _where(noise)
+    T = int(noise.shape[1])
+    D = {SQ_DILUTE_TIME: T, SQ_DILUTE_SPIN_COLOUR: 12, SQ_DILUTE_FULL: 12 * T}.get(int(scheme), 1)
+    shape = (int(n_noise) * D,) + tuple(noise.shape[1:])
+    if out is None:
+        if where == SQ_HOST:
+            out = np.zeros(shape, dtype=noise.dtype)
+        else:
+            import torch
+            out = torch.zeros(shape, dtype=noise.dtype, device=noise.device)
+    elif _where(out) != where:
+        raise ValueError("out must live where noise does")
+    _check(ctx, _lib.sq_dilute(ctx, _ptr(noise), int(n_noise), int(scheme), _ptr(out), where))
+    return out
 
 
 def sq_contract_pion(ctx, solutions, n_rhs: int, src_tslice=None) -> np.ndarray:

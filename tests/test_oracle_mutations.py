@@ -240,3 +240,41 @@ def test_propagator_trace_mutation_is_caught(kind, monkeypatch):
     monkeypatch.setattr(dirac, attr, fn)
     monkeypatch.setattr(oracle, attr, fn)
     assert not _run_pins(FILL_PINS), f"mutation not caught: {kind}"
+
+
+def _dilute_component_major(noise, scheme):
+    """full dilution enumerated component-major (d = T*a + t) instead of 12*t + a"""
+    out = _orig_dilute(noise, scheme)
+    if scheme != "full":
+        return out
+    n, T = noise.shape[0], noise.shape[1]
+    idx = [12 * t + a for a in range(12) for t in range(T)]
+    return np.concatenate([out[k * 12 * T:(k + 1) * 12 * T][idx] for k in range(n)])
+
+
+def _dilute_shifted_time(noise, scheme):
+    """time index off by one"""
+    out = _orig_dilute(noise, scheme)
+    if scheme != "time":
+        return out
+    n, T = noise.shape[0], noise.shape[1]
+    return np.concatenate([np.roll(out[k * T:(k + 1) * T], 1, axis=0) for k in range(n)])
+
+
+_orig_dilute = dirac.dilute
+DILUTION_PINS = ["test_dilution_completeness_and_supports"]
+
+
+@pytest.mark.parametrize("fn", [_dilute_component_major, _dilute_shifted_time])
+def test_dilution_mutation_is_caught(fn, monkeypatch):
+    import oracle
+
+    monkeypatch.setattr(dirac, "dilute", fn)
+    monkeypatch.setattr(oracle, "dilute", fn)
+    caught = False
+    for scheme, D in [("time", 4), ("spin_colour", 12), ("full", 48)]:
+        try:
+            pins.test_dilution_completeness_and_supports(scheme, D)
+        except AssertionError:
+            caught = True
+    assert caught

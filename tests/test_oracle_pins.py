@@ -540,3 +540,53 @@ def test_propagator_trace_gram_identity():
                     Q = np.vdot(eA[i, t0], eB[j, t0])
                     G[t0, t] += P * Q
     assert np.allclose(C, G / n**2, rtol=1e-12, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# dilution (time, spin-colour, full) and point sources
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("scheme,D", [("time", 4), ("spin_colour", 12), ("full", 48)])
+def test_dilution_completeness_and_supports(scheme, D):
+    """The D sources of a noise vector sum to it, their supports are
+    disjoint, and each keeps exactly its timeslice / component (explicit
+    loops over the index space)."""
+    dims = (2, 2, 2, 4)
+    noise = inputs.make_z4(dims, 2, 81)
+    out = oracle.dilute(noise, scheme)
+    assert out.shape == (2 * D,) + noise.shape[1:]
+    for k in range(2):
+        blk = out[k * D:(k + 1) * D]
+        assert np.array_equal(blk.sum(axis=0), noise[k])
+        assert np.all(np.count_nonzero(blk, axis=0) == 1)  # Z4 noise is nowhere zero
+        for d in range(D):
+            for t in range(4):
+                for s in range(4):
+                    for c in range(3):
+                        a = 3 * s + c
+                        keep = {"time": t == d, "spin_colour": a == d,
+                                "full": (t == d // 12 and a == d % 12)}[scheme]
+                        got = blk[d][t, :, :, :, s, c]
+                        assert np.array_equal(got, noise[k][t, :, :, :, s, c] if keep else 0 * got)
+
+
+def test_full_dilution_of_a_one_site_noise_is_the_point_propagator():
+    """A noise vector that is 1 on the twelve components of one site: its
+    twelve spin-colour diluted sources are the point sources there, and the
+    estimate sum_a X_a eta_a^dag (Eq. Sfill with N_r = 1) is the column block
+    M^{-1}(., y0) of the dense inverse exactly."""
+    dims = (4, 2, 2, 4)
+    X, Y, Z, T = dims
+    U = inputs.make_links(dims, 0.25, 61)
+    F = oracle.field_strength(U)
+    M = dense_M(U, F, 0.12, 1.0, -1.0, dims)
+    S = np.linalg.inv(M)
+    y0 = (2, 1, 0, 1)  # t, z, y, x
+    noise = np.zeros((1, T, Z, Y, X, 4, 3), dtype=np.complex128)
+    noise[(0,) + y0] = 1.0
+    src = oracle.dilute(noise, "spin_colour")
+    sol = np.array([np.linalg.solve(M, src[a].reshape(-1)) for a in range(12)])
+    est = np.einsum("ai,ab->ib", sol, np.conj(src.reshape(12, -1))[:, :])  # (V*12, V*12)
+    site = ((y0[0] * Z + y0[1]) * Y + y0[2]) * X + y0[3]
+    cols = slice(12 * site, 12 * site + 12)
+    assert np.allclose(est[:, cols], S[:, cols], rtol=0, atol=1e-12)
