@@ -151,6 +151,24 @@ void sq_default_params(sq_solve_params *p);
  * Errors: SQ_ERR_ARG (bad dims/t_bc/NULL ctx), SQ_ERR_CUDA. */
 sq_status sq_create(sq_ctx **ctx, const int dims[4], int t_bc, void *cuda_stream);
 
+/* Caller-supplied device memory for the context's persistent buffers (gauge
+ * copies, clover terms, solver workspaces, contraction and profiling
+ * scratch), e.g. a framework's caching allocator. alloc returns a device
+ * pointer to at least `bytes` bytes, 256-byte aligned, or NULL (reported as
+ * SQ_ERR_OOM / SQ_ERR_CUDA by the call that needed it); free releases a
+ * pointer alloc returned, with the same size. `stream` is the context's
+ * cudaStream_t, on which the buffer is used; the library synchronises that
+ * stream before it frees a buffer, so free may reuse the memory at once.
+ * `user` is passed through. Both NULL restores cudaMalloc / cudaFree (the
+ * default). Per-call staging buffers for host I/O stay on the CUDA
+ * stream-ordered pool (cudaMallocAsync on the context's stream), and the
+ * context's 4-byte device error word is allocated by sq_create.
+ * Errors: SQ_ERR_ARG (only one of alloc/free given), SQ_ERR_STATE (the
+ * context already holds persistent buffers: call it before sq_load_gauge). */
+typedef void *(*sq_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*sq_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+sq_status sq_set_allocator(sq_ctx *ctx, sq_alloc_fn alloc, sq_free_fn free_fn, void *user);
+
 /* Free everything the context owns. NULL is accepted. */
 sq_status sq_destroy(sq_ctx *ctx);
 

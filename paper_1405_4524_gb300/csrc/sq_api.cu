@@ -78,10 +78,31 @@ sq_status read_error_word(sq_ctx* c, int* bits) {
   return cuda_check(c, e, "device error word");
 }
 
-static void free_clover(CloverSet& cs) {
-  cudaFree(cs.A64);
-  cudaFree(cs.Ainv64);
-  cudaFree(cs.Ainv32);
+cudaError_t dev_alloc(const Allocator& a, void** p, size_t bytes) {
+  if (!a.alloc) return cudaMalloc(p, bytes);
+  *p = a.alloc(bytes, (void*)a.stream, a.user);
+  return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+
+void dev_free(const Allocator& a, void* p, size_t bytes) {
+  if (!p) return;
+  if (!a.free) {
+    cudaFree(p);
+    return;
+  }
+  cudaStreamSynchronize(a.stream);  // cudaFree would have waited too
+  a.free(p, bytes, (void*)a.stream, a.user);
+}
+
+static size_t gauge32_bytes(const sq_ctx* c, int recon) {
+  return recon == 12 ? 2 * 4 * 3 * (size_t)c->Vh * sizeof(float4) : 2 * 4 * 9 * (size_t)c->Vh * sizeof(float2);
+}
+
+static void free_clover(sq_ctx* c, CloverSet& cs) {
+  const size_t Vh = c->Vh;
+  dev_free(c->mem, cs.A64, 2 * 36 * Vh * sizeof(double2));
+  dev_free(c->mem, cs.Ainv64, 2 * 36 * Vh * sizeof(double2));
+  dev_free(c->mem, cs.Ainv32, 2 * 18 * Vh * sizeof(float4));
   cs = CloverSet();
 }
 
@@ -112,11 +133,11 @@ sq_status find_clover(sq_ctx* c, double kappa, double csw, CloverSet** out) {
   cs.valid = 0;
   const size_t Vh = c->Vh;
   cudaError_t e = cudaSuccess;
-  if (!cs.A64) e = cudaMalloc((void**)&cs.A64, 2 * 36 * Vh * sizeof(double2));
-  if (e == cudaSuccess && !cs.Ainv64) e = cudaMalloc((void**)&cs.Ainv64, 2 * 36 * Vh * sizeof(double2));
-  if (e == cudaSuccess && !cs.Ainv32) e = cudaMalloc((void**)&cs.Ainv32, 2 * 18 * Vh * sizeof(float4));
+  if (!cs.A64) e = dev_alloc(c->mem, (void**)&cs.A64, 2 * 36 * Vh * sizeof(double2));
+  if (e == cudaSuccess && !cs.Ainv64) e = dev_alloc(c->mem, (void**)&cs.Ainv64, 2 * 36 * Vh * sizeof(double2));
+  if (e == cudaSuccess && !cs.Ainv32) e = dev_alloc(c->mem, (void**)&cs.Ainv32, 2 * 18 * Vh * sizeof(float4));
   if (e != cudaSuccess) {
-    free_clover(cs);
+    free_clover(c, cs);
     return cuda_check(c, e, "clover allocation");
   }
   sq_status s = clover_build(c, cs, kappa, csw);
@@ -197,9 +218,22 @@ sq_status sq_create(sq_ctx** out, const int dims[4], int t_bc, void* cuda_stream
     return e == cudaErrorMemoryAllocation ? SQ_ERR_OOM : SQ_ERR_CUDA;
   }
   c->user_stream = (cudaStream_t)cuda_stream;
+  c->mem.stream = c->stream;
   static std::atomic<unsigned long long> next_uid{1};
   c->uid = next_uid++;
   *out = c;
+  return SQ_OK;
+}
+
+sq_status sq_set_allocator(sq_ctx* c, sq_alloc_fn alloc, sq_free_fn free_fn, void* user) {
+  if (!c) return SQ_ERR_ARG;
+  if ((!alloc) != (!free_fn)) return set_error(c, SQ_ERR_ARG, "sq_set_allocator: give both callbacks or neither");
+  bool held = c->U64 || c->U32 || c->stoch_part || c->ws.base || c->batch;
+  for (auto& cs : c->clover) held = held || cs.A64 || cs.Ainv64 || cs.Ainv32;
+  if (held) return set_error(c, SQ_ERR_STATE, "sq_set_allocator: the context already holds device buffers");
+  c->mem.alloc = alloc;
+  c->mem.free = free_fn;
+  c->mem.user = user;
   return SQ_OK;
 }
 
@@ -207,11 +241,11 @@ sq_status sq_destroy(sq_ctx* c) {
   if (!c) return SQ_OK;
   cudaStreamSynchronize(c->stream);
   release_workspace(c);
-  for (auto& cs : c->clover) free_clover(cs);
-  cudaFree(c->U64);
-  cudaFree(c->U32);
+  for (auto& cs : c->clover) free_clover(c, cs);
+  dev_free(c->mem, c->U64, 2 * 4 * 9 * (size_t)c->Vh * sizeof(double2));
+  dev_free(c->mem, c->U32, gauge32_bytes(c, c->recon));
   cudaFree(c->d_err);
-  cudaFree(c->stoch_part);
+  dev_free(c->mem, c->stoch_part, c->stoch_cap);
   cudaEventDestroy(c->ev);
   cudaStreamDestroy(c->stream);
   delete c;
@@ -231,13 +265,12 @@ sq_status sq_load_gauge(sq_ctx* c, const double* U, int recon, int where) {
   c->have_gauge = 0;
   cudaError_t e = cudaSuccess;
   if (c->U32 && recon != c->recon) {
-    cudaFree(c->U32);
+    dev_free(c->mem, c->U32, gauge32_bytes(c, c->recon));
     c->U32 = nullptr;
   }
   c->recon = recon;
-  if (!c->U64) e = cudaMalloc((void**)&c->U64, 2 * 4 * 9 * Vh * sizeof(double2));
-  if (e == cudaSuccess && !c->U32)
-    e = cudaMalloc(&c->U32, recon == 12 ? 2 * 4 * 3 * Vh * sizeof(float4) : 2 * 4 * 9 * Vh * sizeof(float2));
+  if (!c->U64) e = dev_alloc(c->mem, (void**)&c->U64, 2 * 4 * 9 * Vh * sizeof(double2));
+  if (e == cudaSuccess && !c->U32) e = dev_alloc(c->mem, &c->U32, gauge32_bytes(c, recon));
   if (e != cudaSuccess) return cuda_check(c, e, "gauge allocation");
   const size_t nd = (size_t)c->V * 4 * 18;
   const double* dU = U;
@@ -564,10 +597,10 @@ static sq_status grow_contract_scratch(sq_ctx* c, size_t bytes) {
   if (c->stoch_cap >= bytes) return SQ_OK;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess) {
-    cudaFree(c->stoch_part);
+    dev_free(c->mem, c->stoch_part, c->stoch_cap);
     c->stoch_part = nullptr;
     c->stoch_cap = 0;
-    e = cudaMalloc(&c->stoch_part, bytes);
+    e = dev_alloc(c->mem, &c->stoch_part, bytes);
     if (e == cudaSuccess) c->stoch_cap = bytes;
   }
   return cuda_check(c, e, "contraction scratch");

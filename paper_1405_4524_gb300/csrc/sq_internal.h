@@ -32,7 +32,19 @@ struct Shape {
   int order = 0;  // 0: source blocks fastest in the flattened grid
 };
 
+// Device memory for persistent buffers: the caller's callbacks or
+// cudaMalloc / cudaFree. A buffer is freed through the allocator that made it.
+struct Allocator {
+  sq_alloc_fn alloc = nullptr;
+  sq_free_fn free = nullptr;
+  void* user = nullptr;
+  cudaStream_t stream = nullptr;  // the owning context's stream
+};
+cudaError_t dev_alloc(const Allocator& a, void** p, size_t bytes);
+void dev_free(const Allocator& a, void* p, size_t bytes);  // p may be NULL
+
 struct Workspace {
+  Allocator mem;  // allocator of base and hist
   size_t bytes = 0;
   void* base = nullptr;
   int n_rhs = 0;
@@ -139,6 +151,7 @@ struct sq_ctx {
   int prof_valid = 0;
   int prof_inner = 0;
   sq::KStat prof[sq::KC_N];        // per-class totals of the last profiled solve
+  sq::Allocator mem;               // persistent device buffers
   void* stoch_part = nullptr;      // K-group partials of the stochastic operators
   size_t stoch_cap = 0;            // bytes held by stoch_part
 };

@@ -403,8 +403,8 @@ static void free_ws(Workspace& w) {
     if (ev) cudaEventDestroy(ev);
   if (w.graph) cudaGraphExecDestroy(w.graph);
   for (auto e : w.pev) cudaEventDestroy(e);
-  if (w.hist) cudaFree(w.hist);
-  if (w.base) cudaFree(w.base);
+  dev_free(w.mem, w.hist, 2 * (size_t)w.hist_chunk * sizeof(int));
+  dev_free(w.mem, w.base, w.bytes);
   w = Workspace();
 }
 
@@ -451,12 +451,13 @@ static sq_status alloc_ws(sq_ctx* c, Workspace& w, int n, int inner) {
   size_t o_ts = tot; tot += al((size_t)n * sizeof(int));
   size_t o_fl = tot; tot += al(sizeof(int));
   void* base = nullptr;
-  cudaError_t e = cudaMalloc(&base, tot);
+  cudaError_t e = dev_alloc(c->mem, &base, tot);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return set_error(c, SQ_ERR_OOM, "workspace of %zu bytes for %d sources: %s", tot, n, cudaGetErrorString(e));
   }
   char* b = (char*)base;
+  w.mem = c->mem;
   w.base = base;
   w.bytes = tot;
   w.n_rhs = n;
@@ -1041,9 +1042,10 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       w.pev.push_back(ev);
     }
     if (w.hist_chunk < chunk) {
-      if (w.hist) cudaFree(w.hist);
+      dev_free(w.mem, w.hist, 2 * (size_t)w.hist_chunk * sizeof(int));
       w.hist = nullptr;
-      e = cudaMalloc((void**)&w.hist, 2 * chunk * sizeof(int));
+      w.hist_chunk = 0;
+      e = dev_alloc(w.mem, (void**)&w.hist, 2 * (size_t)chunk * sizeof(int));
       if (e != cudaSuccess) return cuda_check(c0, e, "profile buffers");
       w.hist_chunk = chunk;
     }

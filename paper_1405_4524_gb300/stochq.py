@@ -98,6 +98,7 @@ _SIG = {
     "sq_solve_batch": (_i, [C.POINTER(sq_problem), _i, C.POINTER(sq_solve_params),
                             C.POINTER(sq_solve_stats)]),
     "sq_contract_pion": (_i, [_vp, _vp, _i, _vp, _vp, _i]),
+    "sq_set_allocator": (_i, [_vp, _vp, _vp, _vp]),
     "sq_contract_stoch_op": (_i, [_vp, _vp, _vp, _i, _vp, _vp, _i]),
     "sq_contract_prop_trace": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp, _i]),
     "sq_contract_stoch_op_z4": (_i, [_vp, _vp, _vp, _i, _vp, _vp, _i]),
@@ -186,6 +187,40 @@ def sq_create(dims, t_bc: int = -1, stream=None):
 
 def sq_destroy(ctx) -> None:
     _check(None, _lib.sq_destroy(ctx))
+    _ALLOCATORS.pop(ctx, None)  # after the library has freed through them
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_ALLOCATORS = {}  # ctx -> the ctypes callbacks, alive as long as the context
+
+
+def sq_set_allocator(ctx, alloc=None, free=None) -> None:
+    """Persistent device buffers of the context from Python callables:
+    alloc(nbytes, stream) -> device address (int, 0 on failure),
+    free(address, nbytes, stream). Both None restores cudaMalloc / cudaFree.
+    Call before sq_load_gauge."""
+    if (alloc is None) != (free is None):
+        raise ValueError("give both alloc and free, or neither")
+    if alloc is None:
+        _check(ctx, _lib.sq_set_allocator(ctx, None, None, None))
+        _ALLOCATORS.pop(ctx, None)
+        return
+    a = _ALLOC_FN(lambda nbytes, stream, user: alloc(int(nbytes), stream) or None)
+    f = _FREE_FN(lambda ptr, nbytes, stream, user: free(ptr, int(nbytes), stream))
+    _check(ctx, _lib.sq_set_allocator(ctx, C.cast(a, _vp), C.cast(f, _vp), None))
+    _ALLOCATORS[ctx] = (a, f)
+
+
+def use_torch_allocator(ctx) -> None:
+    """Take the context's persistent buffers from PyTorch's CUDA caching
+    allocator (they then show in torch.cuda.memory_allocated)."""
+    import torch
+
+    dev = torch.cuda.current_device()
+    sq_set_allocator(ctx,
+                     lambda nbytes, stream: torch.cuda.caching_allocator_alloc(nbytes, dev, stream or 0),
+                     lambda ptr, nbytes, stream: torch.cuda.caching_allocator_delete(ptr))
 
 
 def sq_load_gauge(ctx, U, recon: int = 12) -> None:
