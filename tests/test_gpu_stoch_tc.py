@@ -139,3 +139,34 @@ def test_tensor_core_many_sources(sq):
         assert close(C, C64, 1e-12)
     finally:
         sq.sq_destroy(ctx)
+
+
+def test_tensor_core_timeslice_batches(sq):
+    """32^3 x 64 with 16 sources: the packed operands of all 64 timeslices
+    exceed the 8 GiB workspace, so the call runs in batches of 18 timeslices
+    (the last one 10). Inputs made on the device (seeded); every element
+    against the FP64-pipe route and sampled pairs against the oracle."""
+    import torch
+
+    dims, n = (32, 32, 32, 64), 16
+    X_, Y, Z, T = dims
+    g = torch.Generator(device="cuda")
+    g.manual_seed(6901)
+    k = torch.randint(0, 4, (n, T, Z, Y, X_, 4, 3), generator=g, device="cuda")
+    eta = torch.tensor([1, 1j, -1, -1j], dtype=torch.complex128, device="cuda")[k]
+    del k
+    X = torch.randn(eta.shape, dtype=torch.complex128, device="cuda", generator=g)
+    ctx = sq.sq_create(dims, -1)
+    try:
+        O, C = sq.sq_contract_stoch_op(ctx, eta, X, n, tensor_cores=True)
+        O64, C64 = sq.sq_contract_stoch_op(ctx, eta, X, n)
+        O, O64 = O.cpu().numpy(), O64.cpu().numpy()
+        assert close(O, O64, 1e-13)
+        assert close(C.cpu().numpy(), C64.cpu().numpy(), 1e-12)
+        for i, j in [(0, 15), (7, 7), (12, 3)]:
+            want = oracle.stochastic_operator(eta[[i]].cpu().numpy(), X[[j]].cpu().numpy())[:, 0, 0]
+            assert float(np.max(np.abs(O[:, i, j] - want))) <= BAR * float(np.max(np.abs(O)))
+    finally:
+        sq.sq_destroy(ctx)
+        del eta, X
+        torch.cuda.empty_cache()
