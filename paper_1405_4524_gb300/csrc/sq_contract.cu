@@ -157,85 +157,117 @@ __global__ void k_stoch_sum(const double2* part, int n, int T, int nkg, double2*
 }
 
 // C[dt] = 1/(n^2 T) sum_t0 S((t0 + dt) mod T, t0), S(ta, tb) = sum_ij
-// O_ij(ta) O_ji(tb). S is symmetric (swap i and j), so only ta >= tb is
-// formed: k_stoch_corr_pairs, grid (pair, group), walks 32 x 32 tiles of
-// O(ta) and the transposed tiles of O(tb) through shared memory (both read
-// along rows), one partial per (pair, group); k_stoch_corr_sum adds the
-// groups and then the timeslices in a fixed order.
-__global__ void __launch_bounds__(256) k_stoch_corr_pairs(const double2* O, int n, int T, int G, double2* part) {
-  const int p = blockIdx.x, g = blockIdx.y;
-  int ta = (int)((sqrt(8.0 * p + 1.0) - 1.0) * 0.5);
-  while (ta * (ta + 1) / 2 > p) ta--;
-  while ((ta + 1) * (ta + 2) / 2 <= p) ta++;
-  const int tb = p - ta * (ta + 1) / 2;
-  __shared__ double2 sa[32][33], sb[32][33];
+// O_ij(ta) O_ji(tb). S is symmetric (swap i and j), so only blocks of
+// 4 x 4 timeslices (ta block >= tb block) are formed. k_stoch_corr_blocks,
+// grid (block pair, group): the CTA walks 16 x 16 tiles (I, J) of the pair
+// index, stages O(ta)[I, J] for its four ta and O(tb)[J, I] for its four tb in
+// shared memory (both read along rows), and every thread forms the 16
+// products of its (i, j) for all (ta, tb) of the block pair, so each staged
+// value feeds four FMAs pairs. One partial per (block pair, group, ta, tb);
+// k_stoch_corr_sum adds the groups, then the timeslices, in a fixed order.
+constexpr int kCorrTB = 4;   // timeslices per block
+constexpr int kCorrTile = 16;
+
+__global__ void __launch_bounds__(256) k_stoch_corr_blocks(const double2* O, int n, int T, int G, double2* part) {
+  const int bp = blockIdx.x, g = blockIdx.y;
+  int ba = (int)((sqrt(8.0 * bp + 1.0) - 1.0) * 0.5);
+  while (ba * (ba + 1) / 2 > bp) ba--;
+  while ((ba + 1) * (ba + 2) / 2 <= bp) ba++;
+  const int bb = bp - ba * (ba + 1) / 2;
+  __shared__ double2 sa[kCorrTB][kCorrTile][kCorrTile + 1], sb[kCorrTB][kCorrTile][kCorrTile + 1];
   const long long nn = (long long)n * n;
-  const int nt = (n + 31) / 32;
-  double re = 0, im = 0;
+  const int nt = (n + kCorrTile - 1) / kCorrTile;
+  const int r = threadIdx.x / kCorrTile, c = threadIdx.x - r * kCorrTile;
+  double re[kCorrTB][kCorrTB], im[kCorrTB][kCorrTB];
+#pragma unroll
+  for (int q = 0; q < kCorrTB; q++)
+#pragma unroll
+    for (int p = 0; p < kCorrTB; p++) re[q][p] = im[q][p] = 0.0;
   for (int tile = g; tile < nt * nt; tile += G) {
     const int I = tile / nt, J = tile - (tile / nt) * nt;
     __syncthreads();
-    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
-      const int r = e >> 5, c = e & 31;
-      const int ia = I * 32 + r, ja = J * 32 + c;  // O(ta)[ia][ja]
-      const int jb = J * 32 + r, ib = I * 32 + c;  // O(tb)[jb][ib]
-      sa[r][c] = (ia < n && ja < n) ? O[ta * nn + (long long)ia * n + ja] : make_double2(0.0, 0.0);
-      sb[r][c] = (jb < n && ib < n) ? O[tb * nn + (long long)jb * n + ib] : make_double2(0.0, 0.0);
+#pragma unroll
+    for (int q = 0; q < kCorrTB; q++) {
+      const int ta = ba * kCorrTB + q, tb = bb * kCorrTB + q;
+      const int ia = I * kCorrTile + r, ja = J * kCorrTile + c;  // O(ta)[ia][ja]
+      const int jb = J * kCorrTile + r, ib = I * kCorrTile + c;  // O(tb)[jb][ib]
+      sa[q][r][c] = (ta < T && ia < n && ja < n) ? O[ta * nn + (long long)ia * n + ja] : make_double2(0.0, 0.0);
+      sb[q][r][c] = (tb < T && jb < n && ib < n) ? O[tb * nn + (long long)jb * n + ib] : make_double2(0.0, 0.0);
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
-      const int r = e >> 5, c = e & 31;  // i = I*32 + r, j = J*32 + c
-      const double2 a = sa[r][c], b = sb[c][r];
-      re = fma(a.x, b.x, re);
-      re = fma(-a.y, b.y, re);
-      im = fma(a.x, b.y, im);
-      im = fma(a.y, b.x, im);
+    double2 a[kCorrTB], b[kCorrTB];
+#pragma unroll
+    for (int q = 0; q < kCorrTB; q++) {
+      a[q] = sa[q][r][c];  // O(ta)[i][j], i = I*16 + r, j = J*16 + c
+      b[q] = sb[q][c][r];  // O(tb)[j][i]
     }
+#pragma unroll
+    for (int q = 0; q < kCorrTB; q++)
+#pragma unroll
+      for (int p = 0; p < kCorrTB; p++) {
+        re[q][p] = fma(a[q].x, b[p].x, re[q][p]);
+        re[q][p] = fma(-a[q].y, b[p].y, re[q][p]);
+        im[q][p] = fma(a[q].x, b[p].y, im[q][p]);
+        im[q][p] = fma(a[q].y, b[p].x, im[q][p]);
+      }
   }
-  __shared__ double sr[8], si[8];
-  re = warp_sum(re);
-  im = warp_sum(im);
-  if ((threadIdx.x & 31) == 0) {
-    sr[threadIdx.x >> 5] = re;
-    si[threadIdx.x >> 5] = im;
-  }
+  // fixed-order block reduction of the 16 complex sums
+  __shared__ double red[8][kCorrTB * kCorrTB][2];
+#pragma unroll
+  for (int q = 0; q < kCorrTB; q++)
+#pragma unroll
+    for (int p = 0; p < kCorrTB; p++) {
+      const double x = warp_sum(re[q][p]), y = warp_sum(im[q][p]);
+      if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5][q * kCorrTB + p][0] = x;
+        red[threadIdx.x >> 5][q * kCorrTB + p][1] = y;
+      }
+    }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0, b = 0;
+  if (threadIdx.x < kCorrTB * kCorrTB) {
+    double x = 0, y = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-      a += sr[w];
-      b += si[w];
+      x += red[w][threadIdx.x][0];
+      y += red[w][threadIdx.x][1];
     }
-    part[(long long)p * G + g] = make_double2(a, b);
+    part[((long long)bp * G + g) * (kCorrTB * kCorrTB) + threadIdx.x] = make_double2(x, y);
   }
 }
 
+// one warp per dt: lane l adds the terms l, l + 32, ... of the (t0, group)
+// sequence in order, then a fixed butterfly (deterministic)
 __global__ void k_stoch_corr_sum(const double2* part, int n, int T, int G, double2* C) {
-  const int dt = blockIdx.x * blockDim.x + threadIdx.x;
-  if (dt >= T) return;
+  const int dt = blockIdx.x, lane = threadIdx.x;
   double a = 0, b = 0;
-  for (int t0 = 0; t0 < T; t0++) {
+  for (int e = lane; e < T * G; e += 32) {
+    const int t0 = e / G, g = e - t0 * G;
     const int t1 = (t0 + dt) % T;
     const int ta = max(t0, t1), tb = min(t0, t1);
-    const long long p = (long long)ta * (ta + 1) / 2 + tb;
-    double pa = 0, pb = 0;
-    for (int g = 0; g < G; g++) {
-      pa += part[p * G + g].x;
-      pb += part[p * G + g].y;
-    }
-    a += pa;
-    b += pb;
+    const int ba = ta / kCorrTB, bb = tb / kCorrTB;
+    const long long bp = (long long)ba * (ba + 1) / 2 + bb;
+    const double2 v = part[(bp * G + g) * (kCorrTB * kCorrTB) + (ta % kCorrTB) * kCorrTB + (tb % kCorrTB)];
+    a += v.x;
+    b += v.y;
   }
-  const double f = 1.0 / ((double)n * n * T);
-  C[dt] = make_double2(a * f, b * f);
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if (lane == 0) {
+    const double f = 1.0 / ((double)n * n * T);
+    C[dt] = make_double2(a * f, b * f);
+  }
 }
 
-// groups per timeslice pair of the correlator: about 4 CTAs per SM in all
+static long long corr_block_pairs(const sq_ctx* c) {
+  const long long nb = (c->dims[3] + kCorrTB - 1) / kCorrTB;
+  return nb * (nb + 1) / 2;
+}
+
+// groups per block pair of the correlator: about 4 CTAs per SM in all
 int corr_groups(const sq_ctx* c, int n) {
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-  const long long T = c->dims[3], pairs = T * (T + 1) / 2;
-  const long long nt = (n + 31) / 32;
+  const long long pairs = corr_block_pairs(c);
+  const long long nt = (n + kCorrTile - 1) / kCorrTile;
   long long g = (4LL * sms + pairs - 1) / pairs;
   if (g > nt * nt) g = nt * nt;
   if (g < 1) g = 1;
@@ -243,8 +275,7 @@ int corr_groups(const sq_ctx* c, int n) {
 }
 
 size_t corr_scratch_bytes(const sq_ctx* c, int n) {
-  const long long T = c->dims[3];
-  return (size_t)(T * (T + 1) / 2) * corr_groups(c, n) * 2 * sizeof(double);
+  return (size_t)corr_block_pairs(c) * corr_groups(c, n) * kCorrTB * kCorrTB * 2 * sizeof(double);
 }
 
 // C[t0][t] = 1/n^2 sum_ij P_ji(t) Q_ij(t0) = tr[P(t) Q(t0)] / n^2; one CTA per
@@ -316,8 +347,9 @@ void launch_stoch_op(const sq_ctx* c, const double* eta, const double* X, int n,
 
 void launch_stoch_corr(const sq_ctx* c, const double* O, int n, double* C, double* part, cudaStream_t s) {
   const int T = c->dims[3], G = corr_groups(c, n);
-  k_stoch_corr_pairs<<<dim3(T * (T + 1) / 2, G), 256, 0, s>>>((const double2*)O, n, T, G, (double2*)part);
-  k_stoch_corr_sum<<<(T + 127) / 128, 128, 0, s>>>((const double2*)part, n, T, G, (double2*)C);
+  k_stoch_corr_blocks<<<dim3((unsigned)corr_block_pairs(c), G), 256, 0, s>>>((const double2*)O, n, T, G,
+                                                                              (double2*)part);
+  k_stoch_corr_sum<<<T, 32, 0, s>>>((const double2*)part, n, T, G, (double2*)C);
 }
 
 void launch_prop_trace(const sq_ctx* c, const double* etaA, const double* XA, const double* etaB, const double* XB,

@@ -203,29 +203,33 @@ __device__ __forceinline__ uint32_t ternary_half(double v, bool& ok) {
 }
 
 // A tiles of timeslices t0 .. t0 + Tb - 1: grid (nkt, n_itiles, Tb), 256 threads.
-// Sets bit 1 of *flag if a component is not 0 or +-1.
+// The tile is assembled in shared memory from row-contiguous reads (eight
+// threads per source row, 512 bytes) and written out as one contiguous
+// 16 KB block. Sets bit 1 of *flag if a component is not 0 or +-1.
 __global__ void __launch_bounds__(256) k_tc_pack_eta(const double2* eta, int n, int T, int t0, long long K,
                                                      int nkt, int nit, uint4* A, int* flag) {
+  __shared__ __align__(16) unsigned char tile[kTcABytes];
   const int kt = blockIdx.x, it = blockIdx.y, tb = blockIdx.z;
-  char* blk = reinterpret_cast<char*>(A) + (((long long)tb * nit + it) * nkt + kt) * kTcABytes;
+  bool ok = true;
   for (int v = threadIdx.x; v < kTcM * 8; v += blockDim.x) {
-    // row fastest: eight threads fill one 128-byte core matrix
-    const int r = v & (kTcM - 1), q = v >> 7;  // row, group of 8 columns = 4 complex rows
+    const int q = v & 7, r = v >> 3;  // group of 8 columns (4 complex rows) fastest
     const int i = it * kTcM + r;
     uint32_t h[4] = {0, 0, 0, 0};
     if (i < n) {
       const double2* src = eta + ((long long)i * T + t0 + tb) * K + (long long)kt * (kTcK / 2) + q * 4;
-      bool ok = true;
 #pragma unroll
       for (int c = 0; c < 4; c++) {
         const double2 d = src[c];
         const uint32_t lo = ternary_half(d.x, ok), hi = ternary_half(d.y, ok);
         h[c] = lo | (hi << 16);
       }
-      if (!ok) atomicOr(flag, 1);
     }
-    *reinterpret_cast<uint4*>(blk + tile_offset(kTcM, r, q * 8)) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4*>(tile + tile_offset(kTcM, r, q * 8)) = make_uint4(h[0], h[1], h[2], h[3]);
   }
+  if (!ok) atomicOr(flag, 1);
+  __syncthreads();
+  uint4* blk = A + (((long long)tb * nit + it) * nkt + kt) * (kTcABytes / 16);
+  for (int v = threadIdx.x; v < kTcABytes / 16; v += blockDim.x) blk[v] = reinterpret_cast<const uint4*>(tile)[v];
 }
 
 // trunc(x 2^(55-e)) for |x| < 2^e, from the bits of x (integer pipe only)
@@ -488,7 +492,9 @@ TcPlan tc_plan(const sq_ctx* c, int n, size_t cap_bytes) {
   long long tb = (long long)(cap_bytes / per_t);
   if (tb < 1) tb = 1;
   if (tb > p.T) tb = p.T;
-  p.Tb = (int)tb;
+  // equal batches (no short tail batch that leaves most SMs idle)
+  const long long nbatch = (p.T + tb - 1) / tb;
+  p.Tb = (int)((p.T + nbatch - 1) / nbatch);
   p.bytes = per_t * p.Tb + 256;
   return p;
 }

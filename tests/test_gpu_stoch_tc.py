@@ -143,8 +143,8 @@ def test_tensor_core_many_sources(sq):
 
 def test_tensor_core_timeslice_batches(sq):
     """32^3 x 64 with 16 sources: the packed operands of all 64 timeslices
-    exceed the 8 GiB workspace, so the call runs in batches of 18 timeslices
-    (the last one 10). Inputs made on the device (seeded); every element
+    exceed the 8 GiB workspace, so the call runs in four batches of 16
+    timeslices. Inputs made on the device (seeded); every element
     against the FP64-pipe route and sampled pairs against the oracle."""
     import torch
 
