@@ -92,31 +92,6 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                "l"(src), "r"(bytes), "r"(mbar)
                : "memory");
 }
-// the same bytes into the shared memory of every CTA of the cluster in
-// `mask`, at the same offset, completing on each one's barrier at `mbar`
-__device__ __forceinline__ void bulk_load_multicast(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar,
-                                                    uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
-      "%4;" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(mbar), "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ void tc_commit_multicast(uint32_t mbar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(mbar),
-      "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
@@ -325,21 +300,12 @@ __global__ void __launch_bounds__(256) k_tc_pack_x(const double2* X, int n, int 
 }
 
 // ---- the product -----------------------------------------------------------
-// CL > 1: clusters of CL CTAs along the j tiles share the A tile: CTA r of
-// the cluster loads slice r of it and multicasts the slice to all, and every
-// CTA's ring stage is reused only when the products of all CL CTAs have read
-// it (each CTA's commit arrives on every CTA's empty barrier). The CTAs of a
-// cluster leave together (cluster barrier), so none exits while a peer can
-// still write into its shared memory.
-template <int CL>
 __global__ void __launch_bounds__(kTcThreads, 2)
     k_stoch_tc(const uint4* A, const uint4* B, const int* exps, int n, int t0, int nkt, int nit, int njt, int nch,
                double2* O, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int jt = blockIdx.x, it = blockIdx.y, tb = blockIdx.z;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t rank = CL > 1 ? cluster_rank() : 0;
-  constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kTcBarOffset);
   // bars: full[stages], empty[stages], accf, acce, done
   const uint32_t full0 = smem_addr(bars), empty0 = full0 + 8 * kTcStages;
@@ -350,7 +316,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kTcStages; s++) {
       mbar_init(full0 + 8 * s, 1);
-      mbar_init(empty0 + 8 * s, CL);
+      mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(accf, 1);
     mbar_init(acce, 128);
@@ -370,7 +336,6 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (CL > 1) cluster_sync();  // every peer's barriers exist before the first multicast
   const uint32_t tmem = *tslot;
 
   const char* Ablk = reinterpret_cast<const char*>(A) + ((long long)tb * nit + it) * nkt * (long long)kTcABytes;
@@ -389,13 +354,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       if (kt >= kTcStages && !tc_wait(empty0 + 8 * s, ((kt / kTcStages) - 1) & 1, abort, err, true)) break;
       if (lane == 0) {
         mbar_expect_tx(full0 + 8 * s, kTcStageBytes);
-        if (CL > 1) {
-          constexpr uint32_t slice = kTcABytes / CL;
-          bulk_load_multicast(ring + s * kTcStageBytes + rank * slice,
-                              Ablk + (long long)kt * kTcABytes + rank * slice, slice, full0 + 8 * s, kMask);
-        } else {
-          bulk_load(ring + s * kTcStageBytes, Ablk + (long long)kt * kTcABytes, kTcABytes, full0 + 8 * s);
-        }
+        bulk_load(ring + s * kTcStageBytes, Ablk + (long long)kt * kTcABytes, kTcABytes, full0 + 8 * s);
         bulk_load(ring + s * kTcStageBytes + kTcABytes, Bblk + (long long)kt * kTcBBytes, kTcBBytes, full0 + 8 * s);
       }
       __syncwarp();
@@ -420,8 +379,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
           const uint64_t bd = smem_desc(b0 + ks * 2 * (kTcN * 16), kTcN * 16, 128);
           tc_mma(tmem, ad, bd, kTcIdesc, (first && ks == 0) ? 0u : 1u);
         }
-        if (CL > 1) tc_commit_multicast(empty0 + 8 * s, kMask);
-        else tc_commit(empty0 + 8 * s);
+        tc_commit(empty0 + 8 * s);
         if ((kt % kTcChunkTiles) == kTcChunkTiles - 1 || kt == nkt - 1) tc_commit(accf);
       }
       __syncwarp();
@@ -468,7 +426,6 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   }
   tc_fence_before();
   __syncthreads();
-  if (CL > 1) cluster_sync();  // no peer writes into this CTA any more
   if (warp == 0 && !skip) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
@@ -505,16 +462,10 @@ cudaError_t launch_stoch_tc(const sq_ctx* c, const TcPlan& p, const double* eta,
                             void* ws, int* err, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_stoch_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_stoch_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_stoch_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(k_stoch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  // clusters of 4 (or 2) j tiles share the A tile when the j tiles divide
-  const int cl = (p.njt % 4 == 0) ? 4 : (p.njt % 2 == 0 ? 2 : 1);
   char* base = static_cast<char*>(ws);
   uint4* A = reinterpret_cast<uint4*>(base);
   uint4* B = reinterpret_cast<uint4*>(base + p.a_per_t * p.Tb);
@@ -526,25 +477,9 @@ cudaError_t launch_stoch_tc(const sq_ctx* c, const TcPlan& p, const double* eta,
                                                           flag);
     k_tc_pack_x<<<dim3(p.nch, p.njt, tb), 256, 0, s>>>((const double2*)X, n, p.T, t0, p.K, p.nkt, p.njt,
                                                                p.nch, B, exps, flag);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(p.njt, p.nit, tb);
-    cfg.blockDim = dim3(kTcThreads);
-    cfg.dynamicSmemBytes = kTcSmemBytes;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = cl;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaError_t e;
-    if (cl == 4)
-      e = cudaLaunchKernelEx(&cfg, k_stoch_tc<4>, A, B, exps, n, t0, p.nkt, p.nit, p.njt, p.nch, (double2*)O, err);
-    else if (cl == 2)
-      e = cudaLaunchKernelEx(&cfg, k_stoch_tc<2>, A, B, exps, n, t0, p.nkt, p.nit, p.njt, p.nch, (double2*)O, err);
-    else
-      e = cudaLaunchKernelEx(&cfg, k_stoch_tc<1>, A, B, exps, n, t0, p.nkt, p.nit, p.njt, p.nch, (double2*)O, err);
+    k_stoch_tc<<<dim3(p.njt, p.nit, tb), kTcThreads, kTcSmemBytes, s>>>(A, B, exps, n, t0, p.nkt, p.nit, p.njt,
+                                                                         p.nch, (double2*)O, err);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
