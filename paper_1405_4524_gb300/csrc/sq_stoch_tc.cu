@@ -31,16 +31,16 @@
 // bulk copy moves a tile and the matrix descriptors use a leading (column
 // group) stride of R*16 bytes and a stride (row group) of 128 bytes.
 //
-// Kernel. One CTA per (16-source j tile, 128-source i tile, timeslice):
-// warp 4 streams the tiles through a 4-stage shared-memory ring with
-// cp.async.bulk, warp 5 issues tcgen05.mma (4 per tile, K = 16 each) into a
-// tensor-memory accumulator (one chunk of 128 tiles at a time), warps 0-3
-// read the accumulator with tcgen05.ld (warp w owns lanes 32w..32w+31)
-// and add the digits into FP64 registers. Two CTAs share an SM (3-stage ring, 256 tensor-memory columns
-// each), so one CTA's epilogue overlaps the other's products. Every wait is
-// bounded; on a timeout the CTA
-// records ERRBIT_TIMEOUT, lets its copies and products drain, frees its
-// tensor memory and returns.
+// Kernel. One CTA per (16-source j tile, 128-source i tile, timeslice), two
+// CTAs per SM: warp 4 streams the tiles through a 3-stage shared-memory ring
+// with cp.async.bulk, warp 5 issues tcgen05.mma (4 per tile, K = 16 each)
+// into a tensor-memory accumulator of 160 columns (one chunk of 128 tiles at
+// a time), warps 0-3 read the accumulator with tcgen05.ld (warp w owns lanes
+// 32w..32w+31) and add the digits into FP64 registers; while one CTA runs
+// that epilogue the other CTA on the SM keeps the tensor pipe busy. Every
+// wait is bounded; on a timeout the CTA records ERRBIT_TIMEOUT, lets its
+// copies and products drain, frees its tensor memory and returns, and the
+// CTAs that start later see the error word and do no work.
 
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -460,12 +460,10 @@ TcPlan tc_plan(const sq_ctx* c, int n, size_t cap_bytes) {
 // flag word (bits 1: eta not 0/+-1, 2: X not finite) is at the end.
 cudaError_t launch_stoch_tc(const sq_ctx* c, const TcPlan& p, const double* eta, const double* X, int n, double* O,
                             void* ws, int* err, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_stoch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // per call: the attribute belongs to the current device, and contexts of
+  // one process may sit on different devices
+  cudaError_t e0 = cudaFuncSetAttribute(k_stoch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
+  if (e0 != cudaSuccess) return e0;
   char* base = static_cast<char*>(ws);
   uint4* A = reinterpret_cast<uint4*>(base);
   uint4* B = reinterpret_cast<uint4*>(base + p.a_per_t * p.Tb);
