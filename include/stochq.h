@@ -244,8 +244,10 @@ sq_status sq_norm2_eo(sq_ctx *ctx, const void *eo_field, sq_prec prec, int n_rhs
  * fixed static device array of 259 KiB that every GPU which loads the
  * library keeps until the process exits; n_rhs is limited to 256 sources
  * (larger n_rhs: SQ_ERR_ARG). The first call on a device looks up the
- * array's device address for that device (one-time set-up); make that
- * first call before any stream capture starts. Every call shares the
+ * array's device address for that device and loads this entry point's
+ * kernels of all three precisions (one-time set-up, whatever prec that
+ * first call has); make that first call before any stream capture
+ * starts. Every call shares the
  * array, which keeps the last call's contents: calls that overlap on one
  * GPU (other streams, other contexts, other threads) race and must be
  * serialised by the caller. Inputs and outputs as sq_norm2_eo.
@@ -418,6 +420,36 @@ sq_status sq_get_profile(const sq_ctx *ctx, sq_kernel_stat *out, int max, int *n
 /* Number of kernels this context has launched so far (kernel nodes of
  * replayed CUDA graphs included). */
 sq_status sq_kernel_launches(const sq_ctx *ctx, long long *n);
+
+/* Launch shape of the even-odd dslash for fields of precision prec with
+ * n_rhs sources on this context's lattice: the autotuner's choice (made by
+ * the first sq_dslash_eo or sq_solve that needs it, timing the candidates on
+ * that call's own fields) or one set here, e.g. a shape saved from an
+ * earlier run, which then replaces tuning for later calls.
+ *   kind 0: per-site kernel; shape = {sites per CTA (multiple of 32),
+ *           sources per CTA, grid order 0/1, 0, 0}
+ *   kind 1: halo-tiled kernel (SQ_F32 / SQ_F16 with reconstruct-12 links;
+ *           section "dslash" of the hopping term above): every CTA owns all
+ *           X/2 checkerboard sites of shape[0] x shape[1] x shape[2] rows in
+ *           (y, z, t) (each dividing Y, Z, T; 32..256 sites, a multiple of
+ *           32; SQ_F16 needs X a multiple of 8) for shape[3] source slots,
+ *           staging every source's input spinors plus halo rows in a shared-
+ *           memory ring of depth shape[4] (2 or 3)
+ * Errors: SQ_ERR_ARG (unknown kind, a shape the lattice or the shared
+ * memory does not admit, n_rhs <= 0), SQ_ERR_STATE (get: no shape chosen
+ * for this (prec, n_rhs) yet). */
+sq_status sq_set_dslash_shape(sq_ctx *ctx, sq_prec prec, int n_rhs, int kind, const int shape[5]);
+sq_status sq_get_dslash_shape(const sq_ctx *ctx, sq_prec prec, int n_rhs, int *kind, int shape[5]);
+
+/* Limit, in SM clock cycles, of every bounded device-side wait in this
+ * context's kernels (the bulk-copy rings of the halo-tiled dslash and of the
+ * tensor-core stochastic operators); 0 restores the default of 4e9 cycles
+ * (about 2 s). A wait that runs out records a timeout, lets the copies it
+ * issued drain and returns, and the call reports SQ_ERR_TIMEOUT (sq_solve,
+ * sq_dslash_eo with SQ_DS_SYNC, sq_contract_stoch_op_z4); the context stays
+ * usable. A limit of a few cycles makes the first wait run out, which tests
+ * that path. Errors: SQ_ERR_ARG (negative). */
+sq_status sq_set_wait_cycles(sq_ctx *ctx, long long cycles);
 
 const char *sq_status_string(sq_status s);
 const char *sq_last_error(const sq_ctx *ctx);

@@ -426,7 +426,74 @@ sq_status sq_dslash_eo(sq_ctx* c, void* out, const void* in, const void* x, int 
   if (e == cudaSuccess && (flags & SQ_DS_SYNC)) e = cudaStreamSynchronize(c->stream);
   s = cuda_check(c, e, "sq_dslash_eo");
   if (s != SQ_OK) return s;
+  if (flags & SQ_DS_SYNC) {
+    int bits = 0;
+    s = read_error_word(c, &bits);
+    if (s != SQ_OK) return s;
+    if (bits & ERRBIT_TIMEOUT) {
+      leave_stream(c);
+      return set_error(c, SQ_ERR_TIMEOUT, "sq_dslash_eo: a bounded wait on the staged spinors ran out");
+    }
+  }
   return leave_stream(c);
+}
+
+static long long shape_key(const sq_ctx* c, int prec, int n) {
+  const int recon = prec == SQ_F64 ? 18 : c->recon;
+  return ((long long)prec << 56) ^ ((long long)recon << 48) ^ ((long long)c->Vh << 12) ^ n;
+}
+
+sq_status sq_set_dslash_shape(sq_ctx* c, sq_prec prec, int n, int kind, const int shape[5]) {
+  if (!c) return SQ_ERR_ARG;
+  if (!shape || n <= 0 || prec < SQ_F64 || prec > SQ_F16 || (kind != 0 && kind != 1))
+    return set_error(c, SQ_ERR_ARG, "sq_set_dslash_shape: bad argument");
+  Shape sh;
+  sh.kind = kind;
+  if (kind == 0) {
+    if (shape[0] <= 0 || shape[0] % 32 || shape[1] <= 0 || shape[0] * shape[1] > 256 ||
+        (shape[2] != 0 && shape[2] != 1))
+      return set_error(c, SQ_ERR_ARG, "sq_set_dslash_shape: bad per-site CTA shape");
+    sh.sx = shape[0];
+    sh.ry = shape[1];
+    sh.order = shape[2];
+  } else {
+    sh.by = shape[0];
+    sh.bz = shape[1];
+    sh.bt = shape[2];
+    sh.sg = shape[3];
+    sh.nbuf = shape[4];
+    const int recon = prec == SQ_F64 ? 18 : c->recon;
+    if (!tile_shape_ok(c, prec, recon, sh))
+      return set_error(c, SQ_ERR_ARG, "sq_set_dslash_shape: the tiled shape does not apply to this lattice");
+  }
+  c->tuned[shape_key(c, prec, n)] = sh;
+  return SQ_OK;
+}
+
+sq_status sq_get_dslash_shape(const sq_ctx* c, sq_prec prec, int n, int* kind, int shape[5]) {
+  if (!c) return SQ_ERR_ARG;
+  if (!kind || !shape || n <= 0 || prec < SQ_F64 || prec > SQ_F16)
+    return set_error(const_cast<sq_ctx*>(c), SQ_ERR_ARG, "sq_get_dslash_shape: bad argument");
+  auto it = c->tuned.find(shape_key(c, prec, n));
+  if (it == c->tuned.end())
+    return set_error(const_cast<sq_ctx*>(c), SQ_ERR_STATE, "sq_get_dslash_shape: no shape chosen yet");
+  const Shape& sh = it->second;
+  *kind = sh.kind;
+  if (sh.kind == 0) {
+    const int v[5] = {sh.sx, sh.ry, sh.order, 0, 0};
+    for (int i = 0; i < 5; i++) shape[i] = v[i];
+  } else {
+    const int v[5] = {sh.by, sh.bz, sh.bt, sh.sg, sh.nbuf};
+    for (int i = 0; i < 5; i++) shape[i] = v[i];
+  }
+  return SQ_OK;
+}
+
+sq_status sq_set_wait_cycles(sq_ctx* c, long long cycles) {
+  if (!c) return SQ_ERR_ARG;
+  if (cycles < 0) return set_error(c, SQ_ERR_ARG, "sq_set_wait_cycles: negative limit");
+  c->wait_cycles = cycles;
+  return SQ_OK;
 }
 
 sq_status sq_norm2_eo(sq_ctx* c, const void* field, sq_prec prec, int n, double* out, int where) {

@@ -13,8 +13,11 @@
 // times ry sources (threadIdx.y). The ry sources of a CTA read the same
 // links and clover blocks, so those come from HBM once per CTA and from L1
 // for the other sources.
+#include <algorithm>
 #include <cstdio>
+#include <vector>
 
+#include "sq_hop.cuh"
 #include "sq_internal.h"
 
 namespace sq {
@@ -43,86 +46,6 @@ struct KArgs {
 #ifndef SQ_DSLASH_LP_REGS
 #define SQ_DSLASH_LP_REGS 128
 #endif
-
-// h = psi_up + SIGN * B_mu psi_dn   (SIGN = -1: forward hop, +1: backward)
-template <int MU, int SIGN, typename R>
-__device__ __forceinline__ void project(const cx<R> v[12], cx<R> h[6]) {
-  const R sg = (R)SIGN;
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    cx<R> d0, d1;
-    if (MU == 0) {  // B = [[0, i], [i, 0]]
-      d0 = itimes(v[9 + c]);
-      d1 = itimes(v[6 + c]);
-    } else if (MU == 1) {  // B = [[0, -1], [1, 0]]
-      d0 = mk(-v[9 + c].re, -v[9 + c].im);
-      d1 = v[6 + c];
-    } else if (MU == 2) {  // B = [[i, 0], [0, -i]]
-      d0 = itimes(v[6 + c]);
-      d1 = mk(v[9 + c].im, -v[9 + c].re);
-    } else {  // B = 1
-      d0 = v[6 + c];
-      d1 = v[9 + c];
-    }
-    h[c] = mk(v[c].re + sg * d0.re, v[c].im + sg * d0.im);
-    h[3 + c] = mk(v[3 + c].re + sg * d1.re, v[3 + c].im + sg * d1.im);
-  }
-}
-
-// acc_up += w ; acc_dn += SIGN * B_mu^+ w
-template <int MU, int SIGN, typename R>
-__device__ __forceinline__ void accum(cx<R> acc[12], const cx<R> w[6]) {
-  const R sg = (R)SIGN;
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    acc[c] = acc[c] + w[c];
-    acc[3 + c] = acc[3 + c] + w[3 + c];
-    cx<R> e0, e1;
-    if (MU == 0) {  // B^+ = [[0, -i], [-i, 0]]
-      e0 = mk(w[3 + c].im, -w[3 + c].re);
-      e1 = mk(w[c].im, -w[c].re);
-    } else if (MU == 1) {  // B^+ = [[0, 1], [-1, 0]]
-      e0 = w[3 + c];
-      e1 = mk(-w[c].re, -w[c].im);
-    } else if (MU == 2) {  // B^+ = [[-i, 0], [0, i]]
-      e0 = mk(w[c].im, -w[c].re);
-      e1 = itimes(w[3 + c]);
-    } else {
-      e0 = w[c];
-      e1 = w[3 + c];
-    }
-    acc[6 + c] = mk(acc[6 + c].re + sg * e0.re, acc[6 + c].im + sg * e0.im);
-    acc[9 + c] = mk(acc[9 + c].re + sg * e1.re, acc[9 + c].im + sg * e1.im);
-  }
-}
-
-// w[s] = U h[s]
-template <typename R>
-__device__ __forceinline__ void mv(const Link<R>& u, const cx<R> h[6], cx<R> w[6]) {
-#pragma unroll
-  for (int s = 0; s < 2; s++)
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-      cx<R> r = u.e[3 * a] * h[3 * s];
-      r = cfma(u.e[3 * a + 1], h[3 * s + 1], r);
-      r = cfma(u.e[3 * a + 2], h[3 * s + 2], r);
-      w[3 * s + a] = r;
-    }
-}
-
-// w[s] = U^+ h[s]
-template <typename R>
-__device__ __forceinline__ void mv_dag(const Link<R>& u, const cx<R> h[6], cx<R> w[6]) {
-#pragma unroll
-  for (int s = 0; s < 2; s++)
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-      cx<R> r = cmul(u.e[a], h[3 * s]);
-      r = cjfma(u.e[3 + a], h[3 * s + 1], r);
-      r = cjfma(u.e[6 + a], h[3 * s + 2], r);
-      w[3 * s + a] = r;
-    }
-}
 
 // precision of the links and clover blocks read by a dslash on fields of
 // precision P: FP16 fields use the FP32 gauge data (per site, shared by the
@@ -341,7 +264,10 @@ void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s) {
   a.order = d.shape.order;
   dim3 grid((unsigned)a.nsb * (unsigned)a.nrb);
   bool ok = false;
-  if (d.prec == P64) {
+  int nparts = a.nsb * (int)(block.x >> 5);
+  if (d.shape.kind == 1 && launch_dslash_tile(c, d, s, &nparts)) {
+    ok = true;
+  } else if (d.prec == P64) {
     if (d.fin == FIN_TRUE && d.clover && d.xpay) {
       go<P64, 18, 1, 1, FIN_TRUE>(a, grid, block, s);
       ok = true;
@@ -356,7 +282,6 @@ void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s) {
   }
   if (!ok) fprintf(stderr, "libstochq: internal error: no dslash variant for this call\n");
   if (d.fin != FIN_NONE) {  // per-source sums and scalars
-    const int nparts = a.nsb * (int)(block.x >> 5);
     if (d.prec == P64) {
       if (d.fin == FIN_ALPHA) k_finish<double, 2, FIN_ALPHA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
       else if (d.fin == FIN_OMEGA) k_finish<double, 3, FIN_OMEGA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
@@ -374,14 +299,64 @@ bool dslash_tuned(const sq_ctx* c, int prec, int recon, int n) {
   return c->tuned.find(key) != c->tuned.end();
 }
 
-// Pick (sites, sources) per CTA by timing the candidates on the call's own
-// fields (no reduction). Results are cached per (precision, recon, Vh, n).
+// Halo-tiled shapes for the tuner: the tiles (all of x, by x bz x bt rows
+// dividing the lattice, 128 to 256 sites) with the fewest staged rows per
+// site, each with a few source-group sizes and ring depths.
+static void tile_candidates(const sq_ctx* c, int prec, int recon, int n, std::vector<Shape>& out) {
+  if ((prec != P32 && prec != P16) || recon != 12) return;
+  const int X2 = c->dims[0] / 2, Y = c->dims[1], Z = c->dims[2], T = c->dims[3];
+  struct Cand {
+    double halo;
+    int by, bz, bt;
+  };
+  std::vector<Cand> tiles;
+  for (int by = 1; by <= Y; by++)
+    for (int bz = 1; bz <= Z; bz++)
+      for (int bt = 1; bt <= T; bt++) {
+        if (Y % by || Z % bz || T % bt) continue;
+        const int th = X2 * by * bz * bt;
+        if (th < 128 || th > 256 || th % 32) continue;
+        const int hy = by < Y, hz = bz < Z, ht = bt < T;
+        const int rows = bt * bz * (by + 2 * hy) + (hz ? 2 * bt * by : 0) + (ht ? 2 * bz * by : 0);
+        tiles.push_back({(double)rows / (by * bz * bt), by, bz, bt});
+      }
+  std::sort(tiles.begin(), tiles.end(), [](const Cand& a, const Cand& b) { return a.halo < b.halo; });
+  if (tiles.size() > 4) tiles.resize(4);
+  const int groups[] = {2, 4, 8, 16};
+  for (const Cand& t : tiles)
+    for (int sg : groups) {
+      if (sg > n && sg != 2) continue;
+      for (int nbuf = 2; nbuf <= 3; nbuf++) {
+        Shape sh;
+        sh.kind = 1;
+        sh.by = t.by;
+        sh.bz = t.bz;
+        sh.bt = t.bt;
+        sh.sg = sg;
+        sh.nbuf = nbuf;
+        if (tile_shape_ok(c, prec, recon, sh)) out.push_back(sh);
+      }
+    }
+}
+
+// Pick the launch shape by timing the candidates on the call's own fields
+// (no reduction). Results are cached per (precision, recon, Vh, n).
 Shape tune_dslash(sq_ctx* c, DslashCall d, cudaStream_t s) {
   long long key = ((long long)d.prec << 56) ^ ((long long)d.recon << 48) ^ ((long long)c->Vh << 12) ^ d.n;
   auto it = c->tuned.find(key);
   if (it != c->tuned.end()) return it->second;
   static const int cand[][3] = {{32, 1, 0}, {32, 2, 0}, {32, 4, 0}, {32, 8, 0}, {64, 1, 0}, {64, 2, 0},
                                 {64, 4, 0}, {128, 1, 0}, {128, 2, 0}, {256, 1, 0}, {64, 2, 1}, {32, 4, 1}};
+  std::vector<Shape> shapes;
+  for (auto& cd : cand) {
+    if (cd[1] > 1 && cd[1] > d.n) continue;
+    Shape sh;
+    sh.sx = cd[0];
+    sh.ry = cd[1];
+    sh.order = cd[2];
+    shapes.push_back(sh);
+  }
+  tile_candidates(c, d.prec, d.recon, d.n, shapes);
   d.fin = FIN_NONE;
   d.list = nullptr;
   d.count = nullptr;
@@ -390,11 +365,8 @@ Shape tune_dslash(sq_ctx* c, DslashCall d, cudaStream_t s) {
   cudaEventCreate(&e1);
   Shape best;
   float best_ms = 1e30f;
-  for (auto& cd : cand) {
-    if (cd[1] > 1 && cd[1] > d.n) continue;
-    d.shape.sx = cd[0];
-    d.shape.ry = cd[1];
-    d.shape.order = cd[2];
+  for (const Shape& sh : shapes) {
+    d.shape = sh;
     for (int w = 0; w < 2; w++) launch_dslash(c, d, s);
     cudaEventRecord(e0, s);
     for (int r = 0; r < 5; r++) launch_dslash(c, d, s);

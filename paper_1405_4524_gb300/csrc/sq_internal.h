@@ -26,10 +26,15 @@ struct CloverSet {
   unsigned long long tick = 0;
 };
 
-// Dslash launch shape: sites per CTA (x) and sources per CTA (y).
+// Dslash launch shape. kind 0: the per-site kernel, sites per CTA (x) and
+// sources per CTA (y). kind 1: the halo-tiled kernel (FP32 / FP16,
+// reconstruct-12), tile rows by x bz x bt (x complete), sg source slots per
+// CTA, an nbuf-deep ring of staged source buffers.
 struct Shape {
   int sx = 64, ry = 2;
   int order = 0;  // 0: source blocks fastest in the flattened grid
+  int kind = 0;
+  int by = 0, bz = 0, bt = 0, sg = 0, nbuf = 2;
 };
 
 // Device memory for persistent buffers: the caller's callbacks or
@@ -154,6 +159,7 @@ struct sq_ctx {
   sq::Allocator mem;               // persistent device buffers
   void* stoch_part = nullptr;      // K-group partials of the stochastic operators
   size_t stoch_cap = 0;            // bytes held by stoch_part
+  long long wait_cycles = 0;       // limit of the bounded device waits (0: about 2 s)
 };
 
 namespace sq {
@@ -201,6 +207,9 @@ struct DslashCall {
   Shape shape;
 };
 void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s);
+// halo-tiled kernel (sq_dslash_tile.cu): false if d.shape does not apply
+bool launch_dslash_tile(const sq_ctx* c, const DslashCall& d, cudaStream_t s, int* nparts);
+bool tile_shape_ok(const sq_ctx* c, int prec, int recon, const Shape& sh);
 int dslash_nblk(const sq_ctx* c, Shape sh);
 Shape tune_dslash(sq_ctx* c, DslashCall d, cudaStream_t s);
 bool dslash_tuned(const sq_ctx* c, int prec, int recon, int n);

@@ -33,7 +33,15 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {nullptr};
 
+// The norm kernel of sq_norm2_eo with a fixed number of CTAs per source:
+// each thread strides over the sites, then the same two-level reduction.
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_norm2_fixed(int Vh, Field f, RedArgs ra);
+
 // Device address of the scratch array on the current device (set up once).
+// The one-time set-up also loads the kernels of all three precisions (CUDA
+// loads modules lazily by default), so that no later call of any precision
+// loads code, e.g. while another thread captures a graph.
 cudaError_t scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mu);
@@ -41,14 +49,17 @@ cudaError_t scratch_address(int dev, void** out) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_norm2_fixed<P64>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_norm2_fixed<P32>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_norm2_fixed<P16>);
+    if (e != cudaSuccess) return e;
     g_addr[dev] = p;
   }
   *out = g_addr[dev];
   return cudaSuccess;
 }
 
-// The norm kernel of sq_norm2_eo with a fixed number of CTAs per source:
-// each thread strides over the sites, then the same two-level reduction.
 template <int P>
 __global__ void __launch_bounds__(kThreads) k_norm2_fixed(int Vh, Field f, RedArgs ra) {
   typedef typename Real<P>::T R;

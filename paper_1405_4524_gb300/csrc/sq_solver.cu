@@ -526,6 +526,7 @@ struct Marks {
   unsigned mask = 0;          // marks that record (mark kc opens class kc)
   bool capture = false;
   bool cond = false;          // capturing: FP64 update path under an IF node
+  bool* cond_failed = nullptr;  // set when a conditional node could not be added
   int i = 0;
   void mark(cudaStream_t s) {
     if (!ev) return;
@@ -549,13 +550,17 @@ static unsigned profile_mask(int profile) {
 // Stream capture of a conditional IF node: the node is added after the
 // current dependencies of the capturing stream s, its body is captured on
 // `body` (a second stream); cond_end makes the node the new dependency of s.
+// Returns nullptr (and captures nothing on `body`) if the node could not be
+// added; the caller then launches the body on s.
 static cudaStream_t cond_begin(cudaStream_t s, cudaStream_t body, cudaGraphConditionalHandle h,
                                cudaGraphNode_t* node) {
   cudaStreamCaptureStatus cst;
   cudaGraph_t cg = nullptr;
   const cudaGraphNode_t* deps = nullptr;
   size_t nd = 0;
-  cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &nd);
+  if (cudaStreamGetCaptureInfo(s, &cst, nullptr, &cg, &deps, nullptr, &nd) != cudaSuccess ||
+      cst != cudaStreamCaptureStatusActive || !cg)
+    return nullptr;
   // (the union inside has no default constructor: zeroed storage)
   alignas(cudaGraphNodeParams) unsigned char cpbuf[sizeof(cudaGraphNodeParams)];
   memset(cpbuf, 0, sizeof(cpbuf));
@@ -564,9 +569,12 @@ static cudaStream_t cond_begin(cudaStream_t s, cudaStream_t body, cudaGraphCondi
   cp.conditional.handle = h;
   cp.conditional.type = cudaGraphCondTypeIf;
   cp.conditional.size = 1;
-  cudaGraphAddNode(node, cg, deps, nullptr, nd, &cp);
-  cudaStreamBeginCaptureToGraph(body, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                cudaStreamCaptureModeRelaxed);
+  if (cudaGraphAddNode(node, cg, deps, nullptr, nd, &cp) != cudaSuccess || !cp.conditional.phGraph_out ||
+      !cp.conditional.phGraph_out[0])
+    return nullptr;
+  if (cudaStreamBeginCaptureToGraph(body, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return nullptr;
   return body;
 }
 
@@ -648,7 +656,15 @@ static void launch_iteration(sq_ctx* c, Workspace& w, const CloverSet& cs, doubl
     // FP32 refresh: r = bhat - Mhat (x64 + xs) in FP32 for the refresh list.
     // Its FP32 temporaries live in the FP64 update's buffers (the two paths
     // run one after the other)
-    if (cond) us = cond_begin(s, w.aux, h_ref, &cnode);
+    bool in_node = false;
+    if (cond) {
+      us = cond_begin(s, w.aux, h_ref, &cnode);
+      in_node = us != nullptr;
+      if (!in_node) {
+        us = s;
+        if (m.cond_failed) *m.cond_failed = true;
+      }
+    }
     const Field x32 = make_field(w.x64o.data, c->Vh, P32, n), r32 = make_field(w.r64.data, c->Vh, P32, n);
     const Field t32o = make_field(w.t64o.data, c->Vh, P32, n);
     VArgs rf = vargs(c, w, true);
@@ -676,12 +692,20 @@ static void launch_iteration(sq_ctx* c, Workspace& w, const CloverSet& cs, doubl
     k_rel_r<P, P32><<<bgu, bb, 0, us>>>(rf);
     k_finish<R, 2, FIN_REFRESH><<<n, 256, 0, us>>>(rf.ra, w.refresh_list, &w.ctl->n_refresh, n,
                                                     (int)bgu.x * (kBlasShape.sx / 32));
-    if (cond) cond_end(s, w.aux, cnode);
+    if (in_node) cond_end(s, w.aux, cnode);
     us = s;
   }
   m.mark(s);
   // FP64 update
-  if (cond) us = cond_begin(s, w.aux, h_upd, &cnode);
+  bool in_node = false;
+  if (cond) {
+    us = cond_begin(s, w.aux, h_upd, &cnode);
+    in_node = us != nullptr;
+    if (!in_node) {
+      us = s;
+      if (m.cond_failed) *m.cond_failed = true;
+    }
+  }
   VArgs u = vargs(c, w, true);
   u.f0 = w.x64; u.f1 = w.xs; u.f2 = w.b64; u.f3 = w.r64;
   k_rel_x<PX><<<bgu, bb, 0, us>>>(u);
@@ -703,7 +727,7 @@ static void launch_iteration(sq_ctx* c, Workspace& w, const CloverSet& cs, doubl
   k_rel_r<P, P64><<<bgu, bb, 0, us>>>(u);
   k_finish<R, 2, FIN_UPDATE><<<n, 256, 0, us>>>(u.ra, w.update_list, &w.ctl->n_update, n, (int)bgu.x * (kBlasShape.sx / 32));
   m.mark(us);
-  if (cond) cond_end(s, w.aux, cnode);
+  if (in_node) cond_end(s, w.aux, cnode);
   k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n, m.ev ? w.hist : nullptr, it, chunk);
   m.mark(s);
 }
@@ -1089,6 +1113,10 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       memcpy(&kb, &p.kappa, sizeof(kb));
       const unsigned long long v[] = {p.c->uid, (unsigned long long)p.n, (unsigned long long)p.sh.sx,
                                       (unsigned long long)p.sh.ry, (unsigned long long)p.sh.order,
+                                      (unsigned long long)p.sh.kind,
+                                      (unsigned long long)((p.sh.by << 24) ^ (p.sh.bz << 16) ^ (p.sh.bt << 8) ^
+                                                           p.sh.nbuf),
+                                      (unsigned long long)p.sh.sg,
                                       (unsigned long long)p.c->recon, (unsigned long long)(uintptr_t)p.w->base,
                                       (unsigned long long)(uintptr_t)p.c->U64, (unsigned long long)(uintptr_t)p.c->U32,
                                       (unsigned long long)(uintptr_t)p.cs->Ainv64,
@@ -1099,6 +1127,8 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       key.insert(key.end(), v, v + sizeof(v) / sizeof(v[0]));
     }
     const bool use_graph = prm.use_graph != 0;
+    bool cond_ok = true;      // conditional update nodes may be used
+    bool cond_failed = false;  // adding one failed during the capture
     auto launch_chunk = [&](bool capture) {
       for (int i = 0; i < np; i++) {
         Prob& p = P[i];
@@ -1114,7 +1144,8 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
             m.mask = pmask;
             m.capture = capture;
           }
-          m.cond = capture && prm.profile != 1;
+          m.cond = capture && prm.profile != 1 && cond_ok;
+          m.cond_failed = &cond_failed;
           p.iter(p.c, *p.w, *p.cs, p.kappa, p.sh, ps, m, it, chunk);
         }
         if (ps != sb) {  // join
@@ -1133,6 +1164,17 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       if (e == cudaSuccess) {
         launch_chunk(true);
         e = cudaStreamEndCapture(sb, &g);
+      }
+      if (e == cudaSuccess && cond_failed) {
+        // a conditional node could not be added: capture again with the
+        // update paths as plain launches (they exit on an empty list)
+        cudaGraphDestroy(g);
+        cond_ok = false;
+        e = cudaStreamBeginCapture(sb, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          launch_chunk(true);
+          e = cudaStreamEndCapture(sb, &g);
+        }
       }
       if (e == cudaSuccess) {
         e = cudaGraphInstantiate(graph, g, 0);
@@ -1283,6 +1325,16 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
   return cuda_check(c0, e, "solution copy");
 }
 
+// A bounded device wait of the solve's kernels (the staged-spinor ring of the
+// tiled dslash) that ran out: the results are not to be trusted.
+static sq_status check_timeouts(sq_ctx* c, const char* what) {
+  int bits = 0;
+  sq_status st = read_error_word(c, &bits);
+  if (st != SQ_OK) return st;
+  if (bits & ERRBIT_TIMEOUT) return set_error(c, SQ_ERR_TIMEOUT, "%s: a bounded device wait ran out", what);
+  return SQ_OK;
+}
+
 sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, double* sol, int n, double tol,
                      const sq_solve_params* prm_in, sq_solve_stats* stats) {
   auto t0 = std::chrono::steady_clock::now();
@@ -1310,6 +1362,8 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
   sq_status result = SQ_OK;
   st = run_problems(P, prm, c->stream, &c->ws.graph, &c->ws.graph_key, evs, &result);
   for (auto ev : evs) cudaEventDestroy(ev);
+  if (st != SQ_OK) return st;
+  st = check_timeouts(c, "sq_solve");
   if (st != SQ_OK) return st;
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats)
@@ -1380,6 +1434,16 @@ sq_status solve_batch_impl(const sq_problem* probs, int np, const sq_solve_param
   sq_status result = SQ_OK;
   st = run_problems(P, prm, c0->stream, &B.graph, &B.key, B.events, &result);
   if (st != SQ_OK) return st;
+  for (int i = 0; i < np; i++) {
+    bool seen = false;
+    for (int j = 0; j < i; j++) seen = seen || P[j].c == P[i].c;
+    if (seen) continue;
+    st = check_timeouts(P[i].c, "sq_solve_batch");
+    if (st != SQ_OK) {
+      if (P[i].c != c0) set_error(c0, st, "%s", P[i].c->last_error.c_str());
+      return st;
+    }
+  }
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats)
     for (size_t k = 0; k < off; k++) stats[k].seconds = secs;

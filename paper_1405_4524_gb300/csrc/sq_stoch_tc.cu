@@ -45,6 +45,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "sq_async.cuh"
 #include "sq_internal.h"
 
 namespace sq {
@@ -66,32 +67,7 @@ constexpr int kTcBarOffset = kTcStages * kTcStageBytes;  // 110592
 constexpr int kTcSmemBytes = kTcBarOffset + 256;
 constexpr long long kTcWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
-// ---- PTX wrappers ----------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t a) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(mbar)
-               : "memory");
-}
+// ---- PTX wrappers (mbarriers and bulk copies: sq_async.cuh) ----------------
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
@@ -128,14 +104,16 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 constexpr uint32_t kTcIdesc = (1u << 4) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
 
 // Wait, as a whole warp (uniform result), for the phase of parity `parity`
-// of barrier `bar`; false after about 2 s (ERRBIT_TIMEOUT, abort set) or,
-// if watch_abort, when another role has aborted.
-__device__ bool tc_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* err, bool watch_abort) {
+// of barrier `bar`; false after `limit` cycles (ERRBIT_TIMEOUT, abort set)
+// or, if watch_abort, when another role has aborted. The waits that drain
+// issued copies and products before the CTA leaves use the default limit.
+__device__ bool tc_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* err, bool watch_abort,
+                        long long limit) {
   const long long t0 = clock64();
   while (true) {
     const bool ready = mbar_try(bar, parity);
     if (__all_sync(0xffffffffu, ready)) return true;
-    const bool timed_out = clock64() - t0 > kTcWaitCycles;
+    const bool timed_out = clock64() - t0 > limit;
     const bool stop = timed_out || (watch_abort && *abort);
     if (__any_sync(0xffffffffu, stop)) {
       if (__any_sync(0xffffffffu, timed_out) && (threadIdx.x & 31) == 0) {
@@ -302,7 +280,7 @@ __global__ void __launch_bounds__(256) k_tc_pack_x(const double2* X, int n, int 
 // ---- the product -----------------------------------------------------------
 __global__ void __launch_bounds__(kTcThreads, 2)
     k_stoch_tc(const uint4* A, const uint4* B, const int* exps, int n, int t0, int nkt, int nit, int njt, int nch,
-               double2* O, int* err) {
+               double2* O, int* err, long long wait) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int jt = blockIdx.x, it = blockIdx.y, tb = blockIdx.z;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -323,7 +301,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     mbar_init(done, 1);
     // a timeout anywhere in this launch: the CTAs that start later do no work
     *abort = *(volatile int*)err & ERRBIT_TIMEOUT;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_init_fence();
   }
   __syncthreads();
   const bool skip = *abort != 0;
@@ -351,7 +329,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     int kt = 0;
     for (; kt < nkt; kt++) {
       const int s = kt % kTcStages;
-      if (kt >= kTcStages && !tc_wait(empty0 + 8 * s, ((kt / kTcStages) - 1) & 1, abort, err, true)) break;
+      if (kt >= kTcStages && !tc_wait(empty0 + 8 * s, ((kt / kTcStages) - 1) & 1, abort, err, true, wait)) break;
       if (lane == 0) {
         mbar_expect_tx(full0 + 8 * s, kTcStageBytes);
         bulk_load(ring + s * kTcStageBytes, Ablk + (long long)kt * kTcABytes, kTcABytes, full0 + 8 * s);
@@ -361,15 +339,15 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     }
     // every copy issued has landed before the CTA can leave
     for (int k = max(0, kt - kTcStages); k < kt; k++)
-      tc_wait(full0 + 8 * (k % kTcStages), (k / kTcStages) & 1, abort, err, false);
+      tc_wait(full0 + 8 * (k % kTcStages), (k / kTcStages) & 1, abort, err, false, kTcWaitCycles);
   } else if (warp == 5) {
     // products (the whole warp waits, lane 0 issues); chunk c starts once
     // the epilogue has read chunk c - 1
     for (int kt = 0; kt < nkt; kt++) {
       const int s = kt % kTcStages, c = kt / kTcChunkTiles;
       const bool first = (kt % kTcChunkTiles) == 0;
-      if (first && c >= 1 && !tc_wait(acce, (c - 1) & 1, abort, err, true)) break;
-      if (!tc_wait(full0 + 8 * s, (kt / kTcStages) & 1, abort, err, true)) break;
+      if (first && c >= 1 && !tc_wait(acce, (c - 1) & 1, abort, err, true, wait)) break;
+      if (!tc_wait(full0 + 8 * s, (kt / kTcStages) & 1, abort, err, true, wait)) break;
       tc_fence_after();
       if (lane == 0) {
         const uint32_t a0 = ring + s * kTcStageBytes, b0 = a0 + kTcABytes;
@@ -387,14 +365,14 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     // all products issued by lane 0 have finished
     if (lane == 0) tc_commit(done);
     __syncwarp();
-    tc_wait(done, 0, abort, err, false);
+    tc_wait(done, 0, abort, err, false, kTcWaitCycles);
   } else if (warp < 4) {
     double re[kTcJ], im[kTcJ];
 #pragma unroll
     for (int q = 0; q < kTcJ; q++) re[q] = im[q] = 0.0;
     const int* ex = exps + ((long long)tb * njt * kTcJ + jt * kTcJ) * nch;
     for (int c = 0; c < nch; c++) {
-      if (!tc_wait(accf, c & 1, abort, err, true)) break;
+      if (!tc_wait(accf, c & 1, abort, err, true, wait)) break;
       tc_fence_after();
       int e[kTcJ];
 #pragma unroll
@@ -408,7 +386,9 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         tc_wait_ld();
 #pragma unroll
         for (int q = 0; q < kTcJ; q++) {
-          const double w = __longlong_as_double((long long)(1023 + e[q] - 55 + 11 * (4 - s)) << 52);
+          // exact power of two (subnormal or zero for chunks whose largest
+          // component is near the bottom of the FP64 range)
+          const double w = scalbn(1.0, e[q] - 55 + 11 * (4 - s));
           re[q] = fma((double)__uint_as_float(vr[q]), w, re[q]);
           im[q] = fma((double)__uint_as_float(vi[q]), w, im[q]);
         }
@@ -476,7 +456,9 @@ cudaError_t launch_stoch_tc(const sq_ctx* c, const TcPlan& p, const double* eta,
     k_tc_pack_x<<<dim3(p.nch, p.njt, tb), 256, 0, s>>>((const double2*)X, n, p.T, t0, p.K, p.nkt, p.njt,
                                                                p.nch, B, exps, flag);
     k_stoch_tc<<<dim3(p.njt, p.nit, tb), kTcThreads, kTcSmemBytes, s>>>(A, B, exps, n, t0, p.nkt, p.nit, p.njt,
-                                                                         p.nch, (double2*)O, err);
+                                                                         p.nch, (double2*)O, err,
+                                                                         c->wait_cycles > 0 ? c->wait_cycles
+                                                                                            : kTcWaitCycles);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -105,6 +105,9 @@ _SIG = {
     "sq_dilute": (_i, [_vp, _vp, _i, _i, _vp, _i]),
     "sq_get_profile": (_i, [_vp, C.POINTER(sq_kernel_stat), _i, C.POINTER(_i)]),
     "sq_kernel_launches": (_i, [_vp, C.POINTER(C.c_longlong)]),
+    "sq_set_dslash_shape": (_i, [_vp, _i, _i, _i, C.POINTER(_i)]),
+    "sq_get_dslash_shape": (_i, [_vp, _i, _i, C.POINTER(_i), C.POINTER(_i)]),
+    "sq_set_wait_cycles": (_i, [_vp, C.c_longlong]),
     "sq_status_string": (C.c_char_p, [_i]),
     "sq_last_error": (C.c_char_p, [_vp]),
 }
@@ -465,6 +468,25 @@ def sq_kernel_launches(ctx) -> int:
     n = C.c_longlong()
     _check(ctx, _lib.sq_kernel_launches(ctx, C.byref(n)))
     return n.value
+
+
+def sq_set_dslash_shape(ctx, prec: int, n_rhs: int, kind: int, shape) -> None:
+    """kind 0: shape = (sites per CTA, sources per CTA, order); kind 1 (halo
+    tiles): shape = (rows in y, z, t, source slots per CTA, ring depth)."""
+    v = (C.c_int * 5)(*(list(shape) + [0] * (5 - len(shape))))
+    _check(ctx, _lib.sq_set_dslash_shape(ctx, int(prec), int(n_rhs), int(kind), v))
+
+
+def sq_get_dslash_shape(ctx, prec: int, n_rhs: int):
+    """(kind, shape tuple of 5) chosen for (prec, n_rhs) on this context."""
+    k = C.c_int(0)
+    v = (C.c_int * 5)()
+    _check(ctx, _lib.sq_get_dslash_shape(ctx, int(prec), int(n_rhs), C.byref(k), v))
+    return k.value, tuple(v)
+
+
+def sq_set_wait_cycles(ctx, cycles: int) -> None:
+    _check(ctx, _lib.sq_set_wait_cycles(ctx, C.c_longlong(int(cycles))))
 
 
 class Lattice:

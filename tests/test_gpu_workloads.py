@@ -64,15 +64,20 @@ def test_dslash_full_size(name, prec, tol):
         bin_, bx, bout = device_buffer(fb), device_buffer(fb), device_buffer(fb)
         sq.sq_pack_spinor(ctx, bin_, psi, 1, prec, n)
         sq.sq_pack_spinor(ctx, bx, x, 0, prec, n)
-        sq.sq_dslash_eo(ctx, bout, bin_, bx, 0, prec, n,
-                        sq.SQ_DS_CLOVER_INV | sq.SQ_DS_XPAY | sq.SQ_DS_SYNC, a)
-        got = np.zeros_like(psi)
-        sq.sq_unpack_spinor(ctx, got, bout, 0, prec, n)
         Ainv = np.linalg.inv(oracle.clover_matrices(F, kappa, csw))
-        for k in range(n):
-            w = oracle.site_apply(Ainv, oracle.hopping_eo(U, psi[k], 0, par, -1.0))
-            want = oracle.restrict(x[k] + a * w, par, 0)
-            assert rel(got[k], want) < tol
+        want = [oracle.restrict(x[k] + a * oracle.site_apply(Ainv, oracle.hopping_eo(U, psi[k], 0, par, -1.0)),
+                                par, 0) for k in range(n)]
+        del Ainv
+        # the autotuned shape, then each kernel forced: per-site and halo-tiled
+        for force in [None, (0, (64, 2, 0)), (1, (4, 2, 2, 2, 2))]:
+            if force is not None:
+                sq.sq_set_dslash_shape(ctx, prec, n, *force)
+            sq.sq_dslash_eo(ctx, bout, bin_, bx, 0, prec, n,
+                            sq.SQ_DS_CLOVER_INV | sq.SQ_DS_XPAY | sq.SQ_DS_SYNC, a)
+            got = np.zeros_like(psi)
+            sq.sq_unpack_spinor(ctx, got, bout, 0, prec, n)
+            for k in range(n):
+                assert rel(got[k], want[k]) < tol, (force, k)
     finally:
         sq.sq_destroy(ctx)
 
