@@ -447,9 +447,11 @@ sq_status sq_get_dslash_shape(const sq_ctx *ctx, sq_prec prec, int n_rhs, int *k
  * (about 2 s). A wait that runs out records a timeout, lets the copies it
  * issued drain and returns, and the call reports SQ_ERR_TIMEOUT (sq_solve,
  * sq_dslash_eo with SQ_DS_SYNC, sq_contract_stoch_op_z4); the context stays
- * usable. A limit of a few cycles makes the first wait run out, which tests
- * that path. Errors: SQ_ERR_ARG (negative). */
-sq_status sq_set_wait_cycles(sq_ctx *ctx, long long cycles);
+ * usable. stall_test = 1 (a test of that path) makes those kernels first
+ * wait, with this limit, on a barrier that nothing completes, so the wait
+ * runs out and the call returns SQ_ERR_TIMEOUT; 0 is normal operation.
+ * Errors: SQ_ERR_ARG (negative cycles, stall_test not 0/1). */
+sq_status sq_set_wait_cycles(sq_ctx *ctx, long long cycles, int stall_test);
 
 const char *sq_status_string(sq_status s);
 const char *sq_last_error(const sq_ctx *ctx);

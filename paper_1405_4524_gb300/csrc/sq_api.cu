@@ -489,10 +489,12 @@ sq_status sq_get_dslash_shape(const sq_ctx* c, sq_prec prec, int n, int* kind, i
   return SQ_OK;
 }
 
-sq_status sq_set_wait_cycles(sq_ctx* c, long long cycles) {
+sq_status sq_set_wait_cycles(sq_ctx* c, long long cycles, int stall_test) {
   if (!c) return SQ_ERR_ARG;
-  if (cycles < 0) return set_error(c, SQ_ERR_ARG, "sq_set_wait_cycles: negative limit");
+  if (cycles < 0 || (stall_test != 0 && stall_test != 1))
+    return set_error(c, SQ_ERR_ARG, "sq_set_wait_cycles: bad argument");
   c->wait_cycles = cycles;
+  c->wait_stall = stall_test;
   return SQ_OK;
 }
 

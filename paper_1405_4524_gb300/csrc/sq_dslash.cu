@@ -299,9 +299,15 @@ bool dslash_tuned(const sq_ctx* c, int prec, int recon, int n) {
   return c->tuned.find(key) != c->tuned.end();
 }
 
-// Halo-tiled shapes for the tuner: the tiles (all of x, by x bz x bt rows
-// dividing the lattice, 128 to 256 sites) with the fewest staged rows per
-// site, each with a few source-group sizes and ring depths.
+// Halo-tiled shapes for the tuner: the two tiles (all of x, by x bz x bt
+// rows dividing the lattice, 128 to 256 sites) with the fewest staged rows
+// per site, with a double-buffered ring and the largest source group that
+// fills the machine. Measured on GB300 (16^3x32 .. 32^3x64, FP32 and FP16)
+// the tiled kernel ran 1.4-2x slower than the per-site kernel: with links
+// and clover blocks resident in registers (255 per thread) only 8 warps fit
+// on an SM, so it issues half as often, although it moves 40% fewer bytes
+// from L2. It stays a candidate for the lattices and source counts where
+// that balance turns.
 static void tile_candidates(const sq_ctx* c, int prec, int recon, int n, std::vector<Shape>& out) {
   if ((prec != P32 && prec != P16) || recon != 12) return;
   const int X2 = c->dims[0] / 2, Y = c->dims[1], Z = c->dims[2], T = c->dims[3];
@@ -321,22 +327,24 @@ static void tile_candidates(const sq_ctx* c, int prec, int recon, int n, std::ve
         tiles.push_back({(double)rows / (by * bz * bt), by, bz, bt});
       }
   std::sort(tiles.begin(), tiles.end(), [](const Cand& a, const Cand& b) { return a.halo < b.halo; });
-  if (tiles.size() > 4) tiles.resize(4);
-  const int groups[] = {2, 4, 8, 16};
-  for (const Cand& t : tiles)
-    for (int sg : groups) {
-      if (sg > n && sg != 2) continue;
-      for (int nbuf = 2; nbuf <= 3; nbuf++) {
-        Shape sh;
-        sh.kind = 1;
-        sh.by = t.by;
-        sh.bz = t.bz;
-        sh.bt = t.bt;
-        sh.sg = sg;
-        sh.nbuf = nbuf;
-        if (tile_shape_ok(c, prec, recon, sh)) out.push_back(sh);
-      }
-    }
+  if (tiles.size() > 2) tiles.resize(2);
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+  for (const Cand& t : tiles) {
+    // the largest group (fewest reloads of the gauge data) that still gives
+    // at least four CTAs per SM
+    const int ntiles = (Y / t.by) * (Z / t.bz) * (T / t.bt);
+    int sg = n;
+    while (sg > 2 && (long long)ntiles * ((n + sg - 1) / sg) < 4LL * (nsm > 0 ? nsm : 152)) sg = (sg + 1) / 2;
+    Shape sh;
+    sh.kind = 1;
+    sh.by = t.by;
+    sh.bz = t.bz;
+    sh.bt = t.bt;
+    sh.sg = sg;
+    sh.nbuf = 2;
+    if (tile_shape_ok(c, prec, recon, sh)) out.push_back(sh);
+  }
 }
 
 // Pick the launch shape by timing the candidates on the call's own fields

@@ -39,7 +39,7 @@ namespace sq {
 
 constexpr int kTileMaxThreads = 256;
 constexpr int kTileMaxSlots = 512;  // row segments of a tile (fixed slots)
-constexpr int kTileBarBytes = 64;   // up to 4 ring barriers, 16-byte aligned
+constexpr int kTileBarBytes = 64;   // ring barriers (<= 3), a never-completed one at byte 56
 constexpr long long kTileWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
 struct TileArgs {
@@ -62,6 +62,7 @@ struct TileArgs {
   int S;                // staged sites per source buffer
   uint32_t buf_bytes;   // bytes of one source buffer = bytes copied per source
   long long wait_cycles;
+  int stall;            // test: first wait on a barrier that nothing completes
   RedArgs ra;
   int* err;
 };
@@ -257,6 +258,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, 1) k_dslash_tile(const __grid
 
   if (tid == 0) {
     for (int b = 0; b < a.nbuf; b++) mbar_init(smem_addr(bars + b), 1);
+    mbar_init(smem_addr(bars + 7), 1);  // nothing arrives on it
     mbar_init_fence();
   }
   for (int q = tid; q < a.nslot; q += blockDim.x) {
@@ -334,7 +336,8 @@ __global__ void __launch_bounds__(kTileMaxThreads, 1) k_dslash_tile(const __grid
 
   for (int i = 0; i < ns; i++) {
     const int b = i % a.nbuf;
-    const bool ok = mbar_wait_bounded(smem_addr(bars + b), (uint32_t)((i / a.nbuf) & 1), a.wait_cycles);
+    bool ok = !(a.stall && i == 0) || mbar_wait_bounded(smem_addr(bars + 7), 0u, a.wait_cycles);
+    ok = ok && mbar_wait_bounded(smem_addr(bars + b), (uint32_t)((i / a.nbuf) & 1), a.wait_cycles);
     if (__syncthreads_or(!ok)) {
       // a copy did not land in time: record it, let the issued copies
       // drain (bounded) and stop
@@ -530,6 +533,7 @@ bool launch_dslash_tile(const sq_ctx* c, const DslashCall& d, cudaStream_t s, in
   a.S = p.S;
   a.buf_bytes = p.buf_bytes;
   a.wait_cycles = c->wait_cycles > 0 ? c->wait_cycles : kTileWaitCycles;
+  a.stall = c->wait_stall;
   a.ra = d.ra;
   a.err = c->d_err;
   const int grid = p.ntiles * a.ngroups;

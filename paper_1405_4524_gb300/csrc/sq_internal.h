@@ -160,6 +160,7 @@ struct sq_ctx {
   void* stoch_part = nullptr;      // K-group partials of the stochastic operators
   size_t stoch_cap = 0;            // bytes held by stoch_part
   long long wait_cycles = 0;       // limit of the bounded device waits (0: about 2 s)
+  int wait_stall = 0;              // test: wait first on a barrier nothing completes
 };
 
 namespace sq {

@@ -1116,7 +1116,8 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
                                       (unsigned long long)p.sh.kind,
                                       (unsigned long long)((p.sh.by << 24) ^ (p.sh.bz << 16) ^ (p.sh.bt << 8) ^
                                                            p.sh.nbuf),
-                                      (unsigned long long)p.sh.sg,
+                                      (unsigned long long)p.sh.sg, (unsigned long long)p.c->wait_cycles,
+                                      (unsigned long long)p.c->wait_stall,
                                       (unsigned long long)p.c->recon, (unsigned long long)(uintptr_t)p.w->base,
                                       (unsigned long long)(uintptr_t)p.c->U64, (unsigned long long)(uintptr_t)p.c->U32,
                                       (unsigned long long)(uintptr_t)p.cs->Ainv64,

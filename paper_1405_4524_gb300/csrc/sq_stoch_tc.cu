@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(256) k_tc_pack_x(const double2* X, int n, int 
 // ---- the product -----------------------------------------------------------
 __global__ void __launch_bounds__(kTcThreads, 2)
     k_stoch_tc(const uint4* A, const uint4* B, const int* exps, int n, int t0, int nkt, int nit, int njt, int nch,
-               double2* O, int* err, long long wait) {
+               double2* O, int* err, long long wait, int stall) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int jt = blockIdx.x, it = blockIdx.y, tb = blockIdx.z;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -290,6 +290,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   const uint32_t accf = empty0 + 8 * kTcStages, acce = accf + 8, done = acce + 8;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kTcBarOffset + 8 * (2 * kTcStages + 3));
   volatile int* abort = reinterpret_cast<volatile int*>(tslot + 1);
+  const uint32_t never = smem_addr(bars) + 8 * (2 * kTcStages + 3) + 8;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kTcStages; s++) {
@@ -299,6 +300,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     mbar_init(accf, 1);
     mbar_init(acce, 128);
     mbar_init(done, 1);
+    mbar_init(never, 1);  // nothing arrives on it (the stall test)
     // a timeout anywhere in this launch: the CTAs that start later do no work
     *abort = *(volatile int*)err & ERRBIT_TIMEOUT;
     mbar_init_fence();
@@ -343,7 +345,8 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   } else if (warp == 5) {
     // products (the whole warp waits, lane 0 issues); chunk c starts once
     // the epilogue has read chunk c - 1
-    for (int kt = 0; kt < nkt; kt++) {
+    const bool stalled = stall && !tc_wait(never, 0, abort, err, true, wait);
+    for (int kt = 0; kt < nkt && !stalled; kt++) {
       const int s = kt % kTcStages, c = kt / kTcChunkTiles;
       const bool first = (kt % kTcChunkTiles) == 0;
       if (first && c >= 1 && !tc_wait(acce, (c - 1) & 1, abort, err, true, wait)) break;
@@ -458,7 +461,8 @@ cudaError_t launch_stoch_tc(const sq_ctx* c, const TcPlan& p, const double* eta,
     k_stoch_tc<<<dim3(p.njt, p.nit, tb), kTcThreads, kTcSmemBytes, s>>>(A, B, exps, n, t0, p.nkt, p.nit, p.njt,
                                                                          p.nch, (double2*)O, err,
                                                                          c->wait_cycles > 0 ? c->wait_cycles
-                                                                                            : kTcWaitCycles);
+                                                                                            : kTcWaitCycles,
+                                                                         c->wait_stall);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -107,7 +107,7 @@ _SIG = {
     "sq_kernel_launches": (_i, [_vp, C.POINTER(C.c_longlong)]),
     "sq_set_dslash_shape": (_i, [_vp, _i, _i, _i, C.POINTER(_i)]),
     "sq_get_dslash_shape": (_i, [_vp, _i, _i, C.POINTER(_i), C.POINTER(_i)]),
-    "sq_set_wait_cycles": (_i, [_vp, C.c_longlong]),
+    "sq_set_wait_cycles": (_i, [_vp, C.c_longlong, _i]),
     "sq_status_string": (C.c_char_p, [_i]),
     "sq_last_error": (C.c_char_p, [_vp]),
 }
@@ -485,8 +485,8 @@ def sq_get_dslash_shape(ctx, prec: int, n_rhs: int):
     return k.value, tuple(v)
 
 
-def sq_set_wait_cycles(ctx, cycles: int) -> None:
-    _check(ctx, _lib.sq_set_wait_cycles(ctx, C.c_longlong(int(cycles))))
+def sq_set_wait_cycles(ctx, cycles: int, stall_test: bool = False) -> None:
+    _check(ctx, _lib.sq_set_wait_cycles(ctx, C.c_longlong(int(cycles)), int(bool(stall_test))))
 
 
 class Lattice:

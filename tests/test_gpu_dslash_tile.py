@@ -210,9 +210,10 @@ def test_full_size_fp16_tiled_vs_per_site():
 
 
 def test_bounded_wait_runs_out():
-    """A wait limit of one cycle: the staged-spinor wait runs out, the call
-    reports SQ_ERR_TIMEOUT, and with the limit restored the same context
-    gives the oracle's result."""
+    """The stall test: every CTA first waits, with a limit of 2000 cycles, on a
+    barrier that nothing completes; the wait runs out, the CTA lets its
+    issued copies land and returns, and the call reports SQ_ERR_TIMEOUT.
+    With normal waits restored the same context gives the oracle's result."""
     from paper_1405_4524_gb300 import stochq as sq
 
     dims = (8, 4, 4, 8)
@@ -222,13 +223,38 @@ def test_bounded_wait_runs_out():
         psi = random_spinors(dims, n, 81)
         x = random_spinors(dims, n, 82)
         sq.sq_set_dslash_shape(s.ctx, 1, n, 1, (4, 2, 2, 8, 2))
-        sq.sq_set_wait_cycles(s.ctx, 1)
+        sq.sq_set_wait_cycles(s.ctx, 2000, True)
         with pytest.raises(sq.StochqError) as e:
             run_dslash(s, 1, n, psi, x, 1, 0, 0.0)
         assert e.value.status == sq.SQ_ERR_TIMEOUT
-        sq.sq_set_wait_cycles(s.ctx, 0)
+        sq.sq_set_wait_cycles(s.ctx, 0, False)
         got = run_dslash(s, 1, n, psi, x, 1, 0, 0.0)
         for k in range(n):
             assert rel(got[k], oracle_dslash(s, psi[k], x[k], 1, 0, 0, 0, 0, 0)) < 1e-6
     finally:
         s.close()
+
+
+def test_solve_reports_timeout():
+    """A solve whose tiled dslash waits run out returns SQ_ERR_TIMEOUT; the
+    context then solves normally."""
+    from paper_1405_4524_gb300 import inputs, stochq as sq
+
+    dims = (8, 4, 4, 8)
+    U = inputs.make_links(dims, 0.25, 1007)
+    eta = inputs.make_z4(dims, 2, 2008)
+    ctx = sq.sq_create(dims, -1)
+    try:
+        sq.sq_load_gauge(ctx, U, 12)
+        sq.sq_set_dslash_shape(ctx, 1, 2, 1, (2, 2, 2, 2, 2))
+        sq.sq_set_wait_cycles(ctx, 2000, True)
+        sol = np.zeros_like(eta)
+        st, _ = sq.sq_solve(ctx, 0.12, 1.0, eta, sol, 2, 1e-10, sq.sq_default_params(max_iter=40),
+                            raise_on_error=False)
+        assert st == sq.SQ_ERR_TIMEOUT
+        sq.sq_set_wait_cycles(ctx, 0, False)
+        sol[...] = 0
+        st, stats = sq.sq_solve(ctx, 0.12, 1.0, eta, sol, 2, 1e-10)
+        assert st == 0 and all(x["true_residual"] <= 1e-10 for x in stats)
+    finally:
+        sq.sq_destroy(ctx)

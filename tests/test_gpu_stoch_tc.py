@@ -170,3 +170,40 @@ def test_tensor_core_timeslice_batches(sq):
         sq.sq_destroy(ctx)
         del eta, X
         torch.cuda.empty_cache()
+
+
+def test_tensor_core_bounded_wait_runs_out(sq):
+    """The stall test: the product warp first waits, with a limit of 2000
+    cycles, on a barrier that nothing completes; the call reports
+    SQ_ERR_TIMEOUT after the issued copies and products have drained and the
+    tensor memory is freed. Normal waits then give the oracle's operators."""
+    dims, n = (4, 4, 4, 8), 20
+    eta = inputs.make_z4(dims, n, 7301)
+    X = scaled_spinors(dims, n, 7302)
+    ctx = sq.sq_create(dims, -1)
+    try:
+        sq.sq_set_wait_cycles(ctx, 2000, True)
+        with pytest.raises(sq.StochqError) as e:
+            sq.sq_contract_stoch_op(ctx, eta, X, n, tensor_cores=True)
+        assert e.value.status == sq.SQ_ERR_TIMEOUT
+        sq.sq_set_wait_cycles(ctx, 0, False)
+        O, C = sq.sq_contract_stoch_op(ctx, eta, X, n, tensor_cores=True)
+        assert close(O, oracle.stochastic_operator(eta, X))
+    finally:
+        sq.sq_destroy(ctx)
+
+
+def test_tensor_core_tiny_magnitudes(sq):
+    """Sources whose chunks' largest component sits near the bottom of the
+    FP64 normal range: the exact digit weights become subnormal powers of
+    two and the operators still match the oracle (relative to their size)."""
+    dims, n = (2, 2, 2, 4), 3
+    eta = inputs.make_z4(dims, n, 7401)
+    X = random_spinors(dims, n, 7402) * 2.0 ** -1000
+    ctx = sq.sq_create(dims, -1)
+    try:
+        O, _ = sq.sq_contract_stoch_op(ctx, eta, X, n, tensor_cores=True)
+        want = oracle.stochastic_operator(eta, X)
+        assert float(np.max(np.abs(O - want))) <= 1e-10 * float(np.max(np.abs(want)))
+    finally:
+        sq.sq_destroy(ctx)
