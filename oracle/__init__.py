@@ -7,9 +7,12 @@ and imports nothing from it; both sides take their inputs from the seeded
 generators in ``paper_1405_4524_gb300.inputs``.
 
 Every function here is pinned by a check in ``tests/test_oracle_pins.py``
-against something other than itself (closed forms, invariants, dense LU).
+(``tests/test_oracle_diagrams.py`` for the diagram contractions of
+``oracle.diagrams``) against something other than itself (closed forms,
+invariants, dense LU).
 """
 
+from . import diagrams  # noqa: F401
 from .dirac import (  # noqa: F401
     GAMMA,
     GAMMA5,

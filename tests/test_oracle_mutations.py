@@ -278,3 +278,100 @@ def test_dilution_mutation_is_caught(fn, monkeypatch):
         except AssertionError:
             caught = True
     assert caught
+
+
+# ---------------------------------------------------------------------------
+# diagram contractions (oracle/diagrams.py)
+# ---------------------------------------------------------------------------
+
+def _per_config_variant(kind):
+    from oracle import diagrams as dg
+
+    def per_config(Sp, SA, SB, T):
+        out = np.zeros((7, T), dtype=np.complex128)
+        V3 = Sp.shape[1] * Sp.shape[2] * Sp.shape[3]
+        sp = Sp.reshape(T, V3, 12, 12)
+        for t in range(T):
+            out[0, t] = np.sum(np.abs(sp[t]) ** 2)
+            t0 = t if kind == "q0_source_on_t" else 0
+            A0, B0 = SA[t0][t].reshape(V3, V3, 12, 12), SB[t0][t].reshape(V3, V3, 12, 12)
+            out[1, t] = np.einsum("zxab,zxab->", A0, np.conj(B0))
+            At, Bt = SA[t][t].reshape(V3, V3, 12, 12), SB[t][t].reshape(V3, V3, 12, 12)
+            out[2, t] = np.einsum("zyab,zyab->", At, np.conj(Bt))
+            Ax = SA[t][t if kind == "x_on_t" else 0].reshape(V3, V3, 12, 12)
+            By = SB[t][t].reshape(V3, V3, 12, 12)
+            if kind == "no_dagger_on_B":
+                out[5, t] = np.einsum("xba,xzbc,ycd,yda->", np.conj(sp[0]), Ax, By.sum(axis=1), sp[t], optimize=True)
+            elif kind == "point_transposed":
+                out[5, t] = np.einsum("xab,xzbc,yzdc,yda->", sp[0], Ax, np.conj(By), sp[t], optimize=True)
+            else:
+                out[5, t] = np.einsum("xba,xzbc,yzdc,yda->", np.conj(sp[0]), Ax, np.conj(By), sp[t], optimize=True)
+        out[3] = out[0] * out[1]
+        out[4] = out[2] * (out[0] if kind == "c1_with_P_t" else out[0, 0])
+        out[6] = np.conj(out[5])
+        return out
+    return per_config
+
+
+def _filled_variant(kind):
+    def fill(eta, X, t0):
+        n, T, Z, Y, Xd = eta.shape[:5]
+        Xm = X.reshape(n, T, Z, Y, Xd, 12)
+        em = eta[:, t0].reshape(n, Z, Y, Xd, 12)
+        e = em if kind == "no_conj" else np.conj(em)
+        out = np.einsum("itzyxa,iwvub->tzyxwvuab", Xm, e)
+        return out if kind == "no_norm" else out / n
+    return fill
+
+
+def _point_transposed(Xp):
+    T, Z, Y, X = Xp.shape[1:5]
+    return np.moveaxis(Xp.reshape(12, T, Z, Y, X, 12), 0, -2)
+
+
+def _ensemble_P_t(per_cfg):
+    m = np.mean(per_cfg, axis=0)
+    P, Q0, Qtt, C0, C1, C2, C3 = m
+    c0, c1 = C0 - P * Q0, C1 - Qtt * P
+    return np.array([c0, c1, C2, C3, c0 + c1 - C2 - C3])
+
+
+def _run_diagram_pins():
+    import test_oracle_diagrams as pd
+
+    tiny = pd.setup((2, 2, 2, 2), 61)
+    small = pd.setup((4, 2, 2, 4), 62)
+    tiny, small = ((2, 2, 2, 2), tiny[1]), ((4, 2, 2, 4), small[1])
+    checks = [lambda: pd.test_exact_diagrams_site_loops(tiny),
+              lambda: pd.test_diagram2_gamma5_hermiticity("tiny", tiny, small),
+              lambda: pd.test_complete_basis_is_exact(tiny),
+              lambda: pd.test_stochastic_estimates_are_unbiased(small),
+              lambda: pd.test_point_factor_is_the_pion_contraction(small),
+              lambda: pd.test_two_sets_trace_factors_match_the_filled_trace(small),
+              lambda: pd.test_gram_rearrangement_of_diagram2(small),
+              pd.test_ensemble_subtraction_is_a_covariance]
+    for c in checks:  # the mutation is caught once one pin fails
+        try:
+            c()
+        except AssertionError:
+            return False
+    return True
+
+
+@pytest.mark.parametrize("kind", ["q0_source_on_t", "x_on_t", "no_dagger_on_B", "point_transposed_c2",
+                                  "c1_with_P_t", "fill_no_conj", "fill_no_norm", "point_propagator_transposed",
+                                  "ensemble_P_t"])
+def test_diagram_mutation_is_caught(kind, monkeypatch):
+    from oracle import diagrams as dg
+
+    if kind in ("q0_source_on_t", "x_on_t", "no_dagger_on_B", "c1_with_P_t"):
+        monkeypatch.setattr(dg, "_per_config", _per_config_variant(kind))
+    elif kind == "point_transposed_c2":
+        monkeypatch.setattr(dg, "_per_config", _per_config_variant("point_transposed"))
+    elif kind in ("fill_no_conj", "fill_no_norm"):
+        monkeypatch.setattr(dg, "filled_propagator", _filled_variant(kind[5:]))
+    elif kind == "point_propagator_transposed":
+        monkeypatch.setattr(dg, "point_propagator", _point_transposed)
+    else:
+        monkeypatch.setattr(dg, "ensemble", _ensemble_P_t)
+    assert not _run_diagram_pins(), f"mutation not caught: {kind}"
