@@ -398,6 +398,56 @@ sq_status sq_contract_prop_trace(sq_ctx *ctx, const double *etaA, const double *
                                  const double *etaB, const double *XB, int n_rhs,
                                  double *C, int where);
 
+/* Diagram contractions of the two-pion correlation function at zero
+ * momentum for one gauge configuration (Sec. "Stochastic propagators":
+ * Diagram 0; Sec. "Correlation function": Diagrams 1-3 and the sum
+ * C = C0 + C1 - C2 - C3). Inputs are lexicographic FP64 fields, as sq_solve
+ * takes them:
+ *   Xp        12 solutions Xp[a] = M^{-1} e_a, e_a the unit source of
+ *             spin-colour a = 3*spin + colour at the origin: the point
+ *             propagator S(.;0,0) (sq_dilute's spin-colour dilution of a
+ *             noise vector equal to 1 on the twelve components of site 0
+ *             gives the twelve sources)
+ *   etaA, XA  n_rhs noise sources and their solutions, used for every
+ *             all-to-all S of Eq. Sfill, S(w;w') ~ (1/n_rhs) sum_i XA_i(w) etaA_i(w')^+
+ *   etaB, XB  a second, independent set, used for every S^+ (both NULL:
+ *             set A, the paper's one-set option, which correlates S and S^+)
+ * Output out[7][T] complex (re, im), q = 0..6 at sink timeslice t:
+ *   0 P(t)   = sum_y tr[S(t,y;0,0) S^+(t,y;0,0)]   (real; Table Lcomp's
+ *              "sum_y tr S_p S_p^+")
+ *   1 Q0(t)  = sum_x sum_z tr[S(t,z;0,x) S^+(t,z;0,x)]   (Table Lcomp's
+ *              "sum_x sum_z tr S_s S_s^+")
+ *   2 Qtt(t) = sum_y sum_z tr[S(t,z;t,y) S^+(t,z;t,y)]
+ *   3 C0(t)  = P(t) Q0(t)   Diagram 0 before its vacuum term <P><Q0>
+ *   4 C1(t)  = Qtt(t) P(0)  Diagram 1 before its vacuum terms
+ *   5 C2(t)  = sum_{x,y,z} tr[S^+(0,x;0,0) S(0,x;t,z) S^+(t,y;t,z) S(t,y;0,0)]
+ *   6 C3(t)  = conj C2(t)   Diagram 3
+ * with x on timeslice 0, y and z on timeslice t and daggers on spin-colour
+ * only. Diagram 0's printed second trace pairs S(t,z;0,0) with S^+(t,x;0,0);
+ * the library takes the text around it (a source at (0,x), a sink at
+ * (t,z), the all-to-all S(t,z;0,x)). S is never formed: C2(t) =
+ * (1/n^2) sum_ij Q_ij(t) W_ji(t) with Q_ij(t) = sum_{z in t} etaA_i^+ etaB_j
+ * and W_ji(t) = sum_a conj(GB(t)_aj) GA(0)_ai, G(t)_ai = sum_{y in t}
+ * Xp_a^+ X_i; FP64 with a fixed summation order. All inputs and out host or
+ * all device per `where`; host memory: returns when out is written; device
+ * memory: ordered after the caller's stream, no wait. Uses the context's
+ * contraction buffer. Errors: SQ_ERR_ARG (NULL Xp/etaA/XA/out, only one of
+ * etaB/XB, n_rhs <= 0 or > 4080, bad where), SQ_ERR_OOM, SQ_ERR_CUDA. */
+sq_status sq_contract_diagrams(sq_ctx *ctx, const double *Xp, const double *etaA, const double *XA,
+                               const double *etaB, const double *XB, int n_rhs, double *out, int where);
+
+/* Vacuum-subtracted averages over n_cfg gauge configurations of the records
+ * of sq_contract_diagrams (rec[cfg][7][T] complex; the paper averages every
+ * diagram over configurations, Sec. "Correlation function"): out[5][T] complex,
+ *   0 <C0> - <P><Q0>                   (Diagram 0 with its vacuum term)
+ *   1 <(Qtt - <Qtt>)(P(0) - <P(0)>)>   (Diagram 1)
+ *   2 <C2>   3 <C3>
+ *   4 C = C0 + C1 - C2 - C3            (the sum of the diagrams)
+ * on the context's GPU, configurations summed in order. rec and out host or
+ * device per `where`. Errors: SQ_ERR_ARG (NULL, n_cfg <= 0, bad where),
+ * SQ_ERR_CUDA. */
+sq_status sq_diagrams_ensemble(sq_ctx *ctx, const double *rec, int n_cfg, double *out, int where);
+
 /* Per kernel class of the solver's inner loop (profiling). */
 typedef struct sq_kernel_stat {
   char name[48];       /* kernel class, e.g. "dslash_clover"              */

@@ -823,6 +823,78 @@ sq_status sq_contract_prop_trace(sq_ctx* c, const double* etaA, const double* XA
   return leave_stream(c);
 }
 
+sq_status sq_contract_diagrams(sq_ctx* c, const double* Xp, const double* etaA, const double* XA,
+                               const double* etaB, const double* XB, int n, double* out, int where) {
+  if (!c) return SQ_ERR_ARG;
+  if (!Xp || !etaA || !XA || !out || n <= 0 || n > 4080 || (!etaB) != (!XB) ||
+      (where != SQ_HOST && where != SQ_DEVICE))
+    return set_error(c, SQ_ERR_ARG, "sq_contract_diagrams: bad argument");
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  const int T = c->dims[3];
+  s = grow_contract_scratch(c, diagram_scratch_bytes(c, n));
+  if (s != SQ_OK) return s;
+  const double* in[5] = {Xp, etaA, XA, etaB ? etaB : etaA, XB ? XB : XA};
+  const int cnt[5] = {12, n, n, n, n};
+  const double* dev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  double* tmp[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  const int nin = etaB ? 5 : 3;
+  for (int k = 0; k < nin && s == SQ_OK; k++) s = stage_in(c, in[k], cnt[k], where, &dev[k], &tmp[k]);
+  if (nin == 3) {
+    dev[3] = dev[1];
+    dev[4] = dev[2];
+  }
+  const size_t ob = (size_t)7 * T * 2 * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  double* dout = out;
+  if (s == SQ_OK && where == SQ_HOST) e = cudaMallocAsync((void**)&dout, ob, c->stream);
+  if (s == SQ_OK && e == cudaSuccess) {
+    launch_diagrams(c, dev[0], dev[1], dev[2], dev[3], dev[4], n, dout, c->stoch_part, c->stream);
+    c->launches += 11;
+    e = cudaGetLastError();
+    if (e == cudaSuccess && where == SQ_HOST) e = cudaMemcpyAsync(out, dout, ob, cudaMemcpyDeviceToHost, c->stream);
+  }
+  if (where == SQ_HOST && dout && dout != out) cudaFreeAsync(dout, c->stream);
+  for (int k = 0; k < 5; k++)
+    if (tmp[k]) cudaFreeAsync(tmp[k], c->stream);
+  if (s != SQ_OK) return s;
+  if (e == cudaSuccess && where == SQ_HOST) e = cudaStreamSynchronize(c->stream);
+  s = cuda_check(c, e, "sq_contract_diagrams");
+  if (s != SQ_OK) return s;
+  return leave_stream(c);
+}
+
+sq_status sq_diagrams_ensemble(sq_ctx* c, const double* rec, int ncfg, double* out, int where) {
+  if (!c) return SQ_ERR_ARG;
+  if (!rec || !out || ncfg <= 0 || (where != SQ_HOST && where != SQ_DEVICE))
+    return set_error(c, SQ_ERR_ARG, "sq_diagrams_ensemble: bad argument");
+  sq_status s = enter_stream(c);
+  if (s != SQ_OK) return s;
+  const int T = c->dims[3];
+  const size_t rb = (size_t)ncfg * 7 * T * 2 * sizeof(double), ob = (size_t)5 * T * 2 * sizeof(double);
+  const double* drec = rec;
+  double* dout = out;
+  char* tmp = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (where == SQ_HOST) {
+    e = cudaMallocAsync((void**)&tmp, rb + ob + 256, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, rec, rb, cudaMemcpyHostToDevice, c->stream);
+    drec = (const double*)tmp;
+    dout = (double*)(tmp + ((rb + 255) & ~(size_t)255));
+  }
+  if (e == cudaSuccess) {
+    launch_diag_ensemble(drec, ncfg, T, dout, c->stream);
+    c->launches += 1;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && where == SQ_HOST) e = cudaMemcpyAsync(out, dout, ob, cudaMemcpyDeviceToHost, c->stream);
+  if (tmp) cudaFreeAsync(tmp, c->stream);
+  if (e == cudaSuccess && where == SQ_HOST) e = cudaStreamSynchronize(c->stream);
+  s = cuda_check(c, e, "sq_diagrams_ensemble");
+  if (s != SQ_OK) return s;
+  return leave_stream(c);
+}
+
 sq_status sq_get_profile(const sq_ctx* c, sq_kernel_stat* out, int max, int* n) {
   static const char* names[KC_N] = {
       "dslash_clover",         "dslash_clover_xpay_alpha", "blas_s_update",

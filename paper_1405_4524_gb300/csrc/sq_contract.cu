@@ -7,6 +7,8 @@
 // One CTA per (source, timeslice): a timeslice of the lexicographic FP64
 // field is one contiguous block of X*Y*Z*24 doubles, read with coalesced
 // 16-byte loads and summed in FP64 in a fixed tree (bitwise reproducible).
+#include <algorithm>
+
 #include "sq_internal.h"
 
 namespace sq {
@@ -92,13 +94,13 @@ __device__ __forceinline__ void stoch_fetch(double2 (&v)[6], const double2* ea, 
 }
 
 template <bool G5>
-__global__ void __launch_bounds__(256, 4) k_pair_partial(const double2* eta, const double2* X, int n, int T,
-                                                         long long slice2, int nkg, double2* part) {
+__global__ void __launch_bounds__(256, 4) k_pair_partial(const double2* eta, const double2* X, int ni, int nj,
+                                                         int T, long long slice2, int nkg, double2* part) {
   __shared__ double a_r[kStochTile][kStochPitch], a_i[kStochTile][kStochPitch], a_d[kStochTile][kStochPitch];
   __shared__ double b_r[kStochTile][kStochPitch], b_i[kStochTile][kStochPitch], b_s[kStochTile][kStochPitch];
   const int t = blockIdx.x, kg = blockIdx.y;
-  const int ntile = (n + kStochTile - 1) / kStochTile;
-  const int ti = blockIdx.z / ntile, tj = blockIdx.z - ti * ntile;
+  const int ntj = (nj + kStochTile - 1) / kStochTile;
+  const int ti = blockIdx.z / ntj, tj = blockIdx.z - ti * ntj;
   const int li = threadIdx.x / kStochTile, lj = threadIdx.x - li * kStochTile;
   const int i = ti * kStochTile + li, j = tj * kStochTile + lj;
   const long long nchunk = (slice2 + kStochChunk - 1) / kStochChunk;
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(256, 4) k_pair_partial(const double2* eta, con
   const long long stride = (long long)T * slice2;
   const double2* ea = eta + (long long)ti * kStochTile * stride + (long long)t * slice2;
   const double2* xa = X + (long long)tj * kStochTile * stride + (long long)t * slice2;
-  const int ne = min(kStochTile, n - ti * kStochTile), nx = min(kStochTile, n - tj * kStochTile);
+  const int ne = min(kStochTile, ni - ti * kStochTile), nx = min(kStochTile, nj - tj * kStochTile);
   double2 v[6];
   if (c0 < c1) stoch_fetch(v, ea, xa, stride, ne, nx, c0 * kStochChunk);
   for (long long c = c0; c < c1; c++) {
@@ -138,18 +140,19 @@ __global__ void __launch_bounds__(256, 4) k_pair_partial(const double2* eta, con
       P3 = fma(a_d[li][q], b_s[lj][q], P3);
     }
   }
-  if (i < n && j < n) part[(((long long)t * nkg + kg) * n + i) * n + j] = make_double2(P1 + P2, P3 - P1 + P2);
+  if (i < ni && j < nj) part[(((long long)t * nkg + kg) * ni + i) * nj + j] = make_double2(P1 + P2, P3 - P1 + P2);
 }
 
-// O[t][i][j] = sum over K-groups in order
-__global__ void k_stoch_sum(const double2* part, int n, int T, int nkg, double2* O) {
+// O[t][i][j] = sum over K-groups in order (ni x nj pairs per timeslice)
+__global__ void k_stoch_sum(const double2* part, int ni, int nj, int T, int nkg, double2* O) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = (long long)T * n * n;
+  const long long nn = (long long)ni * nj;
+  const long long total = (long long)T * nn;
   if (idx >= total) return;
-  const long long t = idx / ((long long)n * n), ij = idx - t * n * n;
+  const long long t = idx / nn, ij = idx - t * nn;
   double re = 0, im = 0;
   for (int kg = 0; kg < nkg; kg++) {
-    const double2 v = part[(t * nkg + kg) * n * n + ij];
+    const double2 v = part[(t * nkg + kg) * nn + ij];
     re += v.x;
     im += v.y;
   }
@@ -311,37 +314,41 @@ __global__ void __launch_bounds__(256) k_prop_trace(const double2* P, const doub
 }
 
 // K-groups per timeslice: about four CTAs per SM in one wave
-int stoch_groups(const sq_ctx* c, int n) {
+int stoch_groups(const sq_ctx* c, int n) { return stoch_groups2(c, n, n); }
+
+int stoch_groups2(const sq_ctx* c, int ni, int nj) {
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   const int T = c->dims[3];
-  const int ntile = (n + kStochTile - 1) / kStochTile;
+  const long long nti = (ni + kStochTile - 1) / kStochTile, ntj = (nj + kStochTile - 1) / kStochTile;
   const long long slice2 = (long long)c->dims[0] * c->dims[1] * c->dims[2] * 12;
   const long long nchunk = (slice2 + kStochChunk - 1) / kStochChunk;
-  long long g = 4LL * sms / ((long long)T * ntile * ntile);
+  long long g = 4LL * sms / ((long long)T * nti * ntj);
   if (g < 1) g = 1;
   if (g > nchunk) g = nchunk;
   return (int)g;
 }
 
-// out[t][k][l] = sum over timeslice t of F_k^+ (gamma5) G_l
-static void launch_pairs(const sq_ctx* c, bool g5, const double* F, const double* G, int n, double* out, double* part,
-                         int nkg, cudaStream_t s) {
+// out[t][k][l] = sum over timeslice t of F_k^+ (gamma5) G_l, k < ni, l < nj
+static void launch_pairs(const sq_ctx* c, bool g5, const double* F, const double* G, int ni, int nj, double* out,
+                         double* part, int nkg, cudaStream_t s) {
   const int T = c->dims[3];
   const long long slice2 = (long long)c->dims[0] * c->dims[1] * c->dims[2] * 12;
-  const int ntile = (n + kStochTile - 1) / kStochTile;
-  const dim3 grid(T, nkg, ntile * ntile);
+  const int nti = (ni + kStochTile - 1) / kStochTile, ntj = (nj + kStochTile - 1) / kStochTile;
+  const dim3 grid(T, nkg, nti * ntj);
   if (g5)
-    k_pair_partial<true><<<grid, 256, 0, s>>>((const double2*)F, (const double2*)G, n, T, slice2, nkg, (double2*)part);
+    k_pair_partial<true><<<grid, 256, 0, s>>>((const double2*)F, (const double2*)G, ni, nj, T, slice2, nkg,
+                                              (double2*)part);
   else
-    k_pair_partial<false><<<grid, 256, 0, s>>>((const double2*)F, (const double2*)G, n, T, slice2, nkg, (double2*)part);
-  const long long total = (long long)T * n * n;
-  k_stoch_sum<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((const double2*)part, n, T, nkg, (double2*)out);
+    k_pair_partial<false><<<grid, 256, 0, s>>>((const double2*)F, (const double2*)G, ni, nj, T, slice2, nkg,
+                                               (double2*)part);
+  const long long total = (long long)T * ni * nj;
+  k_stoch_sum<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((const double2*)part, ni, nj, T, nkg, (double2*)out);
 }
 
 void launch_stoch_op(const sq_ctx* c, const double* eta, const double* X, int n, double* O, double* C, double* part,
                      int nkg, cudaStream_t s) {
-  launch_pairs(c, true, eta, X, n, O, part, nkg, s);
+  launch_pairs(c, true, eta, X, n, n, O, part, nkg, s);
   if (C) launch_stoch_corr(c, O, n, C, part, s);
 }
 
@@ -355,9 +362,163 @@ void launch_stoch_corr(const sq_ctx* c, const double* O, int n, double* C, doubl
 void launch_prop_trace(const sq_ctx* c, const double* etaA, const double* XA, const double* etaB, const double* XB,
                        int n, double* P, double* Q, double* C, double* part, int nkg, cudaStream_t s) {
   const int T = c->dims[3];
-  launch_pairs(c, false, XB, XA, n, P, part, nkg, s);     // P_ji(t) = sum_z XB_j^+ XA_i
-  launch_pairs(c, false, etaA, etaB, n, Q, part, nkg, s);  // Q_ij(t0) = sum_x etaA_i^+ etaB_j
+  launch_pairs(c, false, XB, XA, n, n, P, part, nkg, s);     // P_ji(t) = sum_z XB_j^+ XA_i
+  launch_pairs(c, false, etaA, etaB, n, n, Q, part, nkg, s);  // Q_ij(t0) = sum_x etaA_i^+ etaB_j
   k_prop_trace<<<T * T, 256, 0, s>>>((const double2*)P, (const double2*)Q, n, T, (double2*)C);
+}
+
+// ---------------------------------------------------------------------------
+// Diagram contractions of the two-pion correlation function at zero momentum
+// (Sec. "Stochastic propagators": Diagram 0; Sec. "Correlation function":
+// Diagrams 1-3), per gauge configuration. With the twelve point solutions
+// Xp[a] = M^{-1} e_a (unit source at the origin) and two sets of noise
+// sources / solutions (A for every S, B for every S^+ of Eq. Sfill):
+//   P(t)   = sum_a sum_{y in t} |Xp[a](y)|^2            (k_pion, summed over a)
+//   Q0(t)  = Ctr[0][t],  Qtt(t) = Ctr[t][t]             (k_prop_trace)
+//   C0(t)  = P(t) Q0(t),  C1(t) = Qtt(t) P(0)
+//   C2(t)  = (1/n^2) sum_ij Q_ij(t) W_ji(t),  W_ji(t) = sum_a conj(GB(t)_aj) GA(0)_ai
+//            with Q_ij(t) = sum_{z in t} etaA_i^+ etaB_j and the Gram matrices
+//            G(t)_ai = sum_{y in t} Xp[a]^+ X_i of the point and noise solutions
+//   C3(t)  = conj C2(t)
+// ---------------------------------------------------------------------------
+
+// one CTA per sink timeslice t; fixed-order tree (bitwise reproducible)
+__global__ void __launch_bounds__(256) k_diag_c2(const double2* Q, const double2* GA, const double2* GB, int n,
+                                                 double2* C2) {
+  const int t = blockIdx.x;
+  const long long nn = (long long)n * n;
+  const double2* q = Q + t * nn;
+  const double2* ga = GA;                    // timeslice 0: [a][i]
+  const double2* gb = GB + (long long)t * 12 * n;  // timeslice t: [a][j]
+  double re = 0, im = 0;
+  for (long long ij = threadIdx.x; ij < nn; ij += blockDim.x) {
+    const int i = (int)(ij / n), j = (int)(ij - (long long)i * n);
+    double wr = 0, wi = 0;  // W_ji = sum_a conj(gb[a][j]) ga[a][i]
+#pragma unroll
+    for (int a = 0; a < 12; a++) {
+      const double2 x = gb[(long long)a * n + j], y = ga[(long long)a * n + i];
+      wr = fma(x.x, y.x, wr);
+      wr = fma(x.y, y.y, wr);
+      wi = fma(x.x, y.y, wi);
+      wi = fma(-x.y, y.x, wi);
+    }
+    const double2 v = q[ij];
+    re = fma(v.x, wr, re);
+    re = fma(-v.y, wi, re);
+    im = fma(v.x, wi, im);
+    im = fma(v.y, wr, im);
+  }
+  __shared__ double sr[8], si[8];
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if ((threadIdx.x & 31) == 0) {
+    sr[threadIdx.x >> 5] = re;
+    si[threadIdx.x >> 5] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      a += sr[w];
+      b += si[w];
+    }
+    const double f = 1.0 / ((double)n * n);
+    C2[t] = make_double2(a * f, b * f);
+  }
+}
+
+// out[q][t], q = P, Q0, Qtt, C0, C1, C2, C3 (complex; P real)
+__global__ void k_diag_final(const double* Cp, const double2* Ctr, const double2* C2, int T, double2* out) {
+  const int t = threadIdx.x;
+  if (t >= T) return;
+  double P = 0, P0 = 0;
+  for (int a = 0; a < 12; a++) {
+    P += Cp[(long long)a * T + t];
+    P0 += Cp[(long long)a * T];
+  }
+  const double2 q0 = Ctr[t], qtt = Ctr[(long long)t * T + t], c2 = C2[t];
+  out[0 * T + t] = make_double2(P, 0.0);
+  out[1 * T + t] = q0;
+  out[2 * T + t] = qtt;
+  out[3 * T + t] = make_double2(P * q0.x, P * q0.y);
+  out[4 * T + t] = make_double2(qtt.x * P0, qtt.y * P0);
+  out[5 * T + t] = c2;
+  out[6 * T + t] = make_double2(c2.x, -c2.y);
+}
+
+size_t diagram_scratch_bytes(const sq_ctx* c, int n) {
+  const size_t T = c->dims[3];
+  const size_t nkg = stoch_groups(c, n), nkg2 = stoch_groups2(c, 12, n);
+  const size_t part = std::max(nkg * T * n * n, nkg2 * T * 12 * n) * 16;
+  return part + 2 * T * n * n * 16 + 2 * T * 12 * n * 16 + 12 * T * 8 + T * T * 16 + T * 16 + 8 * 256;
+}
+
+void launch_diagrams(const sq_ctx* c, const double* Xp, const double* etaA, const double* XA, const double* etaB,
+                     const double* XB, int n, double* out, void* scratch, cudaStream_t s) {
+  const int T = c->dims[3];
+  const int nkg = stoch_groups(c, n), nkg2 = stoch_groups2(c, 12, n);
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  char* b = (char*)scratch;
+  double* part = (double*)b;
+  b += al(std::max((size_t)nkg * T * n * n, (size_t)nkg2 * T * 12 * n) * 16);
+  double* P = (double*)b;
+  b += al((size_t)T * n * n * 16);
+  double* Q = (double*)b;
+  b += al((size_t)T * n * n * 16);
+  double* GA = (double*)b;
+  b += al((size_t)T * 12 * n * 16);
+  double* GB = (double*)b;
+  b += al((size_t)T * 12 * n * 16);
+  double* Cp = (double*)b;
+  b += al((size_t)12 * T * 8);
+  double* Ctr = (double*)b;
+  b += al((size_t)T * T * 16);
+  double* C2 = (double*)b;
+  launch_pion(c, Xp, 12, nullptr, Cp, s);
+  launch_prop_trace(c, etaA, XA, etaB, XB, n, P, Q, Ctr, part, nkg, s);
+  launch_pairs(c, false, Xp, XA, 12, n, GA, part, nkg2, s);  // GA(t)_ai = sum Xp_a^+ XA_i
+  launch_pairs(c, false, Xp, XB, 12, n, GB, part, nkg2, s);  // GB(t)_aj = sum Xp_a^+ XB_j
+  k_diag_c2<<<T, 256, 0, s>>>((const double2*)Q, (const double2*)GA, (const double2*)GB, n, (double2*)C2);
+  k_diag_final<<<1, ((T + 31) / 32) * 32, 0, s>>>(Cp, (const double2*)Ctr, (const double2*)C2, T, (double2*)out);
+}
+
+// Vacuum-subtracted averages over configurations (the paper's ensemble
+// average, Sec. "Correlation function"): from records rec[cfg][q][t]
+// (q as k_diag_final writes them) out[r][t], r = C0 - <P><Q0>,
+// <(Qtt - <Qtt>)(P(0) - <P(0)>)>, <C2>, <C3>, C = C0 + C1 - C2 - C3.
+// One thread per t; the configurations are summed in order.
+__global__ void k_diag_ensemble(const double2* rec, int ncfg, int T, double2* out) {
+  const int t = threadIdx.x;
+  if (t >= T) return;
+  double2 m[7], p0 = make_double2(0, 0);
+  for (int q = 0; q < 7; q++) m[q] = make_double2(0, 0);
+  for (int k = 0; k < ncfg; k++) {
+    for (int q = 0; q < 7; q++) {
+      const double2 v = rec[((long long)k * 7 + q) * T + t];
+      m[q].x += v.x;
+      m[q].y += v.y;
+    }
+    const double2 v0 = rec[(long long)k * 7 * T];  // P(0)
+    p0.x += v0.x;
+    p0.y += v0.y;
+  }
+  const double f = 1.0 / ncfg;
+  for (int q = 0; q < 7; q++) m[q] = make_double2(m[q].x * f, m[q].y * f);
+  p0 = make_double2(p0.x * f, p0.y * f);
+  // complex products <P><Q0>, <Qtt><P(0)>
+  const double2 pq = make_double2(m[0].x * m[1].x - m[0].y * m[1].y, m[0].x * m[1].y + m[0].y * m[1].x);
+  const double2 qp = make_double2(m[2].x * p0.x - m[2].y * p0.y, m[2].x * p0.y + m[2].y * p0.x);
+  const double2 c0 = make_double2(m[3].x - pq.x, m[3].y - pq.y);
+  const double2 c1 = make_double2(m[4].x - qp.x, m[4].y - qp.y);
+  out[0 * T + t] = c0;
+  out[1 * T + t] = c1;
+  out[2 * T + t] = m[5];
+  out[3 * T + t] = m[6];
+  out[4 * T + t] = make_double2(c0.x + c1.x - m[5].x - m[6].x, c0.y + c1.y - m[5].y - m[6].y);
+}
+
+void launch_diag_ensemble(const double* rec, int ncfg, int T, double* out, cudaStream_t s) {
+  k_diag_ensemble<<<1, ((T + 31) / 32) * 32, 0, s>>>((const double2*)rec, ncfg, T, (double2*)out);
 }
 
 }  // namespace sq

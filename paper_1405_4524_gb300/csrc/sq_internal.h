@@ -230,6 +230,7 @@ void launch_dilute(const sq_ctx* c, const double* noise, int n_noise, int scheme
 // ---- contraction (sq_contract.cu)
 void launch_pion(const sq_ctx* c, const double* lex, int n, const int* tsl, double* C, cudaStream_t s);
 int stoch_groups(const sq_ctx* c, int n);
+int stoch_groups2(const sq_ctx* c, int ni, int nj);  // rectangular ni x nj pairs
 void launch_stoch_op(const sq_ctx* c, const double* eta, const double* X, int n, double* O, double* C, double* part,
                      int nkg, cudaStream_t s);
 // Tensor-core stochastic operators (sq_stoch_tc.cu): tile counts and the
@@ -246,5 +247,10 @@ void launch_stoch_corr(const sq_ctx* c, const double* O, int n, double* C, doubl
 size_t corr_scratch_bytes(const sq_ctx* c, int n);
 void launch_prop_trace(const sq_ctx* c, const double* etaA, const double* XA, const double* etaB, const double* XB,
                        int n, double* P, double* Q, double* C, double* part, int nkg, cudaStream_t s);
+// diagram contractions (sq_contract.cu): scratch bytes and the launches
+size_t diagram_scratch_bytes(const sq_ctx* c, int n);
+void launch_diagrams(const sq_ctx* c, const double* Xp, const double* etaA, const double* XA, const double* etaB,
+                     const double* XB, int n, double* out, void* scratch, cudaStream_t s);
+void launch_diag_ensemble(const double* rec, int ncfg, int T, double* out, cudaStream_t s);
 
 }  // namespace sq

@@ -103,6 +103,8 @@ _SIG = {
     "sq_contract_prop_trace": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _vp, _i]),
     "sq_contract_stoch_op_z4": (_i, [_vp, _vp, _vp, _i, _vp, _vp, _i]),
     "sq_dilute": (_i, [_vp, _vp, _i, _i, _vp, _i]),
+    "sq_contract_diagrams": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, _i, _vp, _i]),
+    "sq_diagrams_ensemble": (_i, [_vp, _vp, _i, _vp, _i]),
     "sq_get_profile": (_i, [_vp, C.POINTER(sq_kernel_stat), _i, C.POINTER(_i)]),
     "sq_kernel_launches": (_i, [_vp, C.POINTER(C.c_longlong)]),
     "sq_set_dslash_shape": (_i, [_vp, _i, _i, _i, C.POINTER(_i)]),
@@ -452,6 +454,46 @@ def sq_contract_prop_trace(ctx, etaA, XA, n_rhs: int, etaB=None, XB=None, C=None
     _check(ctx, _lib.sq_contract_prop_trace(ctx, _ptr(etaA), _ptr(XA), _ptr(etaB), _ptr(XB), int(n_rhs),
                                             _ptr(C), where))
     return C
+
+
+DIAGRAM_NAMES = ("P", "Q0", "Qtt", "C0", "C1", "C2", "C3")
+ENSEMBLE_NAMES = ("C0", "C1", "C2", "C3", "C")
+
+
+def sq_contract_diagrams(ctx, Xp, etaA, XA, n_rhs: int, etaB=None, XB=None, out=None):
+    """Per-configuration diagram quantities (DIAGRAM_NAMES) at every sink
+    timeslice: complex (7, T), a numpy array for host inputs or the given /
+    a new torch tensor for device inputs."""
+    where = _where(XA)
+    T = int(np.shape(XA)[1]) if where == SQ_HOST else int(XA.shape[1])
+    if out is None:
+        if where == SQ_HOST:
+            out = np.zeros((7, T), dtype=np.complex128)
+        else:
+            import torch
+
+            out = torch.zeros((7, T), dtype=torch.complex128, device=XA.device)
+    if (etaB is None) != (XB is None):
+        raise ValueError("etaB and XB go together")
+    _check(ctx, _lib.sq_contract_diagrams(ctx, _ptr(Xp), _ptr(etaA), _ptr(XA), _ptr(etaB), _ptr(XB),
+                                          int(n_rhs), _ptr(out), where))
+    return out
+
+
+def sq_diagrams_ensemble(ctx, rec, out=None):
+    """Vacuum-subtracted ensemble averages (ENSEMBLE_NAMES) from records
+    (n_cfg, 7, T) of sq_contract_diagrams; complex (5, T)."""
+    where = _where(rec)
+    n_cfg, _, T = (int(v) for v in rec.shape)
+    if out is None:
+        if where == SQ_HOST:
+            out = np.zeros((5, T), dtype=np.complex128)
+        else:
+            import torch
+
+            out = torch.zeros((5, T), dtype=torch.complex128, device=rec.device)
+    _check(ctx, _lib.sq_diagrams_ensemble(ctx, _ptr(rec), n_cfg, _ptr(out), where))
+    return out
 
 
 def sq_get_profile(ctx):
