@@ -51,8 +51,8 @@ def parse():
     p.add_argument("--extras", type=int, default=1, help="FP64/FP16 comparison solves")
     p.add_argument("--e2e", type=int, default=1, help="end-to-end host-buffer measurement")
     p.add_argument("--cpu", type=int, default=1, help="CPU oracle baseline")
-    p.add_argument("--workloads", type=int, default=0,
-                   help="also time the 24^3x48, 32^3x64 and batch workloads (minutes)")
+    p.add_argument("--workloads", type=int, default=1,
+                   help="also time the 24^3x48, 32^3x64 and batch workloads and their dslash rooflines")
     return p.parse_args()
 
 
@@ -184,44 +184,169 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(workload, seconds_budget=12.0):
-    """The FP64 oracle as it stands, on one source of the same workload: time
-    whole BiCGStab iterations for about `seconds_budget` seconds and scale by
-    the iteration count the oracle needs for 1e-10 (tests/golden)."""
+_ORACLE_CACHE = {}
+
+
+def _oracle_sample(workload, seconds_budget, k=0):
+    """Seconds per BiCGStab iteration of the FP64 oracle as it stands on
+    source k of the workload, from about `seconds_budget` seconds of whole
+    iterations; returns (seconds per iteration, iterations timed, seconds).
+    The links and their field strength are built once per process."""
     import oracle
     from paper_1405_4524_gb300 import inputs
 
-    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")))[workload]
-    spec, U, eta = inputs.workload(workload, n_rhs=1)
-    F = oracle.field_strength(U)
+    if workload not in _ORACLE_CACHE:
+        spec = dict(inputs.WORKLOADS[workload])
+        U = inputs.make_links(spec["dims"], spec["eps"], spec["link_seed"])
+        _ORACLE_CACHE[workload] = (spec, U, oracle.field_strength(U))
+    spec, U, F = _ORACLE_CACHE[workload]
+    T = spec["dims"][3]
+    # source k of the workload (source k draws from seed + k)
+    eta = inputs.make_z4(spec["dims"], 1, spec["src_seed"] + k, [k % T] if spec["diluted"] else None)[0]
     apply = lambda v: oracle.apply_M(U, F, v, spec["kappa"], spec["csw"], -1.0)
     t0 = time.perf_counter()
-    apply(eta[0])
+    apply(eta)
     t_apply = time.perf_counter() - t0
     # bicgstab(maxiter=m) costs 2m operator applications plus one for the
     # initial and one for the final residual: m + 1 iteration equivalents
     m = int(max(1, min(40, seconds_budget / (2.0 * t_apply) - 1)))
     t0 = time.perf_counter()
-    oracle.bicgstab(apply, eta[0], tol=1e-300, maxiter=m)
+    oracle.bicgstab(apply, eta, tol=1e-300, maxiter=m)
     el = time.perf_counter() - t0
-    per_it = el / (m + 1)
-    it = m
-    value = 1.0 / (per_it * gold["iterations"])
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"1 source of {workload}: {it} oracle BiCGStab iterations ({el:.1f} s, "
-                       f"counted as {it + 1} with the initial and final residual), scaled to the "
-                       f"{gold['iterations']} iterations the oracle needs for 1e-10 "
-                       f"(tests/golden/oracle_iterations.json)")}
+    return el / (m + 1), m, el
+
+
+def _oracle_worker(job):
+    workload, budget, k = job
+    return _oracle_sample(workload, budget, k)
+
+
+class OraclePool:
+    """One oracle process per host core (spawned, so none is forked from a
+    process that has used the GPU). Each runs the oracle on its own source of
+    the workload, sources k = 0 .. n-1 dealt round-robin to the cores."""
+
+    def __init__(self):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+
+        self.cores = os.cpu_count() or 1
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(v, "1")
+        self.ex = cf.ProcessPoolExecutor(max_workers=self.cores, mp_context=mp.get_context("spawn"))
+
+    def sample(self, workload, n_src, budget):
+        """Sources/s of the oracle over all cores: one source of the workload
+        per core (sources 0 .. min(n_src, cores) - 1, a bounded sample of the
+        n_src-source workload), each its measured seconds per iteration times
+        the iterations the oracle needs for 1e-10
+        (tests/golden/oracle_iterations.json); the cores run concurrently.
+        Returns (sources/s, wall seconds, sources timed, iterations)."""
+        gold = json.load(open(os.path.join(ROOT, "tests", "golden", "oracle_iterations.json")))[workload]
+        m = min(n_src, self.cores)
+        t0 = time.perf_counter()
+        res = list(self.ex.map(_oracle_worker, [(workload, budget, k) for k in range(m)]))
+        wall = time.perf_counter() - t0
+        return sum(1.0 / (per_it * gold["iterations"]) for per_it, _, _ in res), wall, m, gold["iterations"]
+
+    def close(self):
+        self.ex.shutdown()
+
+
+def cpu_baseline(workload, n_src, seconds_budget=10.0):
+    """The FP64 oracle as it stands on the host cores: all cores, one source
+    per core (the reported value); one core; and one full, non-extrapolated
+    oracle solve of the small 4^3 x 8 workload (4 sources to 1e-12)."""
+    import oracle
+    from paper_1405_4524_gb300 import inputs
+
+    pool = OraclePool()
+    try:
+        value, wall, m_src, iters = pool.sample(workload, n_src, seconds_budget)
+    finally:
+        pool.close()
+    per_it, m, el = _oracle_sample(workload, seconds_budget, 0)
+    spec, U, eta = inputs.workload("4x4x4x8")
+    F = oracle.field_strength(U)
+    t0 = time.perf_counter()
+    for k in range(spec["n_rhs"]):
+        oracle.solve(U, eta[k], spec["kappa"], spec["csw"], -1.0, tol=1e-12, F=F)
+    full = time.perf_counter() - t0
+    cpu = ""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                cpu = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle",
+            "sample": (f"{m_src} of the {n_src} sources of {workload}, one oracle process per host core "
+                       f"({pool.cores} cores, {cpu or 'cpu model unknown'}): each times whole BiCGStab "
+                       f"iterations of its own source for about {seconds_budget:.0f} s, scaled to the {iters} "
+                       f"iterations the oracle needs for 1e-10 (tests/golden/oracle_iterations.json); "
+                       f"{wall:.1f} s wall"),
+            "one_core": {"value": 1.0 / (per_it * iters), "unit": UNIT, "cores": 1,
+                         "sample": f"1 source, {m} iterations in {el:.1f} s, scaled to {iters}"},
+            "full_solve_4x4x4x8": {"value": spec["n_rhs"] / full, "unit": UNIT, "cores": 1,
+                                   "sample": f"4 sources of 4x4x4x8 solved to 1e-12 by the oracle, {full:.2f} s "
+                                             f"(measured, not extrapolated)"}}
+
+
+def dslash_roofline(sq, ctx, dims, prec, n, reps=10):
+    """The clover dslash (hop + A^-1) on n sources of precision prec at the
+    autotuned shape, timed alone with CUDA events on the caller's stream
+    (the library orders its own stream between them). Algorithmic bytes per
+    launch: links and clover blocks once, every source's input and output
+    spinor once (FP32 96 + 96 B, FP16 52 + 52 B per site and source)."""
+    import torch
+
+    X, Y, Z, T = dims
+    fb = sq.sq_field_bytes(ctx, prec, n)
+    bi = torch.zeros(fb, dtype=torch.uint8, device="cuda")
+    bo = torch.zeros(fb, dtype=torch.uint8, device="cuda")
+    g = torch.Generator(device="cuda").manual_seed(5)
+    psi = torch.randn((n, T, Z, Y, X, 4, 3), dtype=torch.complex128, device="cuda", generator=g)
+    sq.sq_pack_spinor(ctx, bi, psi, 1, prec, n)
+    del psi
+    flags = sq.SQ_DS_CLOVER_INV
+    sq.sq_dslash_eo(ctx, bo, bi, None, 0, prec, n, flags | sq.SQ_DS_SYNC, 0.0)  # tunes the shape
+    kind, shape = sq.sq_get_dslash_shape(ctx, prec, n)
+    for _ in range(3):
+        sq.sq_dslash_eo(ctx, bo, bi, None, 0, prec, n, flags, 0.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        sq.sq_dslash_eo(ctx, bo, bi, None, 0, prec, n, flags, 0.0)
+    e1.record()
+    torch.cuda.synchronize()
+    us = 1000.0 * e0.elapsed_time(e1) / reps
+    vh = X * Y * Z * T // 2
+    per_src = 192 if prec == sq.SQ_F32 else 104
+    bytes_ = vh * (8 * 48 + 288 + n * per_src)
+    hbm, how = peaks()
+    gbs = bytes_ / (us * 1e-6) / 1e9
+    del bi, bo
+    return {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
+            "traffic": None, "kernel": f"dslash_clover ({'f32' if prec == sq.SQ_F32 else 'f16'}, recon-12, "
+                                       f"{n} sources, {'tiled' if kind == 1 else 'per-site'} shape {list(shape)})",
+            "bytes_per_launch": bytes_, "us_per_launch": round(us, 2),
+            "peak_kind": f"{how} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
 
 
 def other_workloads(sq):
-    """Sources/s of the larger workloads (one timed solve each after a
-    warm-up solve), device-resident inputs, tol 1e-10."""
+    """The large workloads, device-resident inputs, tol 1e-10: one timed
+    solve each after a warm-up solve (24^3 x 48, 64 time-diluted sources,
+    FP16 inner; 32^3 x 64, 24 sources, FP16 defect correction), the clover
+    dslash timed alone at both sizes (FP16, and FP32 at 32^3 x 64), and the
+    96-source batch over two lattices and three kappas."""
     import torch
 
     from paper_1405_4524_gb300 import inputs
 
     out = {}
+    links = {}
 
     def timed_solve(fn):
         fn()
@@ -234,37 +359,32 @@ def other_workloads(sq):
     for name, prm in [("24x24x24x48", sq.sq_default_params(inner_prec=sq.SQ_F16)),
                       ("32x32x32x64", sq.sq_default_params(inner_prec=sq.SQ_F16, outer=sq.SQ_OUTER_DEFECT))]:
         spec, U, eta = inputs.workload(name)
+        links[name] = U
         ctx = sq.sq_create(spec["dims"], -1)
         sq.sq_load_gauge(ctx, U, 12)
         e = torch.from_numpy(eta).cuda()
+        del eta
         x = torch.zeros_like(e)
         dt, (_, st) = timed_solve(lambda: sq.sq_solve(ctx, spec["kappa"], spec["csw"], e, x, spec["n_rhs"], TOL, prm))
         out[name] = {"sources_per_s": round(spec["n_rhs"] / dt, 2), "n_sources": spec["n_rhs"],
                      "iterations": int(np.mean([s["iterations"] for s in st])),
                      "max_true_residual": max(s["true_residual"] for s in st),
                      "solver": "FP16 inner, " + ("defect correction" if prm.outer else "reliable updates")}
-        # the FP16 clover dslash at this size: one more solve with events
-        # around its launches (algorithmic bytes: links, clover once; every
-        # active source's spinor in and out once)
-        prm_p = sq.sq_solve_params.from_buffer_copy(prm)
-        prm_p.profile = 2
-        sq.sq_solve(ctx, spec["kappa"], spec["csw"], e, x, spec["n_rhs"], TOL, prm_p)
-        row = [r for r in sq.sq_get_profile(ctx) if r["name"] == "dslash_clover"]
-        if row and row[0]["ms"] > 0:
-            hbm, how = peaks()
-            gbs = sum(r["bytes"] for r in row) / (sum(r["ms"] for r in row) / 1000.0) / 1e9
-            out[name]["dslash_f16"] = {"us_per_launch": round(1000.0 * sum(r["ms"] for r in row) /
-                                                              max(1, sum(r["launches"] for r in row)), 2),
-                                       "GB/s": round(gbs, 1), "frac": round(gbs / hbm, 4),
-                                       "peak": hbm, "peak_kind": how}
         del e, x
+        sq.sq_build_clover(ctx, spec["kappa"], spec["csw"])
+        out[name]["roofline_dslash_f16"] = dslash_roofline(sq, ctx, spec["dims"], sq.SQ_F16, spec["n_rhs"])
+        if name == "32x32x32x64":
+            out[name]["roofline_dslash_f32"] = dslash_roofline(sq, ctx, spec["dims"], sq.SQ_F32, spec["n_rhs"])
         sq.sq_destroy(ctx)
     # 96 sources: 16^3x32 and 24^3x48 at kappa 0.118, 0.121, 0.124 in one batch
     ctxs, probs, bufs = [], [], []
     for gi, name in enumerate(["16x16x16x32", "24x24x24x48"]):
         spec = inputs.WORKLOADS[name]
         ctx = sq.sq_create(spec["dims"], -1)
-        sq.sq_load_gauge(ctx, inputs.make_links(spec["dims"], spec["eps"], spec["link_seed"]), 12)
+        U = links.get(name)
+        if U is None:
+            U = inputs.make_links(spec["dims"], spec["eps"], spec["link_seed"])
+        sq.sq_load_gauge(ctx, U, 12)
         ctxs.append(ctx)
         for ki, kappa in enumerate([0.118, 0.121, 0.124]):
             e = torch.from_numpy(inputs.make_z4(spec["dims"], 16, 3000 + 10 * gi + ki)).cuda()
@@ -285,26 +405,37 @@ def other_workloads(sq):
 def reference_arm(args, rank, world):
     if rank != 0:
         return
+    from paper_1405_4524_gb300 import inputs
+
     steps, warm = args.steps, args.warmup
-    budget = max(2.0, 150.0 / max(1, steps + warm))
-    for _ in range(warm):
-        cpu_baseline(args.workload, seconds_budget=budget / 2)
-    vals = []
-    t0 = time.perf_counter()
-    last = None
-    for _ in range(steps):
-        last = cpu_baseline(args.workload, seconds_budget=budget)
-        vals.append(last["value"])
-    wall = time.perf_counter() - t0
+    n_src = inputs.WORKLOADS[args.workload]["n_rhs"]
+    budget = max(1.0, 120.0 / max(1, steps + warm))
+    pool = OraclePool()
+    try:
+        for _ in range(warm):
+            pool.sample(args.workload, n_src, budget / 2)
+        vals, walls = [], []
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            v, w, m_src, iters = pool.sample(args.workload, n_src, budget)
+            vals.append(v)
+            walls.append(w)
+        wall = time.perf_counter() - t0
+    finally:
+        pool.close()
     value = statistics.median(vals)
+    sample = (f"{m_src} of the {n_src} sources of {args.workload}, one oracle process per host core "
+              f"({pool.cores} cores): each step times whole BiCGStab iterations of each core's source for "
+              f"about {budget:.1f} s, scaled to the {iters} iterations the oracle needs for 1e-10")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
-            "warmup": warm, "ms_per_step": 1000.0 / value, "higher_is_better": True,
+            "warmup": warm, "ms_per_step": 1000.0 * statistics.mean(walls), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": args.workload, "n_sources": 1, "tol": TOL,
+            "config": {"workload": args.workload, "n_sources": n_src, "tol": TOL,
                        "solver": "oracle: unpreconditioned FP64 BiCGStab (numpy)"},
-            "cpu_baseline": dict(last, value=value),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "ms_per_source": 1000.0 / value,
             "wall_s": wall}
     print(json.dumps(line), flush=True)
 
@@ -612,6 +743,38 @@ def main():
                                    "max_true_residual": max(x["true_residual"] for x in st_d)}
         sq.sq_destroy(ctx_d)
         del noise_d, src_d, sol_d
+        # the four diagrams at zero momentum (Sec. "Stochastic propagators",
+        # Sec. "Correlation function") on the bench lattice: the twelve
+        # point solutions of the origin, set A = the bench's own 16 sources
+        # and solutions, set B = 16 more sources; FP64-pipe bound (Gram
+        # matrices of the two sets, of the point and noise solutions)
+        one = torch.zeros((1,) + tuple(eta_dev.shape[1:]), dtype=torch.complex128, device="cuda")
+        one[0, 0, 0, 0, 0] = 1.0
+        src_p = sq.sq_dilute(ctx, one, 1, sq.SQ_DILUTE_SPIN_COLOUR)
+        Xp = torch.zeros_like(src_p)
+        sq.sq_solve(ctx, kappa, csw, src_p, Xp, 12, TOL, sq.sq_default_params(inner_prec=inner))
+        eB = torch.from_numpy(inputs.make_z4(dims, n, spec["src_seed"] + 500000)).cuda()
+        xB = torch.zeros_like(eB)
+        sq.sq_solve(ctx, kappa, csw, eB, xB, n, TOL, sq.sq_default_params(inner_prec=inner))
+        Dg = sq.sq_contract_diagrams(ctx, Xp, eta_dev, sol_dev, n, eB, xB)
+        e0.record(stream)
+        for _ in range(reps):
+            sq.sq_contract_diagrams(ctx, Xp, eta_dev, sol_dev, n, eB, xB, out=Dg)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_dg = e0.elapsed_time(e1) / reps
+        vol = float(np.prod(dims)) * 12
+        terms_dg = 2.0 * n * n * vol + 2.0 * 12 * n * vol  # complex terms of the Gram matrices
+        tflops = 6.0 * terms_dg / (ms_dg / 1000.0) / 1e12
+        extras["diagrams"] = {"bound": "alu", "achieved": round(tflops, 3), "peak": FP64_PEAK_TFLOPS,
+                              "unit": "TFLOP/s", "frac": round(tflops / FP64_PEAK_TFLOPS, 4),
+                              "ms_per_call": round(ms_dg, 3),
+                              "workload": f"{WORKLOAD}: 12 point solutions, two sets of {n} Z4 sources",
+                              "C0_plus_C1_minus_C2_minus_C3_at_t1": float((Dg[3, 1] + Dg[4, 1] - Dg[5, 1]
+                                                                            - Dg[6, 1]).real),
+                              "note": "device I/O; P, Q0, Qtt, C0..C3 per sink timeslice; 3 FP64 FMAs per "
+                                      "complex term of the Gram matrices (noise-noise and point-noise)"}
+        del one, src_p, Xp, eB, xB, Dg
 
     if args.workloads and rank == 0:
         extras["workloads"] = other_workloads(sq)
@@ -641,7 +804,7 @@ def main():
         "extras": extras,
     }
     if rank == 0 and world == 1 and args.cpu:
-        line["cpu_baseline"] = cpu_baseline(args.workload)
+        line["cpu_baseline"] = cpu_baseline(args.workload, n)
     sq.sq_destroy(ctx)
     if rank == 0:
         print(json.dumps(line), flush=True)
