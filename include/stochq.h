@@ -85,7 +85,10 @@ enum { SQ_HOST = 0, SQ_DEVICE = 1 };
 enum {
   SQ_DS_CLOVER_INV = 1, /* apply A_pp^{-1} after the hopping term */
   SQ_DS_XPAY = 2,       /* out = x + a * (...) instead of out = (...) */
-  SQ_DS_SYNC = 4        /* wait for the result before returning */
+  SQ_DS_SYNC = 4,       /* wait for the result before returning */
+  SQ_DS_F64_EMULATED = 8 /* SQ_F64 fields: FP64-accurate double-FP32 arithmetic
+                            on the FP32 pipe (the solver's FP64 steps; about
+                            46 correct bits) instead of FP64 instructions */
 };
 
 /* sq_solve_params.outer */

@@ -103,6 +103,8 @@ static void free_clover(sq_ctx* c, CloverSet& cs) {
   dev_free(c->mem, cs.A64, 2 * 36 * Vh * sizeof(double2));
   dev_free(c->mem, cs.Ainv64, 2 * 36 * Vh * sizeof(double2));
   dev_free(c->mem, cs.Ainv32, 2 * 18 * Vh * sizeof(float4));
+  dev_free(c->mem, cs.Adf, 2 * 36 * Vh * sizeof(float4));
+  dev_free(c->mem, cs.Ainvdf, 2 * 36 * Vh * sizeof(float4));
   cs = CloverSet();
 }
 
@@ -136,11 +138,19 @@ sq_status find_clover(sq_ctx* c, double kappa, double csw, CloverSet** out) {
   if (!cs.A64) e = dev_alloc(c->mem, (void**)&cs.A64, 2 * 36 * Vh * sizeof(double2));
   if (e == cudaSuccess && !cs.Ainv64) e = dev_alloc(c->mem, (void**)&cs.Ainv64, 2 * 36 * Vh * sizeof(double2));
   if (e == cudaSuccess && !cs.Ainv32) e = dev_alloc(c->mem, (void**)&cs.Ainv32, 2 * 18 * Vh * sizeof(float4));
+  if (e == cudaSuccess && !cs.Adf) e = dev_alloc(c->mem, (void**)&cs.Adf, 2 * 36 * Vh * sizeof(float4));
+  if (e == cudaSuccess && !cs.Ainvdf) e = dev_alloc(c->mem, (void**)&cs.Ainvdf, 2 * 36 * Vh * sizeof(float4));
   if (e != cudaSuccess) {
     free_clover(c, cs);
     return cuda_check(c, e, "clover allocation");
   }
   sq_status s = clover_build(c, cs, kappa, csw);
+  if (s == SQ_OK) {  // float-pair copies for the emulated-FP64 operator
+    launch_split_copy(cs.A64, cs.Adf, 2 * 36 * Vh, c->stream);
+    launch_split_copy(cs.Ainv64, cs.Ainvdf, 2 * 36 * Vh, c->stream);
+    c->launches += 2;
+    s = cuda_check(c, cudaGetLastError(), "clover copies");
+  }
   int bits = 0;
   if (s == SQ_OK) s = read_error_word(c, &bits);
   if (s == SQ_OK && (bits & ERRBIT_CLOVER))
@@ -229,7 +239,8 @@ sq_status sq_set_allocator(sq_ctx* c, sq_alloc_fn alloc, sq_free_fn free_fn, voi
   if (!c) return SQ_ERR_ARG;
   if ((!alloc) != (!free_fn)) return set_error(c, SQ_ERR_ARG, "sq_set_allocator: give both callbacks or neither");
   bool held = c->U64 || c->U32 || c->stoch_part || c->ws.base || c->batch;
-  for (auto& cs : c->clover) held = held || cs.A64 || cs.Ainv64 || cs.Ainv32;
+  for (auto& cs : c->clover) held = held || cs.A64 || cs.Ainv64 || cs.Ainv32 || cs.Adf || cs.Ainvdf;
+  held = held || c->Udf;
   if (held) return set_error(c, SQ_ERR_STATE, "sq_set_allocator: the context already holds device buffers");
   c->mem.alloc = alloc;
   c->mem.free = free_fn;
@@ -243,6 +254,7 @@ sq_status sq_destroy(sq_ctx* c) {
   release_workspace(c);
   for (auto& cs : c->clover) free_clover(c, cs);
   dev_free(c->mem, c->U64, 2 * 4 * 9 * (size_t)c->Vh * sizeof(double2));
+  dev_free(c->mem, c->Udf, 2 * 4 * 9 * (size_t)c->Vh * sizeof(float4));
   dev_free(c->mem, c->U32, gauge32_bytes(c, c->recon));
   cudaFree(c->d_err);
   dev_free(c->mem, c->stoch_part, c->stoch_cap);
@@ -271,6 +283,7 @@ sq_status sq_load_gauge(sq_ctx* c, const double* U, int recon, int where) {
   c->recon = recon;
   if (!c->U64) e = dev_alloc(c->mem, (void**)&c->U64, 2 * 4 * 9 * Vh * sizeof(double2));
   if (e == cudaSuccess && !c->U32) e = dev_alloc(c->mem, &c->U32, gauge32_bytes(c, recon));
+  if (e == cudaSuccess && !c->Udf) e = dev_alloc(c->mem, (void**)&c->Udf, 2 * 4 * 9 * Vh * sizeof(float4));
   if (e != cudaSuccess) return cuda_check(c, e, "gauge allocation");
   const size_t nd = (size_t)c->V * 4 * 18;
   const double* dU = U;
@@ -282,7 +295,8 @@ sq_status sq_load_gauge(sq_ctx* c, const double* U, int recon, int where) {
     dU = stage;
   }
   s = gauge_convert(c, dU);
-  c->launches += 1;
+  launch_split_copy(c->U64, c->Udf, 2 * 4 * 9 * Vh, c->stream);  // for the emulated-FP64 operator
+  c->launches += 2;
   if (stage) cudaFreeAsync(stage, c->stream);
   int bits = 0;
   if (s == SQ_OK) s = read_error_word(c, &bits);
@@ -401,6 +415,7 @@ sq_status sq_dslash_eo(sq_ctx* c, void* out, const void* in, const void* x, int 
   d.recon = prec == SQ_F64 ? 18 : c->recon;  // FP16 fields use the FP32 links
   d.clover = (flags & SQ_DS_CLOVER_INV) ? 1 : 0;
   d.xpay = (flags & SQ_DS_XPAY) ? 1 : 0;
+  d.emul = (prec == SQ_F64 && (flags & SQ_DS_F64_EMULATED)) ? 1 : 0;
   d.a = a;
   d.cs = cs;
   d.n = n;
@@ -410,7 +425,7 @@ sq_status sq_dslash_eo(sq_ctx* c, void* out, const void* in, const void* x, int 
     // output so that an in-place xpay (x == out) is never applied twice
     void* scratch = nullptr;
     long long key = ((long long)d.prec << 56) ^ ((long long)d.recon << 48) ^ ((long long)c->Vh << 12) ^ n;
-    if (c->tuned.find(key) == c->tuned.end()) {
+    if (!d.emul && c->tuned.find(key) == c->tuned.end()) {
       cudaError_t e = cudaMallocAsync(&scratch, field_bytes(c->Vh, prec, n), c->stream);
       if (e != cudaSuccess) return cuda_check(c, e, "sq_dslash_eo tuning buffer");
       DslashCall t = d;
@@ -418,7 +433,7 @@ sq_status sq_dslash_eo(sq_ctx* c, void* out, const void* in, const void* x, int 
       tune_dslash(c, t, c->stream);
       cudaFreeAsync(scratch, c->stream);
     }
-    d.shape = tune_dslash(c, d, c->stream);
+    if (!d.emul) d.shape = tune_dslash(c, d, c->stream);  // the emulated kernel has one shape
   }
   launch_dslash(c, d, c->stream);
   c->launches += 1;

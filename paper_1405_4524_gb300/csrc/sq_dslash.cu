@@ -265,7 +265,9 @@ void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s) {
   dim3 grid((unsigned)a.nsb * (unsigned)a.nrb);
   bool ok = false;
   int nparts = a.nsb * (int)(block.x >> 5);
-  if (d.shape.kind == 1 && launch_dslash_tile(c, d, s, &nparts)) {
+  if (d.prec == P64 && d.emul) {
+    ok = launch_dslash_df(c, d, d.out2, d.xfirst, s, &nparts);
+  } else if (d.shape.kind == 1 && launch_dslash_tile(c, d, s, &nparts)) {
     ok = true;
   } else if (d.prec == P64) {
     if (d.fin == FIN_TRUE && d.clover && d.xpay) {

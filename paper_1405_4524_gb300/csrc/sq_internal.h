@@ -21,6 +21,8 @@ struct CloverSet {
   double2* A64 = nullptr;     // [2][36][Vh] packed A (FP64)
   double2* Ainv64 = nullptr;  // [2][36][Vh] packed A^{-1} (FP64)
   float4* Ainv32 = nullptr;   // [2][18][Vh]
+  float4* Adf = nullptr;      // [2][36][Vh] A split into float pairs (re.h, im.h, re.l, im.l)
+  float4* Ainvdf = nullptr;   // [2][36][Vh] A^{-1} split likewise
   double a_bound = 1.0;       // max over sites of a Gershgorin bound on ||A||_2
   int valid = 0;              // built for the current gauge field
   unsigned long long tick = 0;
@@ -141,6 +143,7 @@ struct sq_ctx {
   int su3 = 0;  // links passed the SU(3) check (needed by reconstruct-12)
   double2* U64 = nullptr;  // [2][4][9][Vh]
   void* U32 = nullptr;     // recon 12: float4 [2][4][3][Vh]; 18: float2 [2][4][9][Vh]
+  float4* Udf = nullptr;   // [2][4][9][Vh] U64 split into float pairs (emulated FP64)
   // clover cache
   std::vector<sq::CloverSet> clover;
   int cur_clover = -1;
@@ -206,8 +209,19 @@ struct DslashCall {
   Field r1; // extra operand of the reduction (rhat for FIN_ALPHA)
   RedArgs ra;
   Shape shape;
+  // FP64 fields only: emul = 1 does the arithmetic in double-FP32 on the
+  // FP32 pipe (sq_dslash_df.cu); xfirst = 1 applies A^-1 after the xpay
+  // (out = A^-1 (x + a D in)), writing x + a D in to out2 if it is set
+  int emul;
+  int xfirst;
+  Field out2;
 };
 void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s);
+// emulated-FP64 kernels (sq_dslash_df.cu)
+bool launch_dslash_df(const sq_ctx* c, const DslashCall& d, Field out2, int xfirst, cudaStream_t s, int* nparts);
+void launch_clover_df(const sq_ctx* c, const CloverSet& cs, Field out, Field x, Field in, int parity, double c1,
+                      double c2, int which, int n, cudaStream_t s);
+void launch_split_copy(const double2* in, float4* out, size_t n, cudaStream_t s);
 // halo-tiled kernel (sq_dslash_tile.cu): false if d.shape does not apply
 bool launch_dslash_tile(const sq_ctx* c, const DslashCall& d, cudaStream_t s, int* nparts);
 bool tile_shape_ok(const sq_ctx* c, int prec, int recon, const Shape& sh);

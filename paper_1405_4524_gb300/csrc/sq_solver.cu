@@ -716,6 +716,7 @@ static void launch_iteration(sq_ctx* c, Workspace& w, const CloverSet& cs, doubl
   d64.list = w.update_list;
   d64.count = &w.ctl->n_update;
   d64.shape = k64Shape;
+  d64.emul = P != P64 ? 1 : 0;  // mixed solvers: FP64-accurate arithmetic on the FP32 pipe
   d64.out = w.t64o; d64.in = w.x64; d64.p_out = 1; d64.xpay = 0; d64.fin = FIN_NONE;
   launch_dslash(c, d64, us);
   m.mark(us);
@@ -764,6 +765,7 @@ static void launch_update(sq_ctx* c, Workspace& w, const CloverSet& cs, double k
   d64.n = n;
   d64.ra = red_args(w);
   d64.shape = k64Shape;
+  d64.emul = P != P64 ? 1 : 0;
   d64.out = w.t64o; d64.in = w.x64; d64.p_out = 1;
   launch_dslash(c, d64, s);
   d64.out = w.r64; d64.in = w.t64o; d64.x = w.r64; d64.p_out = 0; d64.xpay = 1; d64.a = kappa * kappa;
@@ -836,6 +838,7 @@ static Cost class_cost(int kc, int inner, int recon, double Vh, double na, doubl
 //   r_e = eta_e - A_ee psi_e + k D_eo psi_o,   r_o = t64o - A_oo psi_o.
 static void launch_full_residual(sq_ctx* c, Workspace& w, const CloverSet& cs, double kappa, cudaStream_t s) {
   const int n = w.n_rhs;
+  const bool emul = w.inner != P64;  // mixed solvers: emulated-FP64 arithmetic
   DslashCall d;
   memset(&d, 0, sizeof(d));
   d.prec = P64;
@@ -844,10 +847,13 @@ static void launch_full_residual(sq_ctx* c, Workspace& w, const CloverSet& cs, d
   d.n = n;
   d.shape = kBlasShape;
   d.ra = red_args(w);
-  launch_clover64(c, cs, w.r64, w.eta_e, w.x64, 0, 1.0, -1.0, 0, n, s);
+  d.emul = emul ? 1 : 0;
+  if (emul) launch_clover_df(c, cs, w.r64, w.eta_e, w.x64, 0, 1.0, -1.0, 0, n, s);
+  else launch_clover64(c, cs, w.r64, w.eta_e, w.x64, 0, 1.0, -1.0, 0, n, s);
   d.out = w.r64; d.in = w.x64o; d.x = w.r64; d.p_out = 0; d.xpay = 1; d.a = kappa;
   launch_dslash(c, d, s);
-  launch_clover64(c, cs, w.t64o, w.t64o, w.x64o, 1, 1.0, -1.0, 0, n, s);
+  if (emul) launch_clover_df(c, cs, w.t64o, w.t64o, w.x64o, 1, 1.0, -1.0, 0, n, s);
+  else launch_clover64(c, cs, w.t64o, w.t64o, w.x64o, 1, 1.0, -1.0, 0, n, s);
   RedArgs ra = red_args(w);
   launch_norm2(c, w.r64, P64, n, w.scal, ra, s);
   launch_norm2(c, w.t64o, P64, n, w.scal + n, ra, s);
@@ -949,7 +955,6 @@ static sq_status setup_problem(Prob& p, const sq_solve_params& prm) {
     launch_pack(c, sub64(w.eta_o, k0), gsrc, 1, P64, ng, s);
     launch_norm2(c, sub64(w.eta_e, k0), P64, ng, w.scal + k0, ra, s);
     launch_norm2(c, sub64(w.eta_o, k0), P64, ng, w.scal + n + k0, ra, s);
-    launch_clover64(c, *p.cs, sub64(w.t64o, k0), none, sub64(w.eta_o, k0), 1, 0.0, 1.0, 1, ng, s);
     DslashCall d;
     memset(&d, 0, sizeof(d));
     d.prec = P64;
@@ -958,11 +963,25 @@ static sq_status setup_problem(Prob& p, const sq_solve_params& prm) {
     d.n = ng;
     d.shape = kBlasShape;
     d.ra = ra;
-    d.out = sub64(w.r64, k0); d.in = sub64(w.t64o, k0); d.x = sub64(w.eta_e, k0); d.p_out = 0; d.xpay = 1;
-    d.a = p.kappa;
-    launch_dslash(c, d, s);
-    launch_clover64(c, *p.cs, sub64(w.b64, k0), none, sub64(w.r64, k0), 0, 0.0, 1.0, 1, ng, s);
-    c->launches += 8;
+    if (inner != P64) {
+      // emulated-FP64 arithmetic, A_ee^{-1} fused after the xpay:
+      // bhat = A_ee^{-1} (eta_e + k D_eo A_oo^{-1} eta_o)
+      launch_clover_df(c, *p.cs, sub64(w.t64o, k0), none, sub64(w.eta_o, k0), 1, 0.0, 1.0, 1, ng, s);
+      d.emul = 1;
+      d.clover = 1;
+      d.xfirst = 1;
+      d.out = sub64(w.b64, k0); d.in = sub64(w.t64o, k0); d.x = sub64(w.eta_e, k0); d.p_out = 0; d.xpay = 1;
+      d.a = p.kappa;
+      launch_dslash(c, d, s);
+      c->launches += 7;
+    } else {
+      launch_clover64(c, *p.cs, sub64(w.t64o, k0), none, sub64(w.eta_o, k0), 1, 0.0, 1.0, 1, ng, s);
+      d.out = sub64(w.r64, k0); d.in = sub64(w.t64o, k0); d.x = sub64(w.eta_e, k0); d.p_out = 0; d.xpay = 1;
+      d.a = p.kappa;
+      launch_dslash(c, d, s);
+      launch_clover64(c, *p.cs, sub64(w.b64, k0), none, sub64(w.r64, k0), 0, 0.0, 1.0, 1, ng, s);
+      c->launches += 8;
+    }
   }
   std::vector<double> eta2(2 * n);
   int bad = 0;
@@ -1259,11 +1278,22 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       d.n = n;
       d.shape = kBlasShape;
       d.ra = red_args(w);
-      d.out = w.t64o; d.in = w.x64; d.x = w.eta_o; d.p_out = 1; d.xpay = 1; d.a = p.kappa;
-      launch_dslash(c, d, sb);
-      Field none = make_field(nullptr, c->Vh, P64, n);
-      launch_clover64(c, *p.cs, w.x64o, none, w.t64o, 1, 0.0, 1.0, 1, n, sb);
-      c->launches += 2;
+      if (prm.inner_prec != P64) {
+        // emulated FP64, one launch: t64o = eta_o + k D_oe psi_e, psi_o = A_oo^{-1} t64o
+        d.emul = 1;
+        d.clover = 1;
+        d.xfirst = 1;
+        d.out2 = w.t64o;
+        d.out = w.x64o; d.in = w.x64; d.x = w.eta_o; d.p_out = 1; d.xpay = 1; d.a = p.kappa;
+        launch_dslash(c, d, sb);
+        c->launches += 1;
+      } else {
+        d.out = w.t64o; d.in = w.x64; d.x = w.eta_o; d.p_out = 1; d.xpay = 1; d.a = p.kappa;
+        launch_dslash(c, d, sb);
+        Field none = make_field(nullptr, c->Vh, P64, n);
+        launch_clover64(c, *p.cs, w.x64o, none, w.t64o, 1, 0.0, 1.0, 1, n, sb);
+        c->launches += 2;
+      }
       // solutions out (and the pion epilogue) on the side stream while the
       // FP64 check runs; a failed check redoes them after the next pass
       cudaEventRecord(w.ev_rec, sb);

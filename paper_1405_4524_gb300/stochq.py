@@ -21,7 +21,7 @@ LIBPATH = os.path.join(_HERE, "libstochq.so")
 
 SQ_F64, SQ_F32, SQ_F16 = 0, 1, 2
 SQ_HOST, SQ_DEVICE = 0, 1
-SQ_DS_CLOVER_INV, SQ_DS_XPAY, SQ_DS_SYNC = 1, 2, 4
+SQ_DS_CLOVER_INV, SQ_DS_XPAY, SQ_DS_SYNC, SQ_DS_F64_EMULATED = 1, 2, 4, 8
 SQ_OUTER_RELIABLE, SQ_OUTER_DEFECT = 0, 1
 SQ_DILUTE_TIME, SQ_DILUTE_SPIN_COLOUR, SQ_DILUTE_FULL = 1, 2, 3
 

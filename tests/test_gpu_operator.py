@@ -67,10 +67,16 @@ def oracle_dslash(s, psi_in, x, p_out, kappa, csw, clover, xpay, a):
     return oracle.restrict(w, s.par, p_out)
 
 
-@pytest.mark.parametrize("prec,recon", [(0, 18), (1, 12), (1, 18), (2, 12)])
+@pytest.mark.parametrize("prec,recon", [(0, 18), (1, 12), (1, 18), (2, 12), ("f64_emulated", 18)])
 @pytest.mark.parametrize("clover,xpay", [(0, 0), (1, 0), (0, 1), (1, 1)])
 def test_dslash_eo(setup, prec, recon, clover, xpay):
+    """FP64, FP32 and FP16 fields; "f64_emulated": FP64 fields through the
+    double-FP32 kernel the mixed solvers use for their FP64 steps (same
+    tolerance as FP64)."""
     s = setup
+    emul = 0
+    if prec == "f64_emulated":
+        prec, emul = 0, s.sq.SQ_DS_F64_EMULATED
     sq = s.sq
     if recon == 18:
         sq.sq_load_gauge(s.ctx, s.U, 18)
@@ -85,7 +91,7 @@ def test_dslash_eo(setup, prec, recon, clover, xpay):
         bin_, bx, bout = device_buffer(fb), device_buffer(fb), device_buffer(fb)
         sq.sq_pack_spinor(s.ctx, bin_, psi, 1 - p_out, prec, n)
         sq.sq_pack_spinor(s.ctx, bx, x, p_out, prec, n)
-        flags = (sq.SQ_DS_CLOVER_INV if clover else 0) | (sq.SQ_DS_XPAY if xpay else 0)
+        flags = (sq.SQ_DS_CLOVER_INV if clover else 0) | (sq.SQ_DS_XPAY if xpay else 0) | emul
         sq.sq_dslash_eo(s.ctx, bout, bin_, bx if xpay else None, p_out, prec, n,
                         flags | sq.SQ_DS_SYNC, a)
         got = np.zeros_like(psi)
