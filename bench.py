@@ -706,6 +706,8 @@ def main():
                                  "speedup_vs_fp64_route": round(ms_tc64 / ms_tc, 1),
                                  "complex_terms_per_s": round(terms_tc / (ms_tc / 1000.0), 1),
                                  "flops_per_term": 40,
+                                 "method_flops_per_term": 8,
+                                 "frac_method_flops": round(8.0 * terms_tc / (ms_tc / 1000.0) / 1e12 / bf16_peak, 4),
                                  "note": "FP16 x FP16 -> FP32 tcgen05 products of 5 exact 11-bit digits of "
                                          "gamma5 X (real and imaginary rows) against ternary sources; whole "
                                          "call (packing, products, FP64 digit sums, correlator) against the "

@@ -133,6 +133,16 @@ typedef struct sq_solve_params {
                           Ignored by sq_solve_batch.                       */
   const int *pion_tslice; /* [n_rhs] source time slices for pion, same
                           memory kind as pion; NULL: all 0                  */
+  double breakdown_tol; /* BiCGStab restarts a source when |rho'| <
+                          breakdown_tol ||rhat|| ||r|| (a near breakdown of
+                          the recurrence); more than 64 restarts end it with
+                          SQ_ERR_BREAKDOWN. <= 0: 1e-14 (the default)       */
+  int fallback;        /* SQ_F16 inner only, sq_solve only: sources the FP16
+                          solve leaves with SQ_ERR_NOCONV or SQ_ERR_BREAKDOWN
+                          (a stagnating FP16 recurrence) are solved again
+                          with the FP32 inner solver from their current
+                          iterate; 1 (default) or 0                         */
+  int fallback_max_iter; /* inner iterations of that FP32 solve; 0: max_iter */
 } sq_solve_params;
 
 typedef struct sq_solve_stats {
@@ -143,6 +153,9 @@ typedef struct sq_solve_stats {
   int restarts;          /* BiCGStab restarts (breakdown or defect cycle) */
   double true_residual;  /* ||eta - M psi|| / ||eta||, FP64, full lattice */
   double seconds;        /* wall time of the whole sq_solve call          */
+  int breakdowns;        /* near breakdowns of the recurrence (restarts)   */
+  int fallback;          /* 1: solved again with the FP32 inner solver
+                            after the FP16 solve did not converge          */
 } sq_solve_stats;
 
 /* Fill *p with the defaults (FP32 inner, reliable updates, automatic delta). */

@@ -179,6 +179,8 @@ void sq_default_params(sq_solve_params* p) {
   p->chunk = 16;
   p->use_graph = 1;
   p->io = SQ_HOST;
+  p->breakdown_tol = 1e-14;
+  p->fallback = 1;
 }
 
 const char* sq_status_string(sq_status s) {

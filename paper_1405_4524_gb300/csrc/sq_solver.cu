@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(256) k_flush(const VArgs a) {
 
 // Initial state: every source asks for an FP64 update with restart.
 __global__ void k_init(RhsState* st, Control* ctl, int* update_list, const double* target2, double delta2,
-                       double margin2, int max_iter, int defect, int refresh, int n) {
+                       double margin2, int max_iter, int defect, int refresh, double bd2, int n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) {
     RhsState q;
@@ -368,6 +368,7 @@ __global__ void k_init(RhsState* st, Control* ctl, int* update_list, const doubl
     q.max_iter = max_iter;
     q.defect = defect;
     q.refresh = refresh;
+    q.bd2 = bd2;
     q.active = 1;
     q.want_update = 1;
     q.want_restart = 1;
@@ -891,6 +892,9 @@ static sq_status validate_params(sq_ctx* c, sq_solve_params& prm) {
   if (!(prm.delta > 0.0))
     prm.delta = prm.inner_prec == P16 ? (prm.outer == SQ_OUTER_DEFECT ? 1e-4 : 3e-3) : 3e-6;
   if (prm.chunk <= 0) prm.chunk = 16;
+  if (!(prm.breakdown_tol > 0.0)) prm.breakdown_tol = 1e-14;
+  if (!std::isfinite(prm.breakdown_tol)) return set_error(c, SQ_ERR_ARG, "sq_solve: breakdown_tol must be finite");
+  if (prm.fallback_max_iter < 0) return set_error(c, SQ_ERR_ARG, "sq_solve: fallback_max_iter must be >= 0");
   if (prm.chunk > 256) return set_error(c, SQ_ERR_ARG, "sq_solve: chunk must be <= 256");
   if (prm.sites_per_block > 0 || prm.rhs_per_block > 0) {
     if (prm.sites_per_block <= 0 || prm.rhs_per_block <= 0 || prm.sites_per_block % 32 ||
@@ -1115,7 +1119,8 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       const double margin = prm.inner_prec == P16 ? 0.5 : prm.inner_prec == P32 ? 0.8 : 1.0;
       k_init<<<(p.n + 127) / 128, 128, 0, p.s>>>(w.st, w.ctl, w.update_list, w.scal, delta * delta,
                                                  margin * margin, prm.max_iter,
-                                                 prm.outer == SQ_OUTER_DEFECT ? 1 : 0, w.refresh ? 1 : 0, p.n);
+                                                 prm.outer == SQ_OUTER_DEFECT ? 1 : 0, w.refresh ? 1 : 0,
+                                                 prm.breakdown_tol * prm.breakdown_tol, p.n);
       p.c->launches += 1;
       p.upd(p.c, w, *p.cs, p.kappa, p.s, attempt == 0 && !prm.use_x0);
       if (p.s != sb) {
@@ -1331,6 +1336,7 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
           o.iterations += hs[k].iter;
           o.updates += hs[k].updates;
           o.restarts += hs[k].restarts;
+          o.breakdowns += hs[k].breakdowns;
           o.true_residual = rr;
         }
         if (status != SQ_OK && *result == SQ_OK) *result = (sq_status)status;
@@ -1366,6 +1372,116 @@ static sq_status check_timeouts(sq_ctx* c, const char* what) {
   return SQ_OK;
 }
 
+// FP16 inner solves whose sources end with NOCONV or BREAKDOWN (the FP16
+// recurrence stagnated) are solved again by the FP32 inner solver from their
+// current iterate; their statistics add up and carry fallback = 1, and their
+// rows of the fused pion epilogue are recomputed. Returns the final status.
+static sq_status fp16_fallback(sq_ctx* c, double kappa, double csw, const double* src, double* sol, int n,
+                               double tol, const sq_solve_params& prm, sq_solve_stats* st) {
+  std::vector<int> bad;
+  for (int k = 0; k < n; k++)
+    if (st[k].status == SQ_ERR_NOCONV || st[k].status == SQ_ERR_BREAKDOWN) bad.push_back(k);
+  const int m = (int)bad.size();
+  if (m > 0) {
+    const size_t per = (size_t)c->V * 24;  // doubles per source
+    sq_solve_params p2 = prm;
+    p2.inner_prec = P32;
+    p2.outer = SQ_OUTER_RELIABLE;
+    p2.delta = 0.0;
+    p2.use_x0 = 1;
+    p2.fallback = 0;
+    p2.profile = 0;
+    p2.pion = nullptr;
+    p2.pion_tslice = nullptr;
+    if (prm.fallback_max_iter > 0) p2.max_iter = prm.fallback_max_iter;
+    std::vector<sq_solve_stats> st2(m);
+    std::vector<double> hs, hx;
+    double* dbuf = nullptr;
+    const double *s2 = nullptr;
+    double* x2 = nullptr;
+    if (prm.io == SQ_HOST) {
+      hs.resize(m * per);
+      hx.resize(m * per);
+      for (int i = 0; i < m; i++) {
+        memcpy(hs.data() + i * per, src + bad[i] * per, per * sizeof(double));
+        memcpy(hx.data() + i * per, sol + bad[i] * per, per * sizeof(double));
+      }
+      s2 = hs.data();
+      x2 = hx.data();
+    } else {
+      cudaError_t e = cudaMallocAsync((void**)&dbuf, 2 * m * per * sizeof(double), c->stream);
+      if (e != cudaSuccess) return cuda_check(c, e, "sq_solve fallback buffers");
+      for (int i = 0; i < m; i++) {
+        cudaMemcpyAsync(dbuf + i * per, src + bad[i] * per, per * sizeof(double), cudaMemcpyDeviceToDevice,
+                        c->stream);
+        cudaMemcpyAsync(dbuf + (m + i) * per, sol + bad[i] * per, per * sizeof(double), cudaMemcpyDeviceToDevice,
+                        c->stream);
+      }
+      s2 = dbuf;
+      x2 = dbuf + m * per;
+    }
+    sq_status r2 = solve_impl(c, kappa, csw, s2, x2, m, tol, &p2, st2.data());
+    if (r2 != SQ_OK && r2 != SQ_ERR_NOCONV && r2 != SQ_ERR_BREAKDOWN) {
+      if (dbuf) cudaFreeAsync(dbuf, c->stream);
+      return r2;
+    }
+    const int T = c->dims[3];
+    for (int i = 0; i < m; i++) {
+      const int k = bad[i];
+      if (prm.io == SQ_HOST) memcpy(sol + k * per, x2 + i * per, per * sizeof(double));
+      else cudaMemcpyAsync(sol + k * per, x2 + i * per, per * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+      sq_solve_stats& o = st[k];
+      o.status = st2[i].status;
+      o.iterations += st2[i].iterations;
+      o.updates += st2[i].updates;
+      o.restarts += st2[i].restarts;
+      o.breakdowns += st2[i].breakdowns;
+      o.true_residual = st2[i].true_residual;
+      o.fallback = 1;
+    }
+    if (prm.pion) {  // those sources' correlator rows, from the new solutions
+      double* dC = nullptr;
+      double* dx = nullptr;
+      cudaError_t e = cudaMallocAsync((void**)&dC, (size_t)m * T * sizeof(double), c->stream);
+      if (e == cudaSuccess && prm.io == SQ_HOST) {
+        e = cudaMallocAsync((void**)&dx, m * per * sizeof(double), c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x2, m * per * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+      }
+      std::vector<int> ts(m, 0);
+      if (e == cudaSuccess && prm.pion_tslice) {
+        for (int i = 0; i < m && e == cudaSuccess; i++)
+          e = cudaMemcpyAsync(&ts[i], prm.pion_tslice + bad[i], sizeof(int),
+                              prm.io == SQ_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      }
+      int* dts = nullptr;
+      if (e == cudaSuccess) e = cudaMallocAsync((void**)&dts, m * sizeof(int), c->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(dts, ts.data(), m * sizeof(int), cudaMemcpyHostToDevice, c->stream);
+      if (e == cudaSuccess) {
+        launch_pion(c, prm.io == SQ_HOST ? dx : x2, m, dts, dC, c->stream);
+        c->launches += 1;
+        for (int i = 0; i < m && e == cudaSuccess; i++)
+          e = cudaMemcpyAsync(prm.pion + (size_t)bad[i] * T, dC + (size_t)i * T, T * sizeof(double),
+                              prm.io == SQ_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      }
+      if (dts) cudaFreeAsync(dts, c->stream);
+      if (dx) cudaFreeAsync(dx, c->stream);
+      if (dC) cudaFreeAsync(dC, c->stream);
+      if (e != cudaSuccess) {
+        if (dbuf) cudaFreeAsync(dbuf, c->stream);
+        return cuda_check(c, e, "sq_solve fallback correlator");
+      }
+    }
+    if (dbuf) cudaFreeAsync(dbuf, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_check(c, e, "sq_solve fallback");
+  }
+  for (int k = 0; k < n; k++)
+    if (st[k].status != SQ_OK) return (sq_status)st[k].status;
+  return SQ_OK;
+}
+
 sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, double* sol, int n, double tol,
                      const sq_solve_params* prm_in, sq_solve_stats* stats) {
   auto t0 = std::chrono::steady_clock::now();
@@ -1375,6 +1491,13 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
   else sq_default_params(&prm);
   sq_status st = validate_params(c, prm);
   if (st != SQ_OK) return st;
+  // per-source statistics are needed to choose the sources of an FP16 fallback
+  std::vector<sq_solve_stats> local;
+  const bool fb = prm.inner_prec == P16 && prm.fallback && n > 0;
+  if (fb && !stats) {
+    local.resize(n);
+    stats = local.data();
+  }
   std::vector<Prob> P(1);
   Prob& p = P[0];
   p.c = c;
@@ -1396,6 +1519,12 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
   if (st != SQ_OK) return st;
   st = check_timeouts(c, "sq_solve");
   if (st != SQ_OK) return st;
+  if (fb && result != SQ_OK) {
+    if (prm.verbose) fprintf(stderr, "libstochq: FP16 solve incomplete, FP32 fallback\n");
+    result = fp16_fallback(c, kappa, csw, src, sol, n, tol, prm, stats);
+    if (result == SQ_ERR_CUDA || result == SQ_ERR_OOM || result == SQ_ERR_TIMEOUT || result == SQ_ERR_ARG)
+      return result;
+  }
   double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats)
     for (int k = 0; k < n; k++) stats[k].seconds = secs;

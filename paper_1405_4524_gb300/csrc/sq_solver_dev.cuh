@@ -35,6 +35,8 @@ struct RhsState {
   double delta2;   // update trigger (squared)
   double ref2;     // residual^2 of the first FP64 update (the reference for
                    // FP32 refreshes)
+  double bd2;      // near-breakdown threshold: restart when |rho'|^2 <
+                   // bd2 ||rhat||^2 ||r||^2
   int iter, updates, restarts, breakdowns;
   int status;        // sq_status value
   int active;        // 1 while iterating
@@ -129,7 +131,7 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int k, const double*
     q.rho_re = nr;
     q.rho_im = ni;
     // |rho'| negligible against ||rhat|| ||r||: near breakdown, restart
-    if (!bad && (nr * nr + ni * ni) < 1e-28 * r2 * q.rstart2 && r2 > q.target2) {
+    if (!bad && (nr * nr + ni * ni) < q.bd2 * r2 * q.rstart2 && r2 > q.target2) {
       q.want_restart = 1;
       q.breakdowns++;
     }

@@ -40,6 +40,7 @@ class sq_solve_params(C.Structure):
         ("rhs_per_block", C.c_int), ("chunk", C.c_int), ("use_graph", C.c_int),
         ("io", C.c_int), ("use_x0", C.c_int), ("verbose", C.c_int),
         ("profile", C.c_int), ("pion", C.c_void_p), ("pion_tslice", C.c_void_p),
+        ("breakdown_tol", C.c_double), ("fallback", C.c_int), ("fallback_max_iter", C.c_int),
     ]
 
 
@@ -47,6 +48,7 @@ class sq_solve_stats(C.Structure):
     _fields_ = [
         ("status", C.c_int), ("iterations", C.c_int), ("updates", C.c_int),
         ("restarts", C.c_int), ("true_residual", C.c_double), ("seconds", C.c_double),
+        ("breakdowns", C.c_int), ("fallback", C.c_int),
     ]
 
 
@@ -327,7 +329,8 @@ def sq_solve(ctx, kappa: float, c_sw: float, sources, solutions, n_rhs: int, tol
     st = _lib.sq_solve(ctx, float(kappa), float(c_sw), _ptr(sources), _ptr(solutions), int(n_rhs),
                        float(tol), C.byref(params), stats)
     out = [dict(status=s.status, iterations=s.iterations, updates=s.updates,
-                restarts=s.restarts, true_residual=s.true_residual, seconds=s.seconds)
+                restarts=s.restarts, true_residual=s.true_residual, seconds=s.seconds,
+                breakdowns=s.breakdowns, fallback=s.fallback)
            for s in stats]
     if raise_on_error:
         _check(ctx, st, out)
@@ -349,7 +352,8 @@ def sq_solve_batch(problems, params: sq_solve_params | None = None, raise_on_err
     stats = (sq_solve_stats * total)()
     st = _lib.sq_solve_batch(arr, len(problems), C.byref(params), stats)
     out = [dict(status=s.status, iterations=s.iterations, updates=s.updates,
-                restarts=s.restarts, true_residual=s.true_residual, seconds=s.seconds)
+                restarts=s.restarts, true_residual=s.true_residual, seconds=s.seconds,
+                breakdowns=s.breakdowns, fallback=s.fallback)
            for s in stats]
     if raise_on_error and st != 0:
         raise StochqError(st, sq_last_error(problems[0]["ctx"]), out)

@@ -355,3 +355,72 @@ def test_solve_batch_mixed_lattices_and_kappas():
     finally:
         sA.close()
         sB.close()
+
+
+def test_near_breakdown_restarts_converge(small):
+    """A loose near-breakdown threshold (|rho'| < 0.3 ||rhat|| ||r||) makes the
+    recurrence restart repeatedly; the solve still reaches the oracle's
+    solution, and the restarts are counted per source."""
+    s, spec, eta, ref = small
+    sq = s.sq
+    n = eta.shape[0]
+    sol = np.zeros_like(eta)
+    st, stats = sq.sq_solve(s.ctx, spec["kappa"], spec["csw"], eta, sol, n, 1e-10,
+                            sq.sq_default_params(breakdown_tol=0.3))
+    assert st == 0
+    assert all(x["breakdowns"] >= 1 and x["restarts"] >= x["breakdowns"] for x in stats)
+    for k in range(n):
+        assert rel(sol[k], ref[k]) <= 1e-9
+
+
+def test_repeated_breakdown_is_reported():
+    """breakdown_tol > 1 declares a near breakdown at every iteration (|rho'| <=
+    ||rhat|| ||r|| always); on a slowly converging system (kappa 0.128, near
+    the critical kappa of these links) the 65th restart comes before
+    convergence and ends every source with SQ_ERR_BREAKDOWN, with the
+    per-source count in the statistics."""
+    from paper_1405_4524_gb300 import stochq as sq
+
+    spec = inputs.WORKLOADS["4x4x4x8"]
+    s = Setup(spec["dims"], spec["eps"], spec["link_seed"])
+    try:
+        eta = inputs.make_z4(spec["dims"], 2, 2101)
+        sol = np.zeros_like(eta)
+        st, stats = sq.sq_solve(s.ctx, 0.128, spec["csw"], eta, sol, 2, 1e-12,
+                                sq.sq_default_params(breakdown_tol=10.0), raise_on_error=False)
+        assert st == sq.SQ_ERR_BREAKDOWN
+        assert all(x["status"] == sq.SQ_ERR_BREAKDOWN and x["breakdowns"] > 64 for x in stats)
+        assert "did not converge" in sq.sq_last_error(s.ctx)
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("io", ["host", "device"])
+def test_fp16_fallback_to_fp32(small, io):
+    """An FP16 solve cut off after 5 iterations leaves every source
+    unconverged; the fallback solves them again with the FP32 inner solver
+    from where the FP16 solve stopped: all converge to the oracle's
+    solutions, carry fallback = 1 and their fused pion rows are those of the
+    final solutions. Without the fallback the call reports SQ_ERR_NOCONV."""
+    import torch
+
+    s, spec, eta, ref = small
+    sq = s.sq
+    n, T = eta.shape[0], eta.shape[1]
+    src = eta if io == "host" else torch.from_numpy(eta).cuda()
+    sol = np.zeros_like(eta) if io == "host" else torch.zeros_like(src)
+    pion = np.zeros((n, T)) if io == "host" else torch.zeros((n, T), dtype=torch.float64, device="cuda")
+    prm = sq.sq_default_params(inner_prec=sq.SQ_F16, max_iter=5, fallback_max_iter=5000)
+    st, stats = sq.sq_solve(s.ctx, spec["kappa"], spec["csw"], src, sol, n, 1e-10, prm, pion=pion)
+    assert st == 0
+    got = sol if io == "host" else sol.cpu().numpy()
+    C = pion if io == "host" else pion.cpu().numpy()
+    for k in range(n):
+        assert stats[k]["fallback"] == 1 and stats[k]["status"] == 0 and stats[k]["true_residual"] <= 1e-10
+        assert rel(got[k], ref[k]) <= 1e-9
+        assert np.allclose(C[k], oracle.pion_correlator(got[k], 0), rtol=1e-13)
+    sol2 = np.zeros_like(eta)
+    st, stats = sq.sq_solve(s.ctx, spec["kappa"], spec["csw"], eta, sol2, n, 1e-10,
+                            sq.sq_default_params(inner_prec=sq.SQ_F16, max_iter=5, fallback=0),
+                            raise_on_error=False)
+    assert st == sq.SQ_ERR_NOCONV and all(x["fallback"] == 0 for x in stats)
