@@ -507,6 +507,19 @@ sq_status sq_kernel_launches(const sq_ctx *ctx, long long *n);
 sq_status sq_set_dslash_shape(sq_ctx *ctx, sq_prec prec, int n_rhs, int kind, const int shape[5]);
 sq_status sq_get_dslash_shape(const sq_ctx *ctx, sq_prec prec, int n_rhs, int *kind, int shape[5]);
 
+/* Persisted launch shapes. sq_tune_save appends one text line per shape
+ * this context holds (tuned or set), keyed by the GPU's name, the lattice
+ * dims, the precision, the reconstruction and n_rhs, to the file `path`;
+ * sq_tune_load reads the lines of such a file that match this context's GPU
+ * and lattice (later lines win) and installs their shapes, so later calls
+ * for those keys skip the tuner. Lines that do not parse, belong to another
+ * GPU or lattice, or name a shape this lattice does not admit are skipped;
+ * *n_loaded (may be NULL) counts the shapes installed.
+ * Errors: SQ_ERR_ARG (NULL path), SQ_ERR_STATE (the file cannot be opened
+ * or written). */
+sq_status sq_tune_save(const sq_ctx *ctx, const char *path);
+sq_status sq_tune_load(sq_ctx *ctx, const char *path, int *n_loaded);
+
 /* Limit, in SM clock cycles, of every bounded device-side wait in this
  * context's kernels (the bulk-copy rings of the halo-tiled dslash and of the
  * tensor-core stochastic operators); 0 restores the default of 4e9 cycles

@@ -484,6 +484,74 @@ sq_status sq_set_dslash_shape(sq_ctx* c, sq_prec prec, int n, int kind, const in
       return set_error(c, SQ_ERR_ARG, "sq_set_dslash_shape: the tiled shape does not apply to this lattice");
   }
   c->tuned[shape_key(c, prec, n)] = sh;
+  c->tuned_meta[shape_key(c, prec, n)] = {(int)prec, prec == SQ_F64 ? 18 : c->recon, n};
+  return SQ_OK;
+}
+
+static std::string gpu_name(const sq_ctx* c) {
+  cudaDeviceProp pr;
+  std::string name = "unknown";
+  if (cudaGetDeviceProperties(&pr, c->device) == cudaSuccess) name = pr.name;
+  for (auto& ch : name)
+    if (ch == ' ' || ch == '\t') ch = '_';
+  return name;
+}
+
+sq_status sq_tune_save(const sq_ctx* c, const char* path) {
+  if (!c) return SQ_ERR_ARG;
+  sq_ctx* cm = const_cast<sq_ctx*>(c);
+  if (!path) return set_error(cm, SQ_ERR_ARG, "sq_tune_save: null path");
+  FILE* f = fopen(path, "a");
+  if (!f) return set_error(cm, SQ_ERR_STATE, "sq_tune_save: cannot open %s", path);
+  const std::string g = gpu_name(c);
+  for (const auto& kv : c->tuned) {
+    auto m = c->tuned_meta.find(kv.first);
+    if (m == c->tuned_meta.end()) continue;
+    const Shape& sh = kv.second;
+    fprintf(f, "stochq-shape %s %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d\n", g.c_str(), c->dims[0], c->dims[1],
+            c->dims[2], c->dims[3], m->second[0], m->second[1], m->second[2], sh.kind, sh.sx, sh.ry, sh.order, sh.by,
+            sh.bz, sh.bt, sh.sg, sh.nbuf);
+  }
+  const bool ok = fclose(f) == 0;
+  return ok ? SQ_OK : set_error(cm, SQ_ERR_STATE, "sq_tune_save: cannot write %s", path);
+}
+
+sq_status sq_tune_load(sq_ctx* c, const char* path, int* n_loaded) {
+  if (!c) return SQ_ERR_ARG;
+  if (!path) return set_error(c, SQ_ERR_ARG, "sq_tune_load: null path");
+  if (n_loaded) *n_loaded = 0;
+  FILE* f = fopen(path, "r");
+  if (!f) return set_error(c, SQ_ERR_STATE, "sq_tune_load: cannot open %s", path);
+  const std::string g = gpu_name(c);
+  char line[512], name[256];
+  int cnt = 0;
+  while (fgets(line, sizeof(line), f)) {
+    int d[4], prec, recon, n, kind, sx, ry, order, by, bz, bt, sg, nbuf;
+    if (sscanf(line, "stochq-shape %255s %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d", name, &d[0], &d[1], &d[2],
+               &d[3], &prec, &recon, &n, &kind, &sx, &ry, &order, &by, &bz, &bt, &sg, &nbuf) != 17)
+      continue;
+    if (g != name || d[0] != c->dims[0] || d[1] != c->dims[1] || d[2] != c->dims[2] || d[3] != c->dims[3]) continue;
+    if (prec < SQ_F64 || prec > SQ_F16 || n <= 0 || recon != (prec == SQ_F64 ? 18 : c->recon)) continue;
+    Shape sh;
+    sh.kind = kind;
+    sh.sx = sx;
+    sh.ry = ry;
+    sh.order = order;
+    sh.by = by;
+    sh.bz = bz;
+    sh.bt = bt;
+    sh.sg = sg;
+    sh.nbuf = nbuf;
+    if (kind == 1 && !tile_shape_ok(c, prec, recon, sh)) continue;
+    if (kind == 0 && (sx <= 0 || sx % 32 || ry <= 0 || sx * ry > 256 || (order != 0 && order != 1))) continue;
+    if (kind != 0 && kind != 1) continue;
+    const long long key = shape_key(c, prec, n);
+    c->tuned[key] = sh;
+    c->tuned_meta[key] = {prec, recon, n};
+    cnt++;
+  }
+  fclose(f);
+  if (n_loaded) *n_loaded = cnt;
   return SQ_OK;
 }
 

@@ -393,6 +393,7 @@ Shape tune_dslash(sq_ctx* c, DslashCall d, cudaStream_t s) {
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   c->tuned[key] = best;
+  c->tuned_meta[key] = {d.prec, d.recon, d.n};
   return best;
 }
 

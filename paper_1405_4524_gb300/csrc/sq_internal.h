@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <map>
 #include <string>
 #include <vector>
@@ -154,6 +155,7 @@ struct sq_ctx {
   sq::BatchCache* batch = nullptr;
   unsigned long long uid = 0;  // unique per context (graph cache keys)
   std::map<long long, sq::Shape> tuned;
+  std::map<long long, std::array<int, 3>> tuned_meta;  // (prec, recon, n) of each tuned key
   std::string last_error;
   long long launches = 0;          // kernels launched (graph nodes included)
   int prof_valid = 0;

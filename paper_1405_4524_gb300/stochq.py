@@ -112,6 +112,8 @@ _SIG = {
     "sq_set_dslash_shape": (_i, [_vp, _i, _i, _i, C.POINTER(_i)]),
     "sq_get_dslash_shape": (_i, [_vp, _i, _i, C.POINTER(_i), C.POINTER(_i)]),
     "sq_set_wait_cycles": (_i, [_vp, C.c_longlong, _i]),
+    "sq_tune_save": (_i, [_vp, C.c_char_p]),
+    "sq_tune_load": (_i, [_vp, C.c_char_p, C.POINTER(_i)]),
     "sq_status_string": (C.c_char_p, [_i]),
     "sq_last_error": (C.c_char_p, [_vp]),
 }
@@ -529,6 +531,17 @@ def sq_get_dslash_shape(ctx, prec: int, n_rhs: int):
     v = (C.c_int * 5)()
     _check(ctx, _lib.sq_get_dslash_shape(ctx, int(prec), int(n_rhs), C.byref(k), v))
     return k.value, tuple(v)
+
+
+def sq_tune_save(ctx, path: str) -> None:
+    _check(ctx, _lib.sq_tune_save(ctx, os.fsencode(path)))
+
+
+def sq_tune_load(ctx, path: str) -> int:
+    """Number of shapes installed from the file."""
+    n = C.c_int(0)
+    _check(ctx, _lib.sq_tune_load(ctx, os.fsencode(path), C.byref(n)))
+    return n.value
 
 
 def sq_set_wait_cycles(ctx, cycles: int, stall_test: bool = False) -> None:

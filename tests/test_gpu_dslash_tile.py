@@ -258,3 +258,43 @@ def test_solve_reports_timeout():
         assert st == 0 and all(x["true_residual"] <= 1e-10 for x in stats)
     finally:
         sq.sq_destroy(ctx)
+
+
+def test_tuned_shapes_persist(tmp_path):
+    """Shapes tuned in one context, saved to a file and loaded into a fresh
+    context of the same lattice, are the ones that context then uses; lines
+    of another lattice, another GPU or an inadmissible shape are skipped."""
+    from paper_1405_4524_gb300 import stochq as sq
+
+    dims = (8, 4, 4, 8)
+    path = str(tmp_path / "shapes.txt")
+    s = Setup(dims, eps=0.3, seed=23)
+    try:
+        n = 4
+        psi = random_spinors(dims, n, 91)
+        run_dslash(s, 1, n, psi, psi, 0, sq.SQ_DS_CLOVER_INV, 0.0)  # the tuner's pick
+        sq.sq_set_dslash_shape(s.ctx, 2, n, 1, (4, 2, 2, 2, 3))     # a set one
+        want = {1: sq.sq_get_dslash_shape(s.ctx, 1, n), 2: sq.sq_get_dslash_shape(s.ctx, 2, n)}
+        sq.sq_tune_save(s.ctx, path)
+    finally:
+        s.close()
+    with open(path, "a") as f:
+        f.write("stochq-shape some_other_gpu 8 4 4 8 1 12 4 0 64 2 0 0 0 0 0 2\n")
+        f.write("garbage line\n")
+    lines = open(path).read().splitlines()
+    gpu = lines[0].split()[1]
+    with open(path, "a") as f:
+        f.write(f"stochq-shape {gpu} 16 4 4 8 1 12 4 0 64 2 0 0 0 0 0 2\n")   # another lattice
+        f.write(f"stochq-shape {gpu} 8 4 4 8 1 12 9 1 3 3 3 2 2 0 0 0\n")      # inadmissible tile
+    s2 = Setup(dims, eps=0.3, seed=23)
+    try:
+        with pytest.raises(sq.StochqError):
+            sq.sq_get_dslash_shape(s2.ctx, 1, n)
+        assert sq.sq_tune_load(s2.ctx, path) == 2
+        assert sq.sq_get_dslash_shape(s2.ctx, 1, n) == want[1]
+        assert sq.sq_get_dslash_shape(s2.ctx, 2, n) == want[2]
+        got = run_dslash(s2, 2, n, psi, psi, 1, 0, 0.0)  # runs at the loaded tiled shape
+        for k in range(n):
+            assert rel(got[k], oracle_dslash(s2, psi[k], psi[k], 1, 0, 0, 0, 0, 0)) < 5e-3
+    finally:
+        s2.close()
