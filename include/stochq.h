@@ -535,6 +535,16 @@ sq_status sq_set_wait_cycles(sq_ctx *ctx, long long cycles, int stall_test);
 const char *sq_status_string(sq_status s);
 const char *sq_last_error(const sq_ctx *ctx);
 
+/* Precision, in bits, in which this build of the library accumulates the
+ * fused sums of sq_solve's inner iteration over FP32 and FP16 fields (the
+ * BiCGStab inner products and norms that give alpha, omega and beta in the
+ * solve of Eq. Sfill's X_i = M^{-1} eta_i): 32 = FP32 per thread and per
+ * warp, then FP64 across warps (the default build); 64 = FP64 from the thread
+ * level up (the build with SQ_INNER_SUMS_FP64). Sums over FP64 fields and
+ * every reliable-update and true-residual sum are FP64 in both. No
+ * arguments, no errors. */
+int sq_inner_sum_bits(void);
+
 #ifdef __cplusplus
 }
 #endif

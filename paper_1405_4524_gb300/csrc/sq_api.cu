@@ -183,6 +183,8 @@ void sq_default_params(sq_solve_params* p) {
   p->fallback = 1;
 }
 
+int sq_inner_sum_bits(void) { return (int)(8 * sizeof(sq::SumOf<float>::T)); }
+
 const char* sq_status_string(sq_status s) {
   switch (s) {
     case SQ_OK: return "SQ_OK";

@@ -76,6 +76,22 @@ struct Real<P64> {
   typedef double T;
 };
 
+// Accumulator of the inner iteration's fused sums (the BiCGStab inner
+// products and norms reduced in the operator and update kernels) for fields
+// of real type R. FP64 fields sum in FP64. FP32 and FP16 fields sum in FP32
+// per thread and per warp and in FP64 across warps; a build with
+// -DSQ_INNER_SUMS_FP64 sums them in FP64 from the thread level up.
+template <typename R>
+struct SumOf {
+  typedef R T;
+};
+#ifdef SQ_INNER_SUMS_FP64
+template <>
+struct SumOf<float> {
+  typedef double T;
+};
+#endif
+
 // ---------------------------------------------------------------------------
 // lattice geometry
 // ---------------------------------------------------------------------------

@@ -123,9 +123,10 @@ __device__ __forceinline__ void dslash_pass(const KArgs& a, int sb, int slot0, i
   const int slot = slot0 + threadIdx.y;
   const int k = slot < cnt ? (a.list ? a.list[slot] : slot) : -1;
   const bool ok = (k >= 0) && (cb < a.g.Vh);
-  R red[NRED];  // FP64 fields reduce in FP64, FP32 / FP16 in FP32 per warp
+  typedef typename SumOf<R>::T S;
+  S red[NRED];
 #pragma unroll
-  for (int i = 0; i < NRED; i++) red[i] = (R)0;
+  for (int i = 0; i < NRED; i++) red[i] = (S)0;
   if (ok) {
     cx<R> acc[12];
 #pragma unroll
@@ -158,29 +159,29 @@ __device__ __forceinline__ void dslash_pass(const KArgs& a, int sb, int slot0, i
     if (FIN == FIN_ALPHA) {  // <r1, out>
       cx<R> rv[12];
       SpinorIO<P>::load(a.r1, k, cb, rv);
-      R sr = 0, si = 0;
+      S sr = 0, si = 0;
 #pragma unroll
       for (int j = 0; j < 12; j++) {
-        sr += rv[j].re * acc[j].re + rv[j].im * acc[j].im;
-        si += rv[j].re * acc[j].im - rv[j].im * acc[j].re;
+        sr += (S)rv[j].re * acc[j].re + (S)rv[j].im * acc[j].im;
+        si += (S)rv[j].re * acc[j].im - (S)rv[j].im * acc[j].re;
       }
       red[0] = sr;
       red[1] = si;
     } else if (FIN == FIN_OMEGA) {  // <out, x>, <out, out>
-      R sr = 0, si = 0, tt = 0;
+      S sr = 0, si = 0, tt = 0;
 #pragma unroll
       for (int j = 0; j < 12; j++) {
-        sr += acc[j].re * xv[j].re + acc[j].im * xv[j].im;
-        si += acc[j].re * xv[j].im - acc[j].im * xv[j].re;
-        tt += acc[j].re * acc[j].re + acc[j].im * acc[j].im;
+        sr += (S)acc[j].re * xv[j].re + (S)acc[j].im * xv[j].im;
+        si += (S)acc[j].re * xv[j].im - (S)acc[j].im * xv[j].re;
+        tt += (S)acc[j].re * acc[j].re + (S)acc[j].im * acc[j].im;
       }
       red[0] = sr;
       red[1] = si;
       red[2] = tt;
     } else if (FIN == FIN_TRUE) {
-      R tt = 0;
+      S tt = 0;
 #pragma unroll
-      for (int j = 0; j < 12; j++) tt += acc[j].re * acc[j].re + acc[j].im * acc[j].im;
+      for (int j = 0; j < 12; j++) tt += (S)acc[j].re * acc[j].re + (S)acc[j].im * acc[j].im;
       red[0] = tt;
     }
   }
@@ -289,9 +290,9 @@ void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s) {
       else if (d.fin == FIN_OMEGA) k_finish<double, 3, FIN_OMEGA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
       else k_finish<double, 1, FIN_TRUE><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
     } else {
-      if (d.fin == FIN_ALPHA) k_finish<float, 2, FIN_ALPHA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
-      else if (d.fin == FIN_OMEGA) k_finish<float, 3, FIN_OMEGA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
-      else k_finish<float, 1, FIN_TRUE><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
+      if (d.fin == FIN_ALPHA) k_finish<SumOf<float>::T, 2, FIN_ALPHA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
+      else if (d.fin == FIN_OMEGA) k_finish<SumOf<float>::T, 3, FIN_OMEGA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
+      else k_finish<SumOf<float>::T, 1, FIN_TRUE><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
     }
   }
 }

@@ -248,11 +248,12 @@ __global__ void __launch_bounds__(64) k_dslash_df(const DfArgs a) {
         // ||out||^2 to FP32 accuracy (a residual norm). A residual is the
         // cancellation of nearly equal terms, after which the leading float
         // of a pair need not carry the value: square the rounded h + l.
-        float q = 0.f;
+        typedef SumOf<float>::T S;
+        S q = 0;
 #pragma unroll
         for (int j = 0; j < 12; j++) {
-          const float re = acc[j].re.h + acc[j].re.l, im = acc[j].im.h + acc[j].im.l;
-          q = fmaf(re, re, fmaf(im, im, q));
+          const S re = acc[j].re.h + acc[j].re.l, im = acc[j].im.h + acc[j].im.l;
+          q = fma(re, re, fma(im, im, q));
         }
         red = (double)q;
       }

@@ -381,33 +381,34 @@ __global__ void __launch_bounds__(kTileMaxThreads, 1) k_dslash_tile(const __grid
     }
     SpinorIO<P>::store(a.out, k, cb, acc);
     if (FIN != FIN_NONE) {
-      float red[NRED];
+      typedef SumOf<float>::T S;
+      S red[NRED];
       if (FIN == FIN_ALPHA) {  // <r1, out>
         cx<float> rv[12];
         SpinorIO<P>::load(a.r1, k, cb, rv);
-        float sr = 0, si = 0;
+        S sr = 0, si = 0;
 #pragma unroll
         for (int j = 0; j < 12; j++) {
-          sr += rv[j].re * acc[j].re + rv[j].im * acc[j].im;
-          si += rv[j].re * acc[j].im - rv[j].im * acc[j].re;
+          sr += (S)rv[j].re * acc[j].re + (S)rv[j].im * acc[j].im;
+          si += (S)rv[j].re * acc[j].im - (S)rv[j].im * acc[j].re;
         }
         red[0] = sr;
         red[1] = si;
       } else if (FIN == FIN_OMEGA) {  // <out, x>, <out, out>
-        float sr = 0, si = 0, q2 = 0;
+        S sr = 0, si = 0, q2 = 0;
 #pragma unroll
         for (int j = 0; j < 12; j++) {
-          sr += acc[j].re * xv[j].re + acc[j].im * xv[j].im;
-          si += acc[j].re * xv[j].im - acc[j].im * xv[j].re;
-          q2 += acc[j].re * acc[j].re + acc[j].im * acc[j].im;
+          sr += (S)acc[j].re * xv[j].re + (S)acc[j].im * xv[j].im;
+          si += (S)acc[j].re * xv[j].im - (S)acc[j].im * xv[j].re;
+          q2 += (S)acc[j].re * acc[j].re + (S)acc[j].im * acc[j].im;
         }
         red[0] = sr;
         red[1] = si;
         red[2] = q2;
       } else {
-        float q2 = 0;
+        S q2 = 0;
 #pragma unroll
-        for (int j = 0; j < 12; j++) q2 += acc[j].re * acc[j].re + acc[j].im * acc[j].im;
+        for (int j = 0; j < 12; j++) q2 += (S)acc[j].re * acc[j].re + (S)acc[j].im * acc[j].im;
         red[0] = q2;
       }
       warp_partials<NRED>(a.ra, red, k, tile * (int)(blockDim.x >> 5) + warp);

@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(256) k_xr_update(const VArgs a) {
   typedef typename Real<P>::T R;
   typedef typename Real<PX>::T RX;
   SLOT_LOOP_BEGIN
-    R red[3] = {(R)0, (R)0, (R)0};
+    typedef typename SumOf<R>::T S;
+    S red[3] = {(S)0, (S)0, (S)0};
     if (ok) {
       const RhsState& q = a.st[k];
       const R ar = (R)q.alpha_re, ai = (R)q.alpha_im, wr = (R)q.omega_re, wi = (R)q.omega_im;
@@ -114,12 +115,12 @@ __global__ void __launch_bounds__(256) k_xr_update(const VArgs a) {
         s[j] = mk(s[j].re - (wr * t[j].re - wi * t[j].im), s[j].im - (wr * t[j].im + wi * t[j].re));
       SpinorIO<P>::store(a.f4, k, cb, s);
       SpinorIO<P>::load(a.f5, k, cb, rh);
-      R n2 = 0, dr = 0, di = 0;
+      S n2 = 0, dr = 0, di = 0;
 #pragma unroll
       for (int j = 0; j < 12; j++) {
-        n2 += s[j].re * s[j].re + s[j].im * s[j].im;
-        dr += rh[j].re * s[j].re + rh[j].im * s[j].im;
-        di += rh[j].re * s[j].im - rh[j].im * s[j].re;
+        n2 += (S)s[j].re * s[j].re + (S)s[j].im * s[j].im;
+        dr += (S)rh[j].re * s[j].re + (S)rh[j].im * s[j].im;
+        di += (S)rh[j].re * s[j].im - (S)rh[j].im * s[j].re;
       }
       red[0] = n2;
       red[1] = dr;
@@ -206,7 +207,8 @@ template <int P, int PS>
 __global__ void __launch_bounds__(256) k_rel_r(const VArgs a) {
   typedef typename Real<P>::T R;
   SLOT_LOOP_BEGIN
-    R red[2] = {(R)0, (R)0};
+    typedef typename SumOf<R>::T S;
+    S red[2] = {(S)0, (S)0};
     if (ok) {
       const bool restart = a.st[k].want_restart != 0;
       cx<typename Real<PS>::T> r64[12];
@@ -223,11 +225,11 @@ __global__ void __launch_bounds__(256) k_rel_r(const VArgs a) {
       } else {
         SpinorIO<P>::load(a.f2, k, cb, rh);
       }
-      R dr = 0, di = 0;
+      S dr = 0, di = 0;
 #pragma unroll
       for (int j = 0; j < 12; j++) {
-        dr += rh[j].re * r[j].re + rh[j].im * r[j].im;
-        di += rh[j].re * r[j].im - rh[j].im * r[j].re;
+        dr += (S)rh[j].re * r[j].re + (S)rh[j].im * r[j].im;
+        di += (S)rh[j].re * r[j].im - (S)rh[j].im * r[j].re;
       }
       red[0] = dr;
       red[1] = di;
@@ -625,7 +627,7 @@ static void launch_iteration(sq_ctx* c, Workspace& w, const CloverSet& cs, doubl
   m.mark(s);
   a.f0 = w.xs; a.f1 = w.p; a.f2 = w.s; a.f3 = w.t; a.f4 = w.r; a.f5 = w.rh;
   k_xr_update<P, PX><<<bg, bb, 0, s>>>(a);
-  k_finish<R, 3, FIN_ITER><<<n, 256, 0, s>>>(a.ra, w.active_list, &w.ctl->n_active, n, (int)bg.x * (kBlasShape.sx / 32));
+  k_finish<typename SumOf<R>::T, 3, FIN_ITER><<<n, 256, 0, s>>>(a.ra, w.active_list, &w.ctl->n_active, n, (int)bg.x * (kBlasShape.sx / 32));
   m.mark(s);
   a.f0 = w.r; a.f1 = w.p; a.f2 = w.v;
   k_p_update<P><<<bg, bb, 0, s>>>(a);
@@ -691,7 +693,7 @@ static void launch_iteration(sq_ctx* c, Workspace& w, const CloverSet& cs, doubl
     launch_dslash(c, d32, us);
     rf.f0 = r32; rf.f1 = w.r; rf.f2 = w.rh; rf.f3 = w.p;
     k_rel_r<P, P32><<<bgu, bb, 0, us>>>(rf);
-    k_finish<R, 2, FIN_REFRESH><<<n, 256, 0, us>>>(rf.ra, w.refresh_list, &w.ctl->n_refresh, n,
+    k_finish<typename SumOf<R>::T, 2, FIN_REFRESH><<<n, 256, 0, us>>>(rf.ra, w.refresh_list, &w.ctl->n_refresh, n,
                                                     (int)bgu.x * (kBlasShape.sx / 32));
     if (in_node) cond_end(s, w.aux, cnode);
     us = s;
@@ -727,7 +729,7 @@ static void launch_iteration(sq_ctx* c, Workspace& w, const CloverSet& cs, doubl
   m.mark(us);
   u.f0 = w.r64; u.f1 = w.r; u.f2 = w.rh; u.f3 = w.p;
   k_rel_r<P, P64><<<bgu, bb, 0, us>>>(u);
-  k_finish<R, 2, FIN_UPDATE><<<n, 256, 0, us>>>(u.ra, w.update_list, &w.ctl->n_update, n, (int)bgu.x * (kBlasShape.sx / 32));
+  k_finish<typename SumOf<R>::T, 2, FIN_UPDATE><<<n, 256, 0, us>>>(u.ra, w.update_list, &w.ctl->n_update, n, (int)bgu.x * (kBlasShape.sx / 32));
   m.mark(us);
   if (in_node) cond_end(s, w.aux, cnode);
   k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n, m.ev ? w.hist : nullptr, it, chunk);
@@ -750,7 +752,7 @@ static void launch_update(sq_ctx* c, Workspace& w, const CloverSet& cs, double k
     k_true_norm<<<bg, bb, 0, s>>>(u);
     u.f0 = w.r64; u.f1 = w.r; u.f2 = w.rh; u.f3 = w.p;
     k_rel_r<P, P64><<<bg, bb, 0, s>>>(u);
-    k_finish<R, 2, FIN_UPDATE><<<n, 256, 0, s>>>(u.ra, w.update_list, &w.ctl->n_update, n, (int)bg.x * (kBlasShape.sx / 32));
+    k_finish<typename SumOf<R>::T, 2, FIN_UPDATE><<<n, 256, 0, s>>>(u.ra, w.update_list, &w.ctl->n_update, n, (int)bg.x * (kBlasShape.sx / 32));
     k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n, nullptr, 0, 0);
     c->launches += 5;
     return;
@@ -774,7 +776,7 @@ static void launch_update(sq_ctx* c, Workspace& w, const CloverSet& cs, double k
   launch_dslash(c, d64, s);
   u.f0 = w.r64; u.f1 = w.r; u.f2 = w.rh; u.f3 = w.p;
   k_rel_r<P, P64><<<bg, bb, 0, s>>>(u);
-  k_finish<R, 2, FIN_UPDATE><<<n, 256, 0, s>>>(u.ra, w.update_list, &w.ctl->n_update, n, (int)bg.x * (kBlasShape.sx / 32));
+  k_finish<typename SumOf<R>::T, 2, FIN_UPDATE><<<n, 256, 0, s>>>(u.ra, w.update_list, &w.ctl->n_update, n, (int)bg.x * (kBlasShape.sx / 32));
   k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n, nullptr, 0, 0);
   c->launches += 8;
 }

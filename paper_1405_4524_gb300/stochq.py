@@ -17,7 +17,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIBPATH = os.path.join(_HERE, "libstochq.so")
+# STOCHQ_LIBRARY selects another build of the library (a build variant such
+# as libstochq_sums64.so); by default the in-tree libstochq.so is loaded.
+LIBPATH = os.environ.get("STOCHQ_LIBRARY") or os.path.join(_HERE, "libstochq.so")
 
 SQ_F64, SQ_F32, SQ_F16 = 0, 1, 2
 SQ_HOST, SQ_DEVICE = 0, 1
@@ -116,6 +118,7 @@ _SIG = {
     "sq_tune_load": (_i, [_vp, C.c_char_p, C.POINTER(_i)]),
     "sq_status_string": (C.c_char_p, [_i]),
     "sq_last_error": (C.c_char_p, [_vp]),
+    "sq_inner_sum_bits": (_i, []),
 }
 for _name, (_res, _args) in _SIG.items():
     _f = getattr(_lib, _name)
@@ -172,6 +175,10 @@ def sq_status_string(status: int) -> str:
 
 def sq_last_error(ctx) -> str:
     return _lib.sq_last_error(ctx).decode()
+
+
+def sq_inner_sum_bits() -> int:
+    return int(_lib.sq_inner_sum_bits())
 
 
 def sq_default_params(**overrides) -> sq_solve_params:

@@ -272,7 +272,7 @@ def test_tuned_shapes_persist(tmp_path):
     try:
         n = 4
         psi = random_spinors(dims, n, 91)
-        run_dslash(s, 1, n, psi, psi, 0, sq.SQ_DS_CLOVER_INV, 0.0)  # the tuner's pick
+        run_dslash(s, 1, n, psi, psi, 0, 0, 0.0)  # the tuner's pick
         sq.sq_set_dslash_shape(s.ctx, 2, n, 1, (4, 2, 2, 2, 3))     # a set one
         want = {1: sq.sq_get_dslash_shape(s.ctx, 1, n), 2: sq.sq_get_dslash_shape(s.ctx, 2, n)}
         sq.sq_tune_save(s.ctx, path)
