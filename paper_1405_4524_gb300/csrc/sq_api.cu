@@ -145,14 +145,18 @@ sq_status find_clover(sq_ctx* c, double kappa, double csw, CloverSet** out) {
     return cuda_check(c, e, "clover allocation");
   }
   sq_status s = clover_build(c, cs, kappa, csw);
-  if (s == SQ_OK) {  // float-pair copies for the emulated-FP64 operator
-    launch_split_copy(cs.A64, cs.Adf, 2 * 36 * Vh, c->stream);
-    launch_split_copy(cs.Ainv64, cs.Ainvdf, 2 * 36 * Vh, c->stream);
-    c->launches += 2;
-    s = cuda_check(c, cudaGetLastError(), "clover copies");
-  }
+  c->launches += 2;
+  // one read-back for the norm bound and the error word
   int bits = 0;
-  if (s == SQ_OK) s = read_error_word(c, &bits);
+  unsigned long long hb = 0;
+  if (s == SQ_OK) {
+    e = cudaMemcpyAsync(&hb, c->d_bound, sizeof(hb), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    s = cuda_check(c, e, "clover build");
+  }
+  if (s == SQ_OK) memcpy(&cs.a_bound, &hb, sizeof(double));
   if (s == SQ_OK && (bits & ERRBIT_CLOVER))
     return set_error(c, SQ_ERR_CLOVER, "clover: a 6x6 block is singular for kappa=%g c_sw=%g", kappa, csw);
   if (s != SQ_OK) return s;
@@ -221,8 +225,9 @@ sq_status sq_create(sq_ctx** out, const int dims[4], int t_bc, void* cuda_stream
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_err, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_err, 16);  // error word at 0, clover bound at 8
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, 16);
+  c->d_bound = (unsigned long long*)((char*)c->d_err + 8);
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (c->stream) cudaStreamDestroy(c->stream);
@@ -244,7 +249,7 @@ sq_status sq_set_allocator(sq_ctx* c, sq_alloc_fn alloc, sq_free_fn free_fn, voi
   if ((!alloc) != (!free_fn)) return set_error(c, SQ_ERR_ARG, "sq_set_allocator: give both callbacks or neither");
   bool held = c->U64 || c->U32 || c->stoch_part || c->ws.base || c->batch;
   for (auto& cs : c->clover) held = held || cs.A64 || cs.Ainv64 || cs.Ainv32 || cs.Adf || cs.Ainvdf;
-  held = held || c->Udf;
+  held = held || c->Udf || c->cloverF;
   if (held) return set_error(c, SQ_ERR_STATE, "sq_set_allocator: the context already holds device buffers");
   c->mem.alloc = alloc;
   c->mem.free = free_fn;
@@ -260,6 +265,7 @@ sq_status sq_destroy(sq_ctx* c) {
   dev_free(c->mem, c->U64, 2 * 4 * 9 * (size_t)c->Vh * sizeof(double2));
   dev_free(c->mem, c->Udf, 2 * 4 * 9 * (size_t)c->Vh * sizeof(float4));
   dev_free(c->mem, c->U32, gauge32_bytes(c, c->recon));
+  dev_free(c->mem, c->cloverF, clover_scratch_bytes(c));
   cudaFree(c->d_err);
   dev_free(c->mem, c->stoch_part, c->stoch_cap);
   cudaEventDestroy(c->ev);
@@ -299,8 +305,7 @@ sq_status sq_load_gauge(sq_ctx* c, const double* U, int recon, int where) {
     dU = stage;
   }
   s = gauge_convert(c, dU);
-  launch_split_copy(c->U64, c->Udf, 2 * 4 * 9 * Vh, c->stream);  // for the emulated-FP64 operator
-  c->launches += 2;
+  c->launches += 1;
   if (stage) cudaFreeAsync(stage, c->stream);
   int bits = 0;
   if (s == SQ_OK) s = read_error_word(c, &bits);

@@ -41,18 +41,6 @@ struct DfArgs {
   RedArgs ra;
 };
 
-__device__ __forceinline__ void load_spinor_df(const Field& f, int k, int cb, cdf v[12]) {
-  const double2* p = (const double2*)f.data + (size_t)k * 12 * f.Vh + cb;
-#pragma unroll
-  for (int c = 0; c < 12; c++) v[c] = cdf_split(__ldg(p + (size_t)c * f.Vh));
-}
-
-__device__ __forceinline__ void store_spinor_df(const Field& f, int k, int cb, const cdf v[12]) {
-  double2* p = (double2*)f.data + (size_t)k * 12 * f.Vh + cb;
-#pragma unroll
-  for (int c = 0; c < 12; c++) p[(size_t)c * f.Vh] = double2_of(v[c]);
-}
-
 __device__ __forceinline__ void load_link_df(const float4* base, int Vh, int p, int mu, int cb, cdf u[9]) {
   const float4* q = base + ((size_t)(p * 4 + mu) * 9) * Vh + cb;
 #pragma unroll
@@ -65,113 +53,102 @@ __device__ __forceinline__ cdf cpm(cdf acc, cdf b) {
   return S > 0 ? cadd(acc, b) : csub(acc, b);
 }
 
-// h = psi_up + SIGN * B_mu psi_dn (the projection of sq_hop.cuh in df32)
-template <int MU, int SIGN>
-__device__ __forceinline__ void project_df(const cdf v[12], cdf h[6]) {
-#pragma unroll
-  for (int c = 0; c < 3; c++) {
-    cdf d0, d1;
-    if (MU == 0) {  // B = [[0, i], [i, 0]]
-      d0 = citimes(v[9 + c]);
-      d1 = citimes(v[6 + c]);
-    } else if (MU == 1) {  // B = [[0, -1], [1, 0]]
-      d0 = cdf{df_neg(v[9 + c].re), df_neg(v[9 + c].im)};
-      d1 = v[6 + c];
-    } else if (MU == 2) {  // B = [[i, 0], [0, -i]]
-      d0 = citimes(v[6 + c]);
-      d1 = cdf{v[9 + c].im, df_neg(v[9 + c].re)};
-    } else {  // B = 1
-      d0 = v[6 + c];
-      d1 = v[9 + c];
-    }
-    h[c] = cpm<SIGN>(v[c], d0);
-    h[3 + c] = cpm<SIGN>(v[3 + c], d1);
-  }
+// flip the sign of z when neg (runtime, exact)
+__device__ __forceinline__ cdf csign(cdf z, bool neg) {
+  const float s = neg ? -1.f : 1.f;
+  return cdf{df{s * z.re.h, s * z.re.l}, df{s * z.im.h, s * z.im.l}};
 }
 
-// acc_up += w ; acc_dn += SIGN * B_mu^+ w
-template <int MU, int SIGN>
-__device__ __forceinline__ void accum_df(cdf acc[12], const cdf w[6]) {
+// Two threads per site and source: lanes l and l ^ 16 of a warp, j = the
+// upper lane bit. In each hop thread j forms row j of the spin projection,
+// h_j = psi_j + SIGN c psi_dn, multiplies it by the link and scatters it
+// back: w_j to spin j and SIGN conj(c) w_j to spin dn, where (rows of B_mu
+// of sq_hop.cuh, chiral basis)
+//   mu = 0: dn = 3 - j, c = i;   mu = 1: dn = 3 - j, c = -1 (j = 0), +1 (j = 1)
+//   mu = 2: dn = 2 + j, c = i (j = 0), -i (j = 1);   mu = 3: dn = 2 + j, c = 1.
+// Spin 3 - j is the partner's own lower spin: those contributions are kept
+// apart and handed over by one shuffle after the eight hops. Each thread then
+// holds one chirality block (spins 2j, 2j + 1) for the clover term, the xpay
+// and the store, so a thread carries half the registers and half the code
+// path of a whole site.
+
+// three colour components of spin s of source k at site cb
+__device__ __forceinline__ void load_spin_df(const Field& f, int k, int cb, int s, cdf v[3]) {
+  const double2* p = (const double2*)f.data + ((size_t)k * 12 + 3 * s) * f.Vh + cb;
 #pragma unroll
-  for (int c = 0; c < 3; c++) {
-    acc[c] = cadd(acc[c], w[c]);
-    acc[3 + c] = cadd(acc[3 + c], w[3 + c]);
-    cdf e0, e1;
-    if (MU == 0) {  // B^+ = [[0, -i], [-i, 0]]
-      e0 = cdf{w[3 + c].im, df_neg(w[3 + c].re)};
-      e1 = cdf{w[c].im, df_neg(w[c].re)};
-    } else if (MU == 1) {  // B^+ = [[0, 1], [-1, 0]]
-      e0 = w[3 + c];
-      e1 = cdf{df_neg(w[c].re), df_neg(w[c].im)};
-    } else if (MU == 2) {  // B^+ = [[-i, 0], [0, i]]
-      e0 = cdf{w[c].im, df_neg(w[c].re)};
-      e1 = citimes(w[3 + c]);
+  for (int c = 0; c < 3; c++) v[c] = cdf_split(__ldg(p + (size_t)c * f.Vh));
+}
+
+// the six components of chirality block ch (spins 2 ch, 2 ch + 1)
+__device__ __forceinline__ void load_block_df(const Field& f, int k, int cb, int ch, cdf v[6]) {
+  const double2* p = (const double2*)f.data + ((size_t)k * 12 + 6 * ch) * f.Vh + cb;
+#pragma unroll
+  for (int c = 0; c < 6; c++) v[c] = cdf_split(__ldg(p + (size_t)c * f.Vh));
+}
+
+__device__ __forceinline__ void store_block_df(const Field& f, int k, int cb, int ch, const cdf v[6]) {
+  double2* p = (double2*)f.data + ((size_t)k * 12 + 6 * ch) * f.Vh + cb;
+#pragma unroll
+  for (int c = 0; c < 6; c++) p[(size_t)c * f.Vh] = double2_of(v[c]);
+}
+
+// w = U h or U^+ h for one colour vector
+template <bool DAG>
+__device__ __forceinline__ void mv3_df(const cdf u[9], const cdf h[3], cdf w[3]) {
+  const cdf z{df{0.f, 0.f}, df{0.f, 0.f}};
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    cdf r;
+    if (DAG) {
+      r = cjfma_df(u[a], h[0], z);
+      r = cjfma_df(u[3 + a], h[1], r);
+      r = cjfma_df(u[6 + a], h[2], r);
     } else {
-      e0 = w[c];
-      e1 = w[3 + c];
+      r = cfma_df(u[3 * a], h[0], z);
+      r = cfma_df(u[3 * a + 1], h[1], r);
+      r = cfma_df(u[3 * a + 2], h[2], r);
     }
-    acc[6 + c] = cpm<SIGN>(acc[6 + c], e0);
-    acc[9 + c] = cpm<SIGN>(acc[9 + c], e1);
+    w[a] = r;
   }
 }
 
-// w[s] = U h[s]
-__device__ __forceinline__ void mv_df(const cdf u[9], const cdf h[6], cdf w[6]) {
-  const cdf z{df{0.f, 0.f}, df{0.f, 0.f}};
+// One hop (MU, forward or backward) of thread j: up += w_j; dn_part (mu 0, 1)
+// or dn_own (mu 2, 3) += SIGN conj(c) w_j
+template <int MU, bool FWD>
+__device__ __forceinline__ void hop_pair_df(const DfArgs& a, int k, int cb, Coord c, int j, cdf up[3],
+                                            cdf dn_part[3], cdf dn_own[3]) {
+  constexpr int SIGN = FWD ? -1 : +1;
+  const Coord nb = step(a.g, c, MU, FWD ? +1 : -1);
+  const int ncb = cb_of(a.g, nb.x, nb.y, nb.z, nb.t);
+  const int dn = MU < 2 ? 3 - j : 2 + j;
+  const bool flip = (MU == 1 && j == 0) || (MU == 2 && j == 1);  // the j-dependent sign of c
+  cdf vu[3], vd[3], h[3], w[3], u[9];
+  load_spin_df(a.in, k, ncb, j, vu);
+  load_spin_df(a.in, k, ncb, dn, vd);
 #pragma unroll
-  for (int s = 0; s < 2; s++)
+  for (int q = 0; q < 3; q++) {
+    const cdf d = csign(MU == 0 || MU == 2 ? citimes(vd[q]) : vd[q], flip);
+    h[q] = cpm<SIGN>(vu[q], d);
+  }
+  load_link_df(a.links, a.g.Vh, FWD ? a.p_out : 1 - a.p_out, MU, FWD ? cb : ncb, u);
+  mv3_df<!FWD>(u, h, w);
+  if (MU == 3 && a.g.tbc < 0 && (FWD ? c.t == a.g.T - 1 : c.t == 0)) {
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-      cdf r = cfma_df(u[3 * a], h[3 * s], z);
-      r = cfma_df(u[3 * a + 1], h[3 * s + 1], r);
-      r = cfma_df(u[3 * a + 2], h[3 * s + 2], r);
-      w[3 * s + a] = r;
-    }
+    for (int q = 0; q < 3; q++) w[q] = cdf{df_neg(w[q].re), df_neg(w[q].im)};
+  }
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+    up[q] = cadd(up[q], w[q]);
+    // conj(c) w, with conj(i) = -i
+    const cdf e = csign(MU == 0 || MU == 2 ? cdf{w[q].im, df_neg(w[q].re)} : w[q], flip);
+    if (MU < 2) dn_part[q] = cpm<SIGN>(dn_part[q], e);
+    else dn_own[q] = cpm<SIGN>(dn_own[q], e);
+  }
 }
 
-// w[s] = U^+ h[s]
-__device__ __forceinline__ void mv_dag_df(const cdf u[9], const cdf h[6], cdf w[6]) {
-  const cdf z{df{0.f, 0.f}, df{0.f, 0.f}};
-#pragma unroll
-  for (int s = 0; s < 2; s++)
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-      cdf r = cjfma_df(u[a], h[3 * s], z);
-      r = cjfma_df(u[3 + a], h[3 * s + 1], r);
-      r = cjfma_df(u[6 + a], h[3 * s + 2], r);
-      w[3 * s + a] = r;
-    }
-}
-
-template <int MU>
-__device__ __forceinline__ void hop_dir_df(const DfArgs& a, int k, int cb, Coord c, cdf acc[12]) {
-  {  // forward: (1 - g_mu) U_mu(x) psi(x + mu)
-    const Coord nb = step(a.g, c, MU, +1);
-    cdf v[12], h[6], w[6], u[9];
-    load_spinor_df(a.in, k, cb_of(a.g, nb.x, nb.y, nb.z, nb.t), v);
-    project_df<MU, -1>(v, h);
-    load_link_df(a.links, a.g.Vh, a.p_out, MU, cb, u);
-    mv_df(u, h, w);
-    if (MU == 3 && c.t == a.g.T - 1 && a.g.tbc < 0) {
-#pragma unroll
-      for (int j = 0; j < 6; j++) w[j] = cdf{df_neg(w[j].re), df_neg(w[j].im)};
-    }
-    accum_df<MU, -1>(acc, w);
-  }
-  {  // backward: (1 + g_mu) U_mu(x - mu)^+ psi(x - mu)
-    const Coord nb = step(a.g, c, MU, -1);
-    const int ncb = cb_of(a.g, nb.x, nb.y, nb.z, nb.t);
-    cdf v[12], h[6], w[6], u[9];
-    load_spinor_df(a.in, k, ncb, v);
-    project_df<MU, +1>(v, h);
-    load_link_df(a.links, a.g.Vh, 1 - a.p_out, MU, ncb, u);
-    mv_dag_df(u, h, w);
-    if (MU == 3 && c.t == 0 && a.g.tbc < 0) {
-#pragma unroll
-      for (int j = 0; j < 6; j++) w[j] = cdf{df_neg(w[j].re), df_neg(w[j].im)};
-    }
-    accum_df<MU, +1>(acc, w);
-  }
+__device__ __forceinline__ cdf shfl16(cdf v) {
+  return cdf{df{__shfl_xor_sync(0xffffffffu, v.re.h, 16), __shfl_xor_sync(0xffffffffu, v.re.l, 16)},
+             df{__shfl_xor_sync(0xffffffffu, v.im.h, 16), __shfl_xor_sync(0xffffffffu, v.im.l, 16)}};
 }
 
 // w = B v for one packed Hermitian 6x6 block held as 18 cdf: the six real
@@ -196,107 +173,119 @@ __device__ __forceinline__ void herm6_apply_df(const float4* blk, int Vh, const 
   }
 }
 
-__device__ __forceinline__ void clover_apply_df(const float4* clov, int Vh, int p, int cb, cdf v[12]) {
-  cdf w[6];
-  const float4* b0 = clov + (size_t)p * 36 * Vh + cb;
-  herm6_apply_df(b0, Vh, v, w);
-#pragma unroll
-  for (int j = 0; j < 6; j++) v[j] = w[j];
-  herm6_apply_df(b0 + (size_t)18 * Vh, Vh, v + 6, w);
-#pragma unroll
-  for (int j = 0; j < 6; j++) v[6 + j] = w[j];
-}
+constexpr int kDfSites = 64;      // sites per CTA: 128 threads, two per site
+constexpr int kDfMinBlocks = 6;   // resident CTAs per SM the register budget is cut for
 
 template <int CLOV, int XPAY, int XFIRST, int FIN, int OUT2>
-__global__ void __launch_bounds__(64) k_dslash_df(const DfArgs a) {
+__global__ void __launch_bounds__(2 * kDfSites, kDfMinBlocks) k_dslash_df(const DfArgs a) {
   const int sb = blockIdx.x / a.nrb, rb = blockIdx.x - (blockIdx.x / a.nrb) * a.nrb;
   const int cnt = a.list ? *a.count : a.n;
-  const int cb = sb * blockDim.x + threadIdx.x;
-  for (int slot0 = rb * blockDim.y; slot0 < cnt; slot0 += a.nrb * blockDim.y) {
-    const int slot = slot0 + threadIdx.y;
-    const int k = slot < cnt ? (a.list ? a.list[slot] : slot) : -1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = lane >> 4;  // row of the projection; at the end, the chirality block
+  const int cb = sb * kDfSites + warp * 16 + (lane & 15);
+  const bool site_ok = cb < a.g.Vh;
+  for (int slot = rb; slot < cnt; slot += a.nrb) {  // uniform over the CTA
+    const int k = a.list ? a.list[slot] : slot;
     double red = 0.0;
-    if (k >= 0 && cb < a.g.Vh) {
+    cdf blk[6];
+    {
       const df z{0.f, 0.f};
-      cdf acc[12];
+      cdf up[3], dn_part[3], dn_own[3];
 #pragma unroll
-      for (int j = 0; j < 12; j++) acc[j] = cdf{z, z};
-      const Coord c = cb_coords(a.g, cb, a.p_out);
-      hop_dir_df<0>(a, k, cb, c, acc);
-      hop_dir_df<1>(a, k, cb, c, acc);
-      hop_dir_df<2>(a, k, cb, c, acc);
-      hop_dir_df<3>(a, k, cb, c, acc);
+      for (int q = 0; q < 3; q++) up[q] = dn_part[q] = dn_own[q] = cdf{z, z};
+      if (site_ok) {
+        const Coord c = cb_coords(a.g, cb, a.p_out);
+        hop_pair_df<0, true>(a, k, cb, c, j, up, dn_part, dn_own);
+        hop_pair_df<0, false>(a, k, cb, c, j, up, dn_part, dn_own);
+        hop_pair_df<1, true>(a, k, cb, c, j, up, dn_part, dn_own);
+        hop_pair_df<1, false>(a, k, cb, c, j, up, dn_part, dn_own);
+        hop_pair_df<2, true>(a, k, cb, c, j, up, dn_part, dn_own);
+        hop_pair_df<2, false>(a, k, cb, c, j, up, dn_part, dn_own);
+        hop_pair_df<3, true>(a, k, cb, c, j, up, dn_part, dn_own);
+        hop_pair_df<3, false>(a, k, cb, c, j, up, dn_part, dn_own);
+      }
+      // lower spin 2 + j complete with the partner's part; then regroup by
+      // chirality: thread 0 keeps spins 0, 1 and thread 1 spins 2, 3
+#pragma unroll
+      for (int q = 0; q < 3; q++) dn_own[q] = cadd(dn_own[q], shfl16(dn_part[q]));
+#pragma unroll
+      for (int q = 0; q < 3; q++) {
+        const cdf got = shfl16(j ? up[q] : dn_own[q]);  // 0 hands over spin 2, 1 spin 1
+        blk[q] = j ? got : up[q];
+        blk[3 + q] = j ? dn_own[q] : got;
+      }
+    }
+    if (site_ok) {
+      const size_t cofs = ((size_t)a.p_out * 36 + 18 * j) * a.g.Vh + cb;
       if (XFIRST) {
-        cdf xv[12];
-        load_spinor_df(a.x, k, cb, xv);
+        cdf xv[6], w[6];
+        load_block_df(a.x, k, cb, j, xv);
 #pragma unroll
-        for (int j = 0; j < 12; j++) acc[j] = cdf{df_fma(a.a, acc[j].re, xv[j].re), df_fma(a.a, acc[j].im, xv[j].im)};
-        if (OUT2) store_spinor_df(a.out2, k, cb, acc);
-        clover_apply_df(a.clov, a.g.Vh, a.p_out, cb, acc);
+        for (int q = 0; q < 6; q++) blk[q] = cdf{df_fma(a.a, blk[q].re, xv[q].re), df_fma(a.a, blk[q].im, xv[q].im)};
+        if (OUT2) store_block_df(a.out2, k, cb, j, blk);
+        herm6_apply_df(a.clov + cofs, a.g.Vh, blk, w);
+#pragma unroll
+        for (int q = 0; q < 6; q++) blk[q] = w[q];
       } else {
-        if (CLOV) clover_apply_df(a.clov, a.g.Vh, a.p_out, cb, acc);
-        if (XPAY) {
-          cdf xv[12];
-          load_spinor_df(a.x, k, cb, xv);
+        if (CLOV) {
+          cdf w[6];
+          herm6_apply_df(a.clov + cofs, a.g.Vh, blk, w);
 #pragma unroll
-          for (int j = 0; j < 12; j++)
-            acc[j] = cdf{df_fma(a.a, acc[j].re, xv[j].re), df_fma(a.a, acc[j].im, xv[j].im)};
+          for (int q = 0; q < 6; q++) blk[q] = w[q];
+        }
+        if (XPAY) {
+          cdf xv[6];
+          load_block_df(a.x, k, cb, j, xv);
+#pragma unroll
+          for (int q = 0; q < 6; q++)
+            blk[q] = cdf{df_fma(a.a, blk[q].re, xv[q].re), df_fma(a.a, blk[q].im, xv[q].im)};
         }
       }
-      store_spinor_df(a.out, k, cb, acc);
+      store_block_df(a.out, k, cb, j, blk);
       if (FIN == FIN_TRUE) {
         // ||out||^2 to FP32 accuracy (a residual norm). A residual is the
         // cancellation of nearly equal terms, after which the leading float
         // of a pair need not carry the value: square the rounded h + l.
         typedef SumOf<float>::T S;
-        S q = 0;
+        S q2 = 0;
 #pragma unroll
-        for (int j = 0; j < 12; j++) {
-          const S re = acc[j].re.h + acc[j].re.l, im = acc[j].im.h + acc[j].im.l;
-          q = fma(re, re, fma(im, im, q));
+        for (int q = 0; q < 6; q++) {
+          const S re = blk[q].re.h + blk[q].re.l, im = blk[q].im.h + blk[q].im.l;
+          q2 = fma(re, re, fma(im, im, q2));
         }
-        red = (double)q;
+        red = (double)q2;
       }
     }
-    if (FIN == FIN_TRUE) {
+    if (FIN == FIN_TRUE) {  // both threads of a site sit in one warp
       double r1[1] = {red};
-      warp_partials<1>(a.ra, r1, k, sb * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5));
+      warp_partials<1>(a.ra, r1, k, sb * (2 * kDfSites / 32) + warp);
     }
   }
 }
 
-// out = c1 x + c2 (C in), C = A or A^{-1} (pre-split blocks); x may be absent
+// out = c1 x + c2 (C in), C = A or A^{-1} (pre-split blocks); x may be
+// absent. The two chirality blocks are independent: a CTA of 128 threads
+// takes 64 sites, warps 0-1 block 0 and warps 2-3 block 1.
 __global__ void __launch_bounds__(128) k_clover_df(int Vh, Field out, Field x, Field in, const float4* C, int parity,
                                                    df c1, df c2, int n) {
-  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ch = threadIdx.x >> 6;
+  const int cb = blockIdx.x * 64 + (threadIdx.x & 63);
   const int k = blockIdx.y;
   if (cb >= Vh || k >= n) return;
-  cdf v[12];
-  load_spinor_df(in, k, cb, v);
-  clover_apply_df(C, Vh, parity, cb, v);
+  cdf v[6], w[6];
+  load_block_df(in, k, cb, ch, v);
+  herm6_apply_df(C + ((size_t)parity * 36 + 18 * ch) * Vh + cb, Vh, v, w);
   if (x.data) {
-    cdf xv[12];
-    load_spinor_df(x, k, cb, xv);
+    load_block_df(x, k, cb, ch, v);
     const df z{0.f, 0.f};
 #pragma unroll
-    for (int j = 0; j < 12; j++) {
-      v[j] = cdf{df_fma(c2, v[j].re, df_fma(c1, xv[j].re, z)), df_fma(c2, v[j].im, df_fma(c1, xv[j].im, z))};
-    }
+    for (int j = 0; j < 6; j++)
+      w[j] = cdf{df_fma(c2, w[j].re, df_fma(c1, v[j].re, z)), df_fma(c2, w[j].im, df_fma(c1, v[j].im, z))};
   } else {
 #pragma unroll
-    for (int j = 0; j < 12; j++) v[j] = cscale(c2, v[j]);
+    for (int j = 0; j < 6; j++) w[j] = cscale(c2, w[j]);
   }
-  store_spinor_df(out, k, cb, v);
-}
-
-// float4 (hi.re, hi.im, lo.re, lo.im) copies of n double2 values, rounded
-// splits in FP64 (once per gauge load or clover build)
-__global__ void k_split_copy(const double2* in, float4* out, size_t n) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double2 d = in[i];
-    const float hr = __double2float_rn(d.x), hi = __double2float_rn(d.y);
-    out[i] = make_float4(hr, hi, __double2float_rn(d.x - (double)hr), __double2float_rn(d.y - (double)hi));
-  }
+  store_block_df(out, k, cb, ch, w);
 }
 
 // ---------------------------------------------------------------------------
@@ -307,14 +296,9 @@ static df df_host(double v) {
   return df{h, (float)(v - (double)h)};
 }
 
-void launch_split_copy(const double2* in, float4* out, size_t n, cudaStream_t s) {
-  const unsigned grid = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
-  k_split_copy<<<grid > 0 ? grid : 1, 256, 0, s>>>(in, out, n);
-}
-
 void launch_clover_df(const sq_ctx* c, const CloverSet& cs, Field out, Field x, Field in, int parity, double c1,
                       double c2, int which, int n, cudaStream_t s) {
-  dim3 grid((c->Vh + 127) / 128, n);
+  dim3 grid((c->Vh + 63) / 64, n);
   k_clover_df<<<grid, 128, 0, s>>>(c->Vh, out, x, in, which ? cs.Ainvdf : cs.Adf, parity, df_host(c1), df_host(c2),
                                    n);
 }
@@ -342,11 +326,10 @@ bool launch_dslash_df(const sq_ctx* c, const DslashCall& d, Field out2, int xfir
   a.count = d.count;
   a.n = d.n;
   a.ra = d.ra;
-  const int sx = 64, ry = 1;
-  a.nsb = (c->Vh + sx - 1) / sx;
-  a.nrb = (d.n + ry - 1) / ry;
-  dim3 block(sx, ry), grid((unsigned)a.nsb * (unsigned)a.nrb);
-  *nparts = a.nsb * (sx / 32);
+  a.nsb = (c->Vh + kDfSites - 1) / kDfSites;
+  a.nrb = d.n;
+  dim3 block(2 * kDfSites), grid((unsigned)a.nsb * (unsigned)a.nrb);
+  *nparts = a.nsb * (2 * kDfSites / 32);
   const int m = (d.clover ? 1 : 0) | (d.xpay ? 2 : 0);
   if (xfirst) {
     if (!d.clover || !d.xpay || d.fin != FIN_NONE) return false;

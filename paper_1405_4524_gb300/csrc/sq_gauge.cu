@@ -13,6 +13,7 @@
 // with G = the matching signed sums of Fhat.
 #include <cstring>
 
+#include "sq_df32.cuh"
 #include "sq_internal.h"
 
 namespace sq {
@@ -20,7 +21,10 @@ namespace sq {
 // ---------------------------------------------------------------------------
 // layout conversion
 // ---------------------------------------------------------------------------
-__global__ void k_gauge_convert(Geom g, const double* lex, double2* U64, void* U32, int recon, int* err) {
+// lex -> U64 (FP64), U32 (reconstruct-12 or -18 FP32) and Udf (each FP64
+// element as a rounded float pair for the emulated-FP64 operator), with the
+// finiteness and SU(3) checks
+__global__ void k_gauge_convert(Geom g, const double* lex, double2* U64, void* U32, float4* Udf, int recon, int* err) {
   const long long V = 2LL * g.Vh;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= V * 4) return;
@@ -67,7 +71,12 @@ __global__ void k_gauge_convert(Geom g, const double* lex, double2* U64, void* U
   const size_t base9 = (size_t)(p * 4 + mu) * 9;
   const size_t base3 = (size_t)(p * 4 + mu) * 3;
 #pragma unroll
-  for (int e = 0; e < 9; e++) U64[(base9 + e) * g.Vh + cb] = u[e];
+  for (int e = 0; e < 9; e++) {
+    U64[(base9 + e) * g.Vh + cb] = u[e];
+    const float hr = __double2float_rn(u[e].x), hi = __double2float_rn(u[e].y);
+    Udf[(base9 + e) * g.Vh + cb] =
+        make_float4(hr, hi, __double2float_rn(u[e].x - (double)hr), __double2float_rn(u[e].y - (double)hi));
+  }
   if (recon == 12) {
     float4* q = (float4*)U32;
 #pragma unroll
@@ -84,7 +93,7 @@ __global__ void k_gauge_convert(Geom g, const double* lex, double2* U64, void* U
 sq_status gauge_convert(sq_ctx* c, const double* dev_lex) {
   Geom g = geom_of(c);
   long long n = (long long)c->V * 4;
-  k_gauge_convert<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(g, dev_lex, c->U64, c->U32, c->recon,
+  k_gauge_convert<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(g, dev_lex, c->U64, c->U32, c->Udf, c->recon,
                                                                       c->d_err);
   return cuda_check(c, cudaGetLastError(), "gauge conversion launch");
 }
@@ -96,93 +105,80 @@ struct M3 {
   cx<double> e[9];
 };
 
-__device__ __forceinline__ M3 load_link(const Geom& g, const double2* U64, int mu, Coord c) {
-  M3 m;
-  const int p = (c.x + c.y + c.z + c.t) & 1;
-  const int cb = cb_of(g, c.x, c.y, c.z, c.t);
-  const double2* q = U64 + ((size_t)(p * 4 + mu) * 9) * g.Vh + cb;
+// ---------------------------------------------------------------------------
+// clover leaves in double-FP32 (sq_df32.cuh) on the FP32 pipe
+// ---------------------------------------------------------------------------
+struct M3d {
+  cdf e[9];
+};
+
+// U_mu(y), or U_mu(y)^+ when dag, from the pre-split link copy
+__device__ __forceinline__ M3d load_link_df3(const Geom& g, const float4* Udf, int mu, Coord y, bool dag) {
+  const int p = (y.x + y.y + y.z + y.t) & 1;
+  const float4* q = Udf + ((size_t)(p * 4 + mu) * 9) * g.Vh + cb_of(g, y.x, y.y, y.z, y.t);
+  const float si = dag ? -1.f : 1.f;
+  M3d m;
 #pragma unroll
-  for (int e = 0; e < 9; e++) {
-    double2 v = q[(size_t)e * g.Vh];
-    m.e[e] = mk(v.x, v.y);
-  }
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      const cdf v = cdf_of(__ldg(q + (size_t)(dag ? j * 3 + i : i * 3 + j) * g.Vh));
+      m.e[i * 3 + j] = cdf{v.re, df{si * v.im.h, si * v.im.l}};
+    }
   return m;
 }
 
-// op: 0 = A B, 1 = A B^+, 2 = A^+ B
-template <int OP>
-__device__ __forceinline__ M3 mm(const M3& A, const M3& B) {
-  M3 C;
+__device__ __forceinline__ M3d mm_df3(const M3d& A, const M3d& B) {
+  const cdf z{df{0.f, 0.f}, df{0.f, 0.f}};
+  M3d C;
 #pragma unroll
   for (int i = 0; i < 3; i++)
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-      cx<double> s = zero<double>();
-#pragma unroll
-      for (int k = 0; k < 3; k++) {
-        if (OP == 0) s = cfma(A.e[i * 3 + k], B.e[k * 3 + j], s);
-        if (OP == 1) s = s + A.e[i * 3 + k] * conj(B.e[j * 3 + k]);
-        if (OP == 2) s = cjfma(A.e[k * 3 + i], B.e[k * 3 + j], s);
-      }
-      C.e[i * 3 + j] = s;
+      cdf r = cfma_df(A.e[i * 3], B.e[j], z);
+      r = cfma_df(A.e[i * 3 + 1], B.e[3 + j], r);
+      C.e[i * 3 + j] = cfma_df(A.e[i * 3 + 2], B.e[6 + j], r);
     }
   return C;
 }
 
-__device__ __forceinline__ M3 dag(const M3& A) {
-  M3 C;
-#pragma unroll
-  for (int i = 0; i < 3; i++)
-#pragma unroll
-    for (int j = 0; j < 3; j++) C.e[i * 3 + j] = conj(A.e[j * 3 + i]);
-  return C;
-}
+// The four clover leaves of the (mu, nu) plane at x, each the product of
+// the four links around a plaquette with a corner at x, walked from x:
+//   x, x+mu, x+mu+nu, x+nu;   x, x+nu, x-mu+nu, x-mu;
+//   x, x-mu, x-mu-nu, x-nu;   x, x-nu, x-nu+mu, x+mu.
+// Factor f of leaf l is U_d(x + a_mu mu + a_nu nu), daggered when the walk
+// goes against d: {d (0 = mu, 1 = nu), a_mu, a_nu, dagger}.
+__constant__ signed char kLeaf[4][4][4] = {
+    {{0, 0, 0, 0}, {1, 1, 0, 0}, {0, 0, 1, 1}, {1, 0, 0, 1}},
+    {{1, 0, 0, 0}, {0, -1, 1, 1}, {1, -1, 0, 1}, {0, -1, 0, 0}},
+    {{0, -1, 0, 1}, {1, -1, -1, 1}, {0, -1, -1, 0}, {1, 0, -1, 0}},
+    {{1, 0, -1, 1}, {0, 0, -1, 0}, {1, 1, -1, 0}, {0, 0, 0, 1}}};
 
-// Fhat_mu_nu(x): clover leaves, all in the (mu, then nu) orientation
-__device__ M3 fhat(const Geom& g, const double2* U64, Coord x, int mu, int nu) {
-  Coord xpm = step(g, x, mu, +1), xpn = step(g, x, nu, +1);
-  Coord xmm = step(g, x, mu, -1), xmn = step(g, x, nu, -1);
-  Coord xmmpn = step(g, xmm, nu, +1), xmmmn = step(g, xmm, nu, -1), xmnpm = step(g, xmn, mu, +1);
-  M3 Um_x = load_link(g, U64, mu, x), Un_x = load_link(g, U64, nu, x);
-  M3 Q;
-  // x -> x+mu -> x+mu+nu -> x+nu -> x
-  M3 l = mm<0>(Um_x, load_link(g, U64, nu, xpm));
-  l = mm<1>(l, load_link(g, U64, mu, xpn));
-  l = mm<1>(l, Un_x);
-  Q = l;
-  // x -> x+nu -> x-mu+nu -> x-mu -> x
-  M3 Um_xmm = load_link(g, U64, mu, xmm);
-  l = mm<1>(Un_x, load_link(g, U64, mu, xmmpn));
-  l = mm<1>(l, load_link(g, U64, nu, xmm));
-  l = mm<0>(l, Um_xmm);
+// Q = the sum of the four leaves (double-FP32 products: every product of
+// leading parts exact, trailing parts and cross terms in FP32; about 2^-44
+// of the O(1) link products per entry), rounded to FP64
+__device__ void clover_leaves(const Geom& g, const float4* Udf, Coord x, int mu, int nu, cx<double> Q[9]) {
 #pragma unroll
-  for (int e = 0; e < 9; e++) Q.e[e] = Q.e[e] + l.e[e];
-  // x -> x-mu -> x-mu-nu -> x-nu -> x
-  M3 Un_xmn = load_link(g, U64, nu, xmn);
-  l = mm<2>(Um_xmm, dag(load_link(g, U64, nu, xmmmn)));
-  l = mm<0>(l, load_link(g, U64, mu, xmmmn));
-  l = mm<0>(l, Un_xmn);
-#pragma unroll
-  for (int e = 0; e < 9; e++) Q.e[e] = Q.e[e] + l.e[e];
-  // x -> x-nu -> x-nu+mu -> x+mu -> x
-  l = mm<2>(Un_xmn, load_link(g, U64, mu, xmn));
-  l = mm<0>(l, load_link(g, U64, nu, xmnpm));
-  l = mm<1>(l, Um_x);
-#pragma unroll
-  for (int e = 0; e < 9; e++) Q.e[e] = Q.e[e] + l.e[e];
-  M3 F;
-#pragma unroll
-  for (int i = 0; i < 3; i++)
-#pragma unroll
-    for (int j = 0; j < 3; j++) {
-      cx<double> a = Q.e[i * 3 + j], b = conj(Q.e[j * 3 + i]);
-      F.e[i * 3 + j] = 0.125 * (a - b);
+  for (int e = 0; e < 9; e++) Q[e] = zero<double>();
+#pragma unroll 1
+  for (int l = 0; l < 4; l++) {
+    M3d acc;
+#pragma unroll 1
+    for (int f = 0; f < 4; f++) {
+      const signed char* t = kLeaf[l][f];
+      Coord y = x;
+      if (t[1]) y = step(g, y, mu, t[1]);
+      if (t[2]) y = step(g, y, nu, t[2]);
+      const M3d W = load_link_df3(g, Udf, t[0] ? nu : mu, y, t[3] != 0);
+      if (f == 0) acc = W;
+      else acc = mm_df3(acc, W);
     }
-  cx<double> tr3 = (1.0 / 3.0) * (F.e[0] + F.e[4] + F.e[8]);
-  F.e[0] = F.e[0] - tr3;
-  F.e[4] = F.e[4] - tr3;
-  F.e[8] = F.e[8] - tr3;
-  return F;
+#pragma unroll
+    for (int e = 0; e < 9; e++) {
+      const double2 v = double2_of(acc.e[e]);
+      Q[e] = Q[e] + mk(v.x, v.y);
+    }
+  }
 }
 
 // Gauss-Jordan inverse of a 6x6 complex matrix with partial pivoting.
@@ -317,46 +313,76 @@ __device__ bool herm6_inverse_ldl(const double a[36], double out[36]) {
   return true;
 }
 
-// Clover build, S sites per CTA in two phases.
-// Phase 1, three threads per site: thread q computes the field strengths of
-// two planes and their chirality combinations (q = 0: G3 from F01, F23;
-// q = 1: G2 from F02, F13; q = 2: G1 from F12, F03) into shared memory.
-// Phase 2, two threads per site: chiral block ch forms
-// A = 1 + i kc [[G3, G1 - i G2], [G1 + i G2, -G3]] packed, bounds its norm,
-// inverts it and writes A, A^{-1} (FP64) and the FP32 / FP16 copies.
+// Clover build in two kernels.
+// k_clover_F, one thread per site and plane (blockIdx.y = plane 01, 02, 03,
+// 12, 13, 23): Fhat = (Q - Q^+)/8 minus its trace/3 in FP64 from the leaves,
+// to F[plane][9][V] (lexicographic site index).
+// k_clover, two threads per site (chiral block ch): the G combinations of
+// the six planes into shared memory, then
+// A = 1 + i kc [[G3, G1 - i G2], [G1 + i G2, -G3]] packed, its norm bound,
+// its inverse, and A, A^{-1} (FP64) and the FP32 A^{-1} copy written.
 constexpr int kCloverSites = 32;
 
-__global__ void __launch_bounds__(3 * kCloverSites) k_clover(Geom g, const double2* U64, double kappa, double csw,
+__global__ void __launch_bounds__(128, 4) k_clover_F(Geom g, const float4* Udf, double2* F) {
+  const int V = 2 * g.Vh;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int pl = blockIdx.y;
+  if (i >= V) return;
+  const int mu = pl < 3 ? 0 : pl < 5 ? 1 : 2;
+  const int nu = pl < 3 ? pl + 1 : pl < 5 ? pl - 1 : 3;
+  Coord x;
+  x.x = i % g.X;
+  int r = i / g.X;
+  x.y = r % g.Y;
+  r /= g.Y;
+  x.z = r % g.Z;
+  x.t = r / g.Z;
+  cx<double> Q[9];
+  clover_leaves(g, Udf, x, mu, nu, Q);
+  cx<double> Fm[9];
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++) Fm[a * 3 + b] = 0.125 * (Q[a * 3 + b] - conj(Q[b * 3 + a]));
+  const cx<double> tr3 = (1.0 / 3.0) * (Fm[0] + Fm[4] + Fm[8]);
+  Fm[0] = Fm[0] - tr3;
+  Fm[4] = Fm[4] - tr3;
+  Fm[8] = Fm[8] - tr3;
+#pragma unroll
+  for (int e = 0; e < 9; e++) F[((size_t)pl * 9 + e) * V + i] = make_double2(Fm[e].re, Fm[e].im);
+}
+
+// a double pair as rounded float pairs (re.h, im.h, re.l, im.l)
+__device__ __forceinline__ float4 split_pair(double a, double b) {
+  const float ha = __double2float_rn(a), hb = __double2float_rn(b);
+  return make_float4(ha, hb, __double2float_rn(a - (double)ha), __double2float_rn(b - (double)hb));
+}
+
+__global__ void __launch_bounds__(2 * kCloverSites) k_clover(Geom g, const double2* F, double kappa, double csw,
                                                              double2* A64, double2* Ainv64, float4* Ainv32,
+                                                             float4* Adf, float4* Ainvdf,
                                                              unsigned long long* abound, int* err) {
   __shared__ M3 sG[kCloverSites][2][3];
   const int t = threadIdx.x;
   const int V = 2 * g.Vh;
   {
-    const int s = t / 3, q = t - 3 * (t / 3);
+    // chirality 0 / 1: G3 = F01 -+ F23, G2 = F02 +- F13, G1 = F12 -+ F03
+    const int s = t >> 1, ch = t & 1;
     const int i = blockIdx.x * kCloverSites + s;
     if (i < V) {
-      Coord x;
-      x.x = i % g.X;
-      int r = i / g.X;
-      x.y = r % g.Y;
-      r /= g.Y;
-      x.z = r % g.Z;
-      x.t = r / g.Z;
-      const int ma = q == 0 ? 0 : q == 1 ? 0 : 1, na = q == 0 ? 1 : q == 1 ? 2 : 2;  // F01, F02, F12
-      const int mb = q == 0 ? 2 : q == 1 ? 1 : 0, nb = q == 0 ? 3 : q == 1 ? 3 : 3;  // F23, F13, F03
-      // chirality 0 / 1: G3 = F01 -+ F23, G2 = F02 +- F13, G1 = F12 -+ F03
-      const double sb0 = q == 1 ? 1.0 : -1.0;
-      const M3 Fa = fhat(g, U64, x, ma, na), Fb = fhat(g, U64, x, mb, nb);
+      const double sgn = ch ? 1.0 : -1.0;
 #pragma unroll
       for (int e = 0; e < 9; e++) {
-        sG[s][0][q].e[e] = Fa.e[e] + sb0 * Fb.e[e];
-        sG[s][1][q].e[e] = Fa.e[e] - sb0 * Fb.e[e];
+        const double2 f01 = F[(size_t)(0 * 9 + e) * V + i], f02 = F[(size_t)(1 * 9 + e) * V + i];
+        const double2 f03 = F[(size_t)(2 * 9 + e) * V + i], f12 = F[(size_t)(3 * 9 + e) * V + i];
+        const double2 f13 = F[(size_t)(4 * 9 + e) * V + i], f23 = F[(size_t)(5 * 9 + e) * V + i];
+        sG[s][ch][0].e[e] = mk(f01.x + sgn * f23.x, f01.y + sgn * f23.y);
+        sG[s][ch][1].e[e] = mk(f02.x - sgn * f13.x, f02.y - sgn * f13.y);
+        sG[s][ch][2].e[e] = mk(f12.x + sgn * f03.x, f12.y + sgn * f03.y);
       }
     }
   }
   __syncthreads();
-  if (t >= 2 * kCloverSites) return;
   const int s = t >> 1, ch = t & 1;
   const int i = blockIdx.x * kCloverSites + s;
   if (i >= V) return;
@@ -407,7 +433,10 @@ __global__ void __launch_bounds__(3 * kCloverSites) k_clover(Geom g, const doubl
   }
   atomicMax(abound, (unsigned long long)__double_as_longlong(bound));
 #pragma unroll
-  for (int m = 0; m < 18; m++) A64[((size_t)p * 36 + 18 * ch + m) * g.Vh + cb] = make_double2(pa[2 * m], pa[2 * m + 1]);
+  for (int m = 0; m < 18; m++) {
+    A64[((size_t)p * 36 + 18 * ch + m) * g.Vh + cb] = make_double2(pa[2 * m], pa[2 * m + 1]);
+    Adf[((size_t)p * 36 + 18 * ch + m) * g.Vh + cb] = split_pair(pa[2 * m], pa[2 * m + 1]);
+  }
   if (!herm6_inverse_ldl(pa, pi)) {
     cx<double> A[36], Ai[36];
     for (int row = 0; row < 6; row++)
@@ -420,35 +449,38 @@ __global__ void __launch_bounds__(3 * kCloverSites) k_clover(Geom g, const doubl
     pack_herm(Ai, pi);
   }
 #pragma unroll
-  for (int m = 0; m < 18; m++)
+  for (int m = 0; m < 18; m++) {
     Ainv64[((size_t)p * 36 + 18 * ch + m) * g.Vh + cb] = make_double2(pi[2 * m], pi[2 * m + 1]);
+    Ainvdf[((size_t)p * 36 + 18 * ch + m) * g.Vh + cb] = split_pair(pi[2 * m], pi[2 * m + 1]);
+  }
 #pragma unroll
   for (int m = 0; m < 9; m++)
     Ainv32[((size_t)p * 18 + 9 * ch + m) * g.Vh + cb] =
         make_float4((float)pi[4 * m], (float)pi[4 * m + 1], (float)pi[4 * m + 2], (float)pi[4 * m + 3]);
 }
 
+size_t clover_scratch_bytes(const sq_ctx* c) { return 6 * 9 * 2 * (size_t)c->Vh * sizeof(double2); }
+
+// Launches the build of cs (no host synchronisation): A, A^{-1} (FP64, and
+// as float pairs for the emulated-FP64 operator), the FP32 A^{-1}, the norm bound into c->d_bound (read back by the caller with
+// the error word) and ERRBIT_CLOVER for a singular block.
 sq_status clover_build(sq_ctx* c, CloverSet& cs, double kappa, double csw) {
   Geom g = geom_of(c);
-  unsigned long long* d_bound = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&d_bound, sizeof(unsigned long long), c->stream);
-  if (e != cudaSuccess) return cuda_check(c, e, "clover bound alloc");
-  cudaMemsetAsync(d_bound, 0, sizeof(unsigned long long), c->stream);
-  k_clover<<<(2 * c->Vh + kCloverSites - 1) / kCloverSites, 3 * kCloverSites, 0, c->stream>>>(
-      g, c->U64, kappa, csw, cs.A64, cs.Ainv64, cs.Ainv32, d_bound, c->d_err);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_check(c, e, "clover launch");
-  unsigned long long hb = 0;
-  cudaMemcpyAsync(&hb, d_bound, sizeof(hb), cudaMemcpyDeviceToHost, c->stream);
-  cudaFreeAsync(d_bound, c->stream);
-  e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_check(c, e, "clover build");
-  double b;
-  memcpy(&b, &hb, sizeof(b));
-  cs.a_bound = b;
+  if (!c->cloverF) {
+    cudaError_t e = dev_alloc(c->mem, (void**)&c->cloverF, clover_scratch_bytes(c));
+    if (e != cudaSuccess) {
+      c->cloverF = nullptr;
+      return cuda_check(c, e, "clover field-strength scratch");
+    }
+  }
+  const size_t V = 2 * (size_t)c->Vh;
+  cudaMemsetAsync(c->d_bound, 0, sizeof(unsigned long long), c->stream);
+  k_clover_F<<<dim3((unsigned)((V + 127) / 128), 6), 128, 0, c->stream>>>(g, (const float4*)c->Udf, c->cloverF);
+  k_clover<<<(unsigned)((V + kCloverSites - 1) / kCloverSites), 2 * kCloverSites, 0, c->stream>>>(
+      g, c->cloverF, kappa, csw, cs.A64, cs.Ainv64, cs.Ainv32, cs.Adf, cs.Ainvdf, c->d_bound, c->d_err);
   cs.kappa = kappa;
   cs.csw = csw;
-  return SQ_OK;
+  return cuda_check(c, cudaGetLastError(), "clover launch");
 }
 
 // ---------------------------------------------------------------------------

@@ -92,6 +92,8 @@ struct Workspace {
   std::vector<cudaEvent_t> pev;
   int* hist = nullptr;  // [2][chunk]: sources active / updated per iteration
   int hist_chunk = 0;
+  int* h_pin = nullptr;  // pinned host read-back buffer of the iteration loop
+  size_t h_pin_n = 0;    // ints it holds
 };
 
 // Workspaces, streams and the captured graph of sq_solve_batch, kept in the
@@ -149,8 +151,10 @@ struct sq_ctx {
   std::vector<sq::CloverSet> clover;
   int cur_clover = -1;
   unsigned long long tick = 0;
-  // device error word
+  // device error word, and the clover build's norm bound (same allocation)
   int* d_err = nullptr;
+  unsigned long long* d_bound = nullptr;
+  double2* cloverF = nullptr;  // [6][9][V] field strengths: the clover build's scratch
   sq::Workspace ws;
   sq::BatchCache* batch = nullptr;
   unsigned long long uid = 0;  // unique per context (graph cache keys)
@@ -182,6 +186,7 @@ sq_status read_error_word(sq_ctx* c, int* bits);
 // ---- gauge / clover (sq_gauge.cu)
 sq_status gauge_convert(sq_ctx* c, const double* dev_lex);
 sq_status clover_build(sq_ctx* c, CloverSet& cs, double kappa, double csw);
+size_t clover_scratch_bytes(const sq_ctx* c);
 // sets *flag (device) to 1 if any of the n doubles is not finite; no sync
 void launch_finite(const sq_ctx* c, const double* dev, size_t n, int* flag, cudaStream_t s);
 
@@ -223,7 +228,6 @@ void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s);
 bool launch_dslash_df(const sq_ctx* c, const DslashCall& d, Field out2, int xfirst, cudaStream_t s, int* nparts);
 void launch_clover_df(const sq_ctx* c, const CloverSet& cs, Field out, Field x, Field in, int parity, double c1,
                       double c2, int which, int n, cudaStream_t s);
-void launch_split_copy(const double2* in, float4* out, size_t n, cudaStream_t s);
 // halo-tiled kernel (sq_dslash_tile.cu): false if d.shape does not apply
 bool launch_dslash_tile(const sq_ctx* c, const DslashCall& d, cudaStream_t s, int* nparts);
 bool tile_shape_ok(const sq_ctx* c, int prec, int recon, const Shape& sh);

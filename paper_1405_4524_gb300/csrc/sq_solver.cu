@@ -408,6 +408,7 @@ static void free_ws(Workspace& w) {
   for (auto e : w.pev) cudaEventDestroy(e);
   dev_free(w.mem, w.hist, 2 * (size_t)w.hist_chunk * sizeof(int));
   dev_free(w.mem, w.base, w.bytes);
+  if (w.h_pin) cudaFreeHost(w.h_pin);
   w = Workspace();
 }
 
@@ -1107,9 +1108,20 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
     cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     evs.push_back(ev);
   }
-  int* h_active = nullptr;
-  e = cudaMallocHost((void**)&h_active, (np + 2 * chunk) * sizeof(int));
-  if (e != cudaSuccess) return cuda_check(c0, e, "pinned read-back buffer");
+  // pinned read-back buffer, kept in the first problem's workspace
+  Workspace& w0 = *P[0].w;
+  if (w0.h_pin_n < (size_t)(np + 2 * chunk)) {
+    if (w0.h_pin) cudaFreeHost(w0.h_pin);
+    w0.h_pin = nullptr;
+    w0.h_pin_n = 0;
+    e = cudaMallocHost((void**)&w0.h_pin, (np + 2 * chunk) * sizeof(int));
+    if (e != cudaSuccess) {
+      w0.h_pin = nullptr;
+      return cuda_check(c0, e, "pinned read-back buffer");
+    }
+    w0.h_pin_n = np + 2 * chunk;
+  }
+  int* h_active = w0.h_pin;
   std::vector<int> tot_it(np, 0);
   for (int attempt = 0; attempt < 4; attempt++) {
     for (int i = 0; i < np; i++) {
@@ -1207,10 +1219,7 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
         e = cudaGraphInstantiate(graph, g, 0);
         cudaGraphDestroy(g);
       }
-      if (e != cudaSuccess) {
-        cudaFreeHost(h_active);
-        return cuda_check(c0, e, "graph capture of the inner loop");
-      }
+      if (e != cudaSuccess) return cuda_check(c0, e, "graph capture of the inner loop");
       *gkey = key;
     }
     long long launched = 0;
@@ -1256,10 +1265,7 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       if (prm.verbose) fprintf(stderr, "libstochq: %lld iterations, %d sources active\n", launched, active);
       if (active == 0 || launched > cap) break;
     }
-    if (e != cudaSuccess) {
-      cudaFreeHost(h_active);
-      return cuda_check(c0, e, "inner loop");
-    }
+    if (e != cudaSuccess) return cuda_check(c0, e, "inner loop");
     // per problem: x64 += xs, psi_o = A_oo^{-1} (eta_o + k D_oe psi_e), full
     // FP64 residual
     bool retry = false;
@@ -1316,10 +1322,7 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       cudaMemcpyAsync(&hc, w.ctl, sizeof(Control), cudaMemcpyDeviceToHost, sb);
       e = cudaStreamSynchronize(sb);
       c->launches += hc.launched;
-      if (e != cudaSuccess) {
-        cudaFreeHost(h_active);
-        return cuda_check(c0, e, "final residual");
-      }
+      if (e != cudaSuccess) return cuda_check(c0, e, "final residual");
       for (int k = 0; k < n; k++) {
         double rr = p.enorm2[k] > 0 ? std::sqrt((res2[k] + res2[n + k]) / p.enorm2[k]) : 0.0;
         int status = hs[k].status;
@@ -1356,7 +1359,6 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
         cudaStreamWaitEvent(p.s, evs[0], 0);
       }
   }
-  cudaFreeHost(h_active);
   for (auto& p : P) {
     e = cudaStreamSynchronize(p.w->aux);
     if (e != cudaSuccess) break;
