@@ -113,7 +113,9 @@ typedef struct sq_solve_params {
                           hop with) follow sq_load_gauge's recon          */
   int sites_per_block; /* dslash CTA shape; 0 = autotune                   */
   int rhs_per_block;   /* dslash sources per CTA; 0 = autotune             */
-  int chunk;           /* iterations per CUDA-graph launch (default 16)    */
+  int chunk;           /* iterations per CUDA-graph launch; 0 (default):
+                          24 in a single-problem solve's first launch and
+                          4 in each later one, 16 per launch in batches    */
   int use_graph;       /* 1 (default): capture the inner loop in graphs    */
   int io;              /* SQ_HOST (default) or SQ_DEVICE for sources and
                           solutions                                        */

@@ -180,7 +180,7 @@ void sq_default_params(sq_solve_params* p) {
   p->delta = 0.0;  // automatic per inner precision
   p->max_iter = 20000;
   p->recon = 12;
-  p->chunk = 16;
+  p->chunk = 0;
   p->use_graph = 1;
   p->io = SQ_HOST;
   p->breakdown_tol = 1e-14;

@@ -45,6 +45,39 @@ __global__ void k_unpack(Geom g, double* lex, Field in, int parity, int n) {
   for (int j = 0; j < 12; j++) dst[j] = make_double2((double)v[j].re, (double)v[j].im);
 }
 
+// FP64 packing with the per-source squared norm of the packed field, in the
+// grid and reduction order of k_norm2<P64> (bitwise the same sums)
+__global__ void __launch_bounds__(128) k_pack_norm2(Geom g, Field out, const double* lex, int parity, int n,
+                                                   RedArgs ra) {
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y < n ? (int)blockIdx.y : -1;
+  double v[1] = {0.0};
+  if (k >= 0 && cb < g.Vh) {
+    Coord c = cb_coords(g, cb, parity);
+    size_t site = (size_t)c.x + (size_t)g.X * (c.y + (size_t)g.Y * (c.z + (size_t)g.Z * c.t));
+    const double2* src = (const double2*)lex + ((size_t)k * 2 * g.Vh + site) * 12;
+    cx<double> a[12];
+#pragma unroll
+    for (int j = 0; j < 12; j++) {
+      const double2 q = src[j];
+      a[j] = mk(q.x, q.y);
+    }
+    SpinorIO<P64>::store(out, k, cb, a);
+    double t = 0;
+#pragma unroll
+    for (int j = 0; j < 12; j++) t += (double)a[j].re * a[j].re + (double)a[j].im * a[j].im;
+    v[0] = t;
+  }
+  reduce_finalize<1, FIN_STORE>(ra, v, k, (int)gridDim.x, (int)blockIdx.x);
+}
+
+void launch_pack_norm2(const sq_ctx* c, Field out, const double* lex, int parity, int n, double* norm, RedArgs ra,
+                       cudaStream_t s) {
+  ra.out = norm;
+  dim3 grid((c->Vh + 127) / 128, n);
+  k_pack_norm2<<<grid, 128, 0, s>>>(geom_of(c), out, lex, parity, n, ra);
+}
+
 void launch_pack(const sq_ctx* c, Field out, const double* lex, int parity, int prec, int n, cudaStream_t s) {
   Geom g = geom_of(c);
   dim3 grid((c->Vh + 127) / 128, n);

@@ -330,6 +330,7 @@ bool launch_dslash_df(const sq_ctx* c, const DslashCall& d, Field out2, int xfir
   a.nrb = d.n;
   dim3 block(2 * kDfSites), grid((unsigned)a.nsb * (unsigned)a.nrb);
   *nparts = a.nsb * (2 * kDfSites / 32);
+  if (d.fin != FIN_NONE && *nparts > d.ra.nblk_stride) return false;  // partials would not fit
   const int m = (d.clover ? 1 : 0) | (d.xpay ? 2 : 0);
   if (xfirst) {
     if (!d.clover || !d.xpay || d.fin != FIN_NONE) return false;

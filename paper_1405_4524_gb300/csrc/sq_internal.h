@@ -88,6 +88,8 @@ struct Workspace {
   // cached graph of `chunk` iterations, keyed by everything baked into it
   cudaGraphExec_t graph = nullptr;
   std::vector<unsigned long long> graph_key;
+  cudaGraphExec_t graph2 = nullptr;  // the tail chunk's graph (chunks sized automatically)
+  std::vector<unsigned long long> graph_key2;
   // profiling: one event before each iteration and after each of its kernels
   std::vector<cudaEvent_t> pev;
   int* hist = nullptr;  // [2][chunk]: sources active / updated per iteration
@@ -198,6 +200,8 @@ void launch_clover64(const sq_ctx* c, const CloverSet& cs, Field out, Field x, F
                      double c1, double c2, int which, int n, cudaStream_t s);
 // per-source FP64 norms^2 of an eo field (any precision) -> out[k]
 void launch_norm2(const sq_ctx* c, Field f, int prec, int n, double* out, RedArgs ra, cudaStream_t s);
+void launch_pack_norm2(const sq_ctx* c, Field out, const double* lex, int parity, int n, double* norm, RedArgs ra,
+                       cudaStream_t s);
 
 // ---- dslash (sq_dslash.cu)
 struct DslashCall {

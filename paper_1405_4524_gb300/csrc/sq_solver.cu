@@ -405,6 +405,7 @@ static void free_ws(Workspace& w) {
   for (auto ev : w.ev_in)
     if (ev) cudaEventDestroy(ev);
   if (w.graph) cudaGraphExecDestroy(w.graph);
+  if (w.graph2) cudaGraphExecDestroy(w.graph2);
   for (auto e : w.pev) cudaEventDestroy(e);
   dev_free(w.mem, w.hist, 2 * (size_t)w.hist_chunk * sizeof(int));
   dev_free(w.mem, w.base, w.bytes);
@@ -434,9 +435,10 @@ static sq_status alloc_ws(sq_ctx* c, Workspace& w, int n, int inner) {
   const int Vh = c->Vh;
   const size_t f64 = field_bytes(Vh, P64, n), fin = field_bytes(Vh, inner, n);
   const size_t fx = field_bytes(Vh, px_of(inner), n);
-  // per source: one partial per warp of the widest launch (sites / 32,
-  // rounded up per CTA of up to 32 warps)
-  const int nblk = (Vh + 31) / 32 + 32;
+  // per source: one partial per warp of the launch with the most warps per
+  // site (the emulated-FP64 operator: two threads per site, 16 sites per
+  // warp), rounded up per CTA of up to 32 warps
+  const int nblk = (Vh + 15) / 16 + 32;
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   size_t tot = 0;
   size_t o_f64 = tot; tot += al(f64) * 7;
@@ -894,7 +896,7 @@ static sq_status validate_params(sq_ctx* c, sq_solve_params& prm) {
   // 1e-4..1e-2: fewest outer cycles for a few more inner iterations)
   if (!(prm.delta > 0.0))
     prm.delta = prm.inner_prec == P16 ? (prm.outer == SQ_OUTER_DEFECT ? 1e-4 : 3e-3) : 3e-6;
-  if (prm.chunk <= 0) prm.chunk = 16;
+  if (prm.chunk < 0) prm.chunk = 0;  // 0: sized automatically
   if (!(prm.breakdown_tol > 0.0)) prm.breakdown_tol = 1e-14;
   if (!std::isfinite(prm.breakdown_tol)) return set_error(c, SQ_ERR_ARG, "sq_solve: breakdown_tol must be finite");
   if (prm.fallback_max_iter < 0) return set_error(c, SQ_ERR_ARG, "sq_solve: fallback_max_iter must be >= 0");
@@ -958,10 +960,8 @@ static sq_status setup_problem(Prob& p, const sq_solve_params& prm) {
       cudaStreamWaitEvent(s, w.ev_in[g], 0);
     }
     launch_finite(c, gsrc, ng * lex_src, w.flag, s);
-    launch_pack(c, sub64(w.eta_e, k0), gsrc, 0, P64, ng, s);
-    launch_pack(c, sub64(w.eta_o, k0), gsrc, 1, P64, ng, s);
-    launch_norm2(c, sub64(w.eta_e, k0), P64, ng, w.scal + k0, ra, s);
-    launch_norm2(c, sub64(w.eta_o, k0), P64, ng, w.scal + n + k0, ra, s);
+    launch_pack_norm2(c, sub64(w.eta_e, k0), gsrc, 0, ng, w.scal + k0, ra, s);
+    launch_pack_norm2(c, sub64(w.eta_o, k0), gsrc, 1, ng, w.scal + n + k0, ra, s);
     DslashCall d;
     memset(&d, 0, sizeof(d));
     d.prec = P64;
@@ -980,14 +980,14 @@ static sq_status setup_problem(Prob& p, const sq_solve_params& prm) {
       d.out = sub64(w.b64, k0); d.in = sub64(w.t64o, k0); d.x = sub64(w.eta_e, k0); d.p_out = 0; d.xpay = 1;
       d.a = p.kappa;
       launch_dslash(c, d, s);
-      c->launches += 7;
+      c->launches += 5;
     } else {
       launch_clover64(c, *p.cs, sub64(w.t64o, k0), none, sub64(w.eta_o, k0), 1, 0.0, 1.0, 1, ng, s);
       d.out = sub64(w.r64, k0); d.in = sub64(w.t64o, k0); d.x = sub64(w.eta_e, k0); d.p_out = 0; d.xpay = 1;
       d.a = p.kappa;
       launch_dslash(c, d, s);
       launch_clover64(c, *p.cs, sub64(w.b64, k0), none, sub64(w.r64, k0), 0, 0.0, 1.0, 1, ng, s);
-      c->launches += 8;
+      c->launches += 6;
     }
   }
   std::vector<double> eta2(2 * n);
@@ -1075,11 +1075,19 @@ static void output_solutions(Prob& p, const sq_solve_params& prm, cudaStream_t s
 // Then per problem: reconstruction, FP64 full residual, solutions out.
 static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, cudaStream_t sb,
                               cudaGraphExec_t* graph, std::vector<unsigned long long>* gkey,
+                              cudaGraphExec_t* graph2, std::vector<unsigned long long>* gkey2,
                               std::vector<cudaEvent_t>& evs, sq_status* result) {
   const int np = (int)P.size();
   const bool prof = prm.profile != 0 && np == 1;
   const unsigned pmask = profile_mask(prm.profile);
-  const int chunk = prm.chunk;
+  // iterations per graph launch: fixed (prm.chunk), or, by default for one
+  // problem, 24 in the first launch and 4 in each later one (graph2), so that
+  // at most 3 iterations run after the last source has converged and no
+  // graph is captured again when the iteration count changes
+  const bool autoc = prm.chunk == 0 && np == 1 && graph2 != nullptr;
+  const int tail = autoc ? 4 : (prm.chunk > 0 ? prm.chunk : 16);
+  const int first = autoc ? 24 : tail;
+  const int chunk = std::max(first, tail);  // the most iterations of one launch
   const double delta = prm.inner_prec == P64 ? 0.0 : prm.delta;
   sq_ctx* c0 = P[0].c;
   cudaError_t e = cudaSuccess;
@@ -1144,7 +1152,7 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
     }
     // the graph key holds everything baked into the captured kernels
     std::vector<unsigned long long> key = {(unsigned long long)np, (unsigned long long)prm.inner_prec,
-                                           (unsigned long long)chunk, (unsigned long long)prof,
+                                           0ull, (unsigned long long)prof,
                                            (unsigned long long)prm.profile, (unsigned long long)prm.outer};
     for (auto& p : P) {
       unsigned long long kb;
@@ -1168,6 +1176,7 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
     const bool use_graph = prm.use_graph != 0;
     bool cond_ok = true;      // conditional update nodes may be used
     bool cond_failed = false;  // adding one failed during the capture
+    int cur = first;  // iterations in the graph launched next
     auto launch_chunk = [&](bool capture) {
       for (int i = 0; i < np; i++) {
         Prob& p = P[i];
@@ -1176,7 +1185,7 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
           cudaEventRecord(evs[np + i], sb);
           cudaStreamWaitEvent(ps, evs[np + i], 0);
         }
-        for (int it = 0; it < chunk; it++) {
+        for (int it = 0; it < cur; it++) {
           Marks m;
           if (prof) {
             m.ev = &p.w->pev[(size_t)it * (KC_N + 1)];
@@ -1185,7 +1194,7 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
           }
           m.cond = capture && prm.profile != 1 && cond_ok;
           m.cond_failed = &cond_failed;
-          p.iter(p.c, *p.w, *p.cs, p.kappa, p.sh, ps, m, it, chunk);
+          p.iter(p.c, *p.w, *p.cs, p.kappa, p.sh, ps, m, it, cur);
         }
         if (ps != sb) {  // join
           cudaEventRecord(evs[i], ps);
@@ -1193,39 +1202,50 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
         }
       }
     };
-    if (use_graph && (!*graph || key != *gkey)) {
-      if (*graph) {
-        cudaGraphExecDestroy(*graph);
-        *graph = nullptr;
+    // the graph of `cur` iterations (the first chunk's, or the tail's when
+    // chunks are sized automatically), captured when its key changes
+    auto ensure_graph = [&](cudaGraphExec_t* gx, std::vector<unsigned long long>* gk) -> cudaError_t {
+      key[2] = (unsigned long long)cur;
+      if (!use_graph || (*gx && key == *gk)) return cudaSuccess;
+      if (*gx) {
+        cudaGraphExecDestroy(*gx);
+        *gx = nullptr;
       }
+      cond_ok = true;
+      cond_failed = false;
       cudaGraph_t g;
-      e = cudaStreamBeginCapture(sb, cudaStreamCaptureModeThreadLocal);
-      if (e == cudaSuccess) {
+      cudaError_t ce = cudaStreamBeginCapture(sb, cudaStreamCaptureModeThreadLocal);
+      if (ce == cudaSuccess) {
         launch_chunk(true);
-        e = cudaStreamEndCapture(sb, &g);
+        ce = cudaStreamEndCapture(sb, &g);
       }
-      if (e == cudaSuccess && cond_failed) {
+      if (ce == cudaSuccess && cond_failed) {
         // a conditional node could not be added: capture again with the
         // update paths as plain launches (they exit on an empty list)
         cudaGraphDestroy(g);
         cond_ok = false;
-        e = cudaStreamBeginCapture(sb, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
+        ce = cudaStreamBeginCapture(sb, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
           launch_chunk(true);
-          e = cudaStreamEndCapture(sb, &g);
+          ce = cudaStreamEndCapture(sb, &g);
         }
       }
-      if (e == cudaSuccess) {
-        e = cudaGraphInstantiate(graph, g, 0);
+      if (ce == cudaSuccess) {
+        ce = cudaGraphInstantiate(gx, g, 0);
         cudaGraphDestroy(g);
       }
-      if (e != cudaSuccess) return cuda_check(c0, e, "graph capture of the inner loop");
-      *gkey = key;
-    }
+      if (ce == cudaSuccess) *gk = key;
+      return ce;
+    };
     long long launched = 0;
     const long long cap = (long long)prm.max_iter + 4LL * chunk;
+    cur = first;
     for (;;) {
-      if (use_graph) e = cudaGraphLaunch(*graph, sb);
+      cudaGraphExec_t* gx = (autoc && cur == tail && cur != first) ? graph2 : graph;
+      std::vector<unsigned long long>* gk = gx == graph ? gkey : gkey2;
+      e = ensure_graph(gx, gk);
+      if (e != cudaSuccess) return cuda_check(c0, e, "graph capture of the inner loop");
+      if (use_graph) e = cudaGraphLaunch(*gx, sb);
       else {
         launch_chunk(false);
         e = cudaGetLastError();
@@ -1233,19 +1253,19 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       if (e != cudaSuccess) break;
       // launches inside conditional nodes are counted on the device
       for (auto& p : P)
-        p.c->launches += (long long)chunk * (kChainLaunches + (use_graph && prm.profile != 1
+        p.c->launches += (long long)cur * (kChainLaunches + (use_graph && prm.profile != 1
                                                                     ? 0
                                                                     : kUpdateLaunches * (p.w->refresh ? 2 : 1)));
-      launched += chunk;
+      launched += cur;
       for (int i = 0; i < np; i++)
         cudaMemcpyAsync(h_active + i, &P[i].w->ctl->n_active, sizeof(int), cudaMemcpyDeviceToHost, sb);
-      if (prof) cudaMemcpyAsync(h_active + np, P[0].w->hist, 2 * chunk * sizeof(int), cudaMemcpyDeviceToHost, sb);
+      if (prof) cudaMemcpyAsync(h_active + np, P[0].w->hist, 2 * cur * sizeof(int), cudaMemcpyDeviceToHost, sb);
       e = cudaStreamSynchronize(sb);
       if (e != cudaSuccess) break;
       if (prof) {
         Workspace& w = *P[0].w;
-        for (int i = 0; i < chunk; i++) {
-          const double na = h_active[np + i], nu = h_active[np + chunk + i];
+        for (int i = 0; i < cur; i++) {
+          const double na = h_active[np + i], nu = h_active[np + cur + i];
           for (int kc = 0; kc < KC_N; kc++) {
             if (!((pmask >> kc) & 1u) || !((pmask >> (kc + 1)) & 1u)) continue;
             float ms = 0;
@@ -1264,6 +1284,7 @@ static sq_status run_problems(std::vector<Prob>& P, const sq_solve_params& prm, 
       for (int i = 0; i < np; i++) active += h_active[i];
       if (prm.verbose) fprintf(stderr, "libstochq: %lld iterations, %d sources active\n", launched, active);
       if (active == 0 || launched > cap) break;
+      cur = tail;
     }
     if (e != cudaSuccess) return cuda_check(c0, e, "inner loop");
     // per problem: x64 += xs, psi_o = A_oo^{-1} (eta_o + k D_oe psi_e), full
@@ -1518,7 +1539,8 @@ sq_status solve_impl(sq_ctx* c, double kappa, double csw, const double* src, dou
   if (st != SQ_OK) return st;
   std::vector<cudaEvent_t> evs;
   sq_status result = SQ_OK;
-  st = run_problems(P, prm, c->stream, &c->ws.graph, &c->ws.graph_key, evs, &result);
+  st = run_problems(P, prm, c->stream, &c->ws.graph, &c->ws.graph_key, &c->ws.graph2, &c->ws.graph_key2, evs,
+                    &result);
   for (auto ev : evs) cudaEventDestroy(ev);
   if (st != SQ_OK) return st;
   st = check_timeouts(c, "sq_solve");
@@ -1596,7 +1618,7 @@ sq_status solve_batch_impl(const sq_problem* probs, int np, const sq_solve_param
   }
   cudaEventDestroy(ev);
   sq_status result = SQ_OK;
-  st = run_problems(P, prm, c0->stream, &B.graph, &B.key, B.events, &result);
+  st = run_problems(P, prm, c0->stream, &B.graph, &B.key, nullptr, nullptr, B.events, &result);
   if (st != SQ_OK) return st;
   for (int i = 0; i < np; i++) {
     bool seen = false;

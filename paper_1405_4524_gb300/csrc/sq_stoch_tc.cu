@@ -196,10 +196,13 @@ __device__ __forceinline__ long long fixed55(double x, int e) {
   return b < 0 ? -m : m;
 }
 
-__device__ __forceinline__ float digit(long long m, int s) {
-  const long long a = m < 0 ? -m : m;
-  const int d = (int)((a >> (11 * (4 - s))) & 2047);
-  return (float)(m < 0 ? -d : d);
+// digit s (0 = most significant) of |m| as a float with the sign of m:
+// 0 <= d < 2^11 placed in the mantissa of 2^23 and 2^23 taken away again
+// (exact, no integer-to-float conversion), the sign bit set directly
+__device__ __forceinline__ float digit(unsigned long long a, unsigned sign, int s) {
+  const unsigned d = (unsigned)(a >> (11 * (4 - s))) & 2047u;
+  const float v = __uint_as_float(0x4B000000u | d) - 8388608.0f;
+  return __uint_as_float(__float_as_uint(v) | sign);
 }
 
 // B tiles and chunk exponents of timeslices t0 .. t0 + Tb - 1: grid (nch,
@@ -248,17 +251,24 @@ __global__ void __launch_bounds__(256) k_tc_pack_x(const double2* X, int n, int 
     const int jl = v & (kTcJ - 1), q = (v >> 4) & 7, kt = kt0 + (v >> 7);
     const int j = jt * kTcJ + jl, e = se[jl];
     const long long row = (long long)kt * (kTcK / 2) + q * 4;
-    long long mr[4], mi[4];
+    // the 4 rows start at a multiple of 4: spin rows 6..11 (gamma5 = -1 on
+    // spins 2, 3) are all four (row % 12 == 8) or the last two (== 4)
+    const int g = (int)(row % 12);
+    unsigned long long ar[4], ai[4];
+    unsigned sr[4], si[4];
 #pragma unroll
     for (int c = 0; c < 4; c++) {
       double2 d = make_double2(0.0, 0.0);
       if (j < n) d = X[((long long)j * T + t0 + tb) * K + row + c];
-      mr[c] = fixed55(d.x, e);
-      mi[c] = fixed55(d.y, e);
-      if (((row + c) % 12) >= 6) {  // gamma5 = -1 on spins 2, 3
-        mr[c] = -mr[c];
-        mi[c] = -mi[c];
+      long long mr = fixed55(d.x, e), mi = fixed55(d.y, e);
+      if (g == 8 || (g == 4 && c >= 2)) {
+        mr = -mr;
+        mi = -mi;
       }
+      ar[c] = (unsigned long long)(mr < 0 ? -mr : mr);
+      ai[c] = (unsigned long long)(mi < 0 ? -mi : mi);
+      sr[c] = mr < 0 ? 0x80000000u : 0u;
+      si[c] = mi < 0 ? 0x80000000u : 0u;
     }
     char* blk = reinterpret_cast<char*>(B) + (((long long)tb * njt + jt) * nkt + kt) * kTcBBytes;
 #pragma unroll
@@ -266,10 +276,11 @@ __global__ void __launch_bounds__(256) k_tc_pack_x(const double2* X, int n, int 
       float fr[8], fi[8];
 #pragma unroll
       for (int c = 0; c < 4; c++) {
-        fr[2 * c] = digit(mr[c], s);
-        fr[2 * c + 1] = digit(mi[c], s);
-        fi[2 * c] = digit(mi[c], s);
-        fi[2 * c + 1] = -digit(mr[c], s);
+        const float dr = digit(ar[c], sr[c], s), di = digit(ai[c], si[c], s);
+        fr[2 * c] = dr;
+        fr[2 * c + 1] = di;
+        fi[2 * c] = di;
+        fi[2 * c + 1] = -dr;
       }
       *reinterpret_cast<uint4*>(blk + tile_offset(kTcN, (s * 2 + 0) * kTcJ + jl, q * 8)) = pack8(fr);
       *reinterpret_cast<uint4*>(blk + tile_offset(kTcN, (s * 2 + 1) * kTcJ + jl, q * 8)) = pack8(fi);

@@ -95,6 +95,57 @@ def test_graph_conditionals_match_plain_launches(small, inner):
         assert rel(out[0][0][k], ref[k]) <= 1e-9
 
 
+@pytest.mark.parametrize("inner", [1, 2])
+def test_default_chunks_match_fixed_chunks(small, inner):
+    """The default chunks (24 iterations in the first graph launch, then 4 at
+    a time) run the same iterations as fixed chunks of 16: bitwise identical
+    solutions and stats, for a solve that ends in a tail launch and for a
+    loose one that ends inside the first launch."""
+    s, spec, eta, ref = small
+    sq = s.sq
+    n = eta.shape[0]
+    kappa, csw = spec["kappa"], spec["csw"]
+
+    def solve(chunk, tol):
+        sol = np.zeros_like(eta)
+        _, st = sq.sq_solve(s.ctx, kappa, csw, eta, sol, n, tol, sq.sq_default_params(inner_prec=inner, chunk=chunk))
+        return sol, [(x["iterations"], x["updates"], x["restarts"]) for x in st]
+
+    for tol in (1e-12, 1e-6):
+        fixed, st_fixed = solve(16, tol)
+        for _ in range(2):
+            auto, st_auto = solve(0, tol)
+            assert np.array_equal(auto, fixed) and st_auto == st_fixed
+    assert max(x[0] for x in st_fixed) < 24  # the loose solve ends inside the first launch
+    auto, _ = solve(0, 1e-10)
+    for k in range(n):
+        assert rel(auto[k], ref[k]) <= 1e-9
+
+
+@pytest.mark.parametrize("inner", [1, 2])
+def test_copies_of_a_source_give_identical_results(inner):
+    """Four copies of one source in a batch: every reduction is per source
+    in a fixed order, so the four solutions and their stats are bitwise
+    equal. 8^4 has enough sites per parity that partial sums of one source
+    would land in the next one's if the partial buffer were too small (the
+    last copies would then differ)."""
+    dims = (8, 8, 8, 8)
+    s = Setup(dims, 0.25, 77)
+    try:
+        sq = s.sq
+        n = 4
+        eta = np.ascontiguousarray(np.repeat(inputs.make_z4(dims, 1, 78), n, axis=0))
+        sol = np.zeros_like(eta)
+        _, st = sq.sq_solve(s.ctx, 0.118, 1.0, eta, sol, n, 1e-10, sq.sq_default_params(inner_prec=inner))
+        rows = [(x["iterations"], x["updates"], x["restarts"], x["true_residual"]) for x in st]
+        for k in range(1, n):
+            assert np.array_equal(sol[k], sol[0]), k
+            assert rows[k] == rows[0], rows
+        assert rows[0][1] >= 2  # an FP64-accurate update after the initial one ran
+    finally:
+        s.close()
+
+
 def test_solve_is_deterministic(small):
     s, spec, eta, ref = small
     sq = s.sq
