@@ -165,8 +165,9 @@ __global__ void k_stoch_sum(const double2* part, int ni, int nj, int T, int nkg,
 // grid (block pair, group): the CTA walks 16 x 16 tiles (I, J) of the pair
 // index, stages O(ta)[I, J] for its four ta and O(tb)[J, I] for its four tb in
 // shared memory (both read along rows), and every thread forms the 16
-// products of its (i, j) for all (ta, tb) of the block pair, so each staged
-// value feeds four FMAs pairs. One partial per (block pair, group, ta, tb);
+// products of its (i, j) for all (ta, tb) of the block pair (the 10 with
+// ta >= tb in a diagonal block), so each staged value feeds up to four
+// complex FMAs. One partial per (block pair, group, ta, tb);
 // k_stoch_corr_sum adds the groups, then the timeslices, in a fixed order.
 constexpr int kCorrTB = 4;   // timeslices per block
 constexpr int kCorrTile = 16;
@@ -204,15 +205,27 @@ __global__ void __launch_bounds__(256) k_stoch_corr_blocks(const double2* O, int
       a[q] = sa[q][r][c];  // O(ta)[i][j], i = I*16 + r, j = J*16 + c
       b[q] = sb[q][c][r];  // O(tb)[j][i]
     }
+    if (ba != bb) {
 #pragma unroll
-    for (int q = 0; q < kCorrTB; q++)
+      for (int q = 0; q < kCorrTB; q++)
 #pragma unroll
-      for (int p = 0; p < kCorrTB; p++) {
-        re[q][p] = fma(a[q].x, b[p].x, re[q][p]);
-        re[q][p] = fma(-a[q].y, b[p].y, re[q][p]);
-        im[q][p] = fma(a[q].x, b[p].y, im[q][p]);
-        im[q][p] = fma(a[q].y, b[p].x, im[q][p]);
-      }
+        for (int p = 0; p < kCorrTB; p++) {
+          re[q][p] = fma(a[q].x, b[p].x, re[q][p]);
+          re[q][p] = fma(-a[q].y, b[p].y, re[q][p]);
+          im[q][p] = fma(a[q].x, b[p].y, im[q][p]);
+          im[q][p] = fma(a[q].y, b[p].x, im[q][p]);
+        }
+    } else {  // diagonal block: the sum reads ta >= tb (q >= p) only
+#pragma unroll
+      for (int q = 0; q < kCorrTB; q++)
+#pragma unroll
+        for (int p = 0; p <= q; p++) {
+          re[q][p] = fma(a[q].x, b[p].x, re[q][p]);
+          re[q][p] = fma(-a[q].y, b[p].y, re[q][p]);
+          im[q][p] = fma(a[q].x, b[p].y, im[q][p]);
+          im[q][p] = fma(a[q].y, b[p].x, im[q][p]);
+        }
+    }
   }
   // fixed-order block reduction of the 16 complex sums
   __shared__ double red[8][kCorrTB * kCorrTB][2];
