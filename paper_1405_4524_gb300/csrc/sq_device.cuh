@@ -76,6 +76,16 @@ struct Real<P64> {
   typedef double T;
 };
 
+// Storage precision of BiCGStab's shadow residual r-hat for inner fields of
+// precision P: FP16 (with its per-site norm) under FP32 and FP16 fields.
+// r-hat is any fixed vector with <r-hat, r0> != 0 and is only read in inner
+// products, so storing it rounded changes which fixed vector it is, not the
+// method; FP64 fields keep it in FP64.
+template <int P>
+struct ShadowPrec {
+  static constexpr int value = P == P64 ? P64 : P16;
+};
+
 // Accumulator of the inner iteration's fused sums (the BiCGStab inner
 // products and norms reduced in the operator and update kernels) for fields
 // of real type R. FP64 fields sum in FP64. FP32 and FP16 fields sum in FP32
@@ -155,6 +165,7 @@ struct SpinorIO;
 template <>
 struct SpinorIO<P64> {
   static constexpr int NC = 12;
+  static __device__ __forceinline__ void round_trip(cx<double>*) {}  // stored exactly
   static __device__ __forceinline__ void load(const Field& f, int k, int cb, cx<double> v[12]) {
     const double2* p = (const double2*)f.data + (size_t)k * 12 * f.Vh + cb;
 #pragma unroll
@@ -247,6 +258,18 @@ struct SpinorIO<P16> {
       p[(size_t)c * f.Vh] = q;
     }
     f.norm[(size_t)k * f.Vh + cb] = m;
+  }
+  // the values that a store followed by a load gives back, without memory
+  static __device__ __forceinline__ void round_trip(cx<float> v[12]) {
+    float m = 0.f;
+#pragma unroll
+    for (int j = 0; j < 12; j++) m = fmaxf(m, fmaxf(fabsf(v[j].re), fabsf(v[j].im)));
+    const float inv = m > 0.f ? 1.0f / m : 0.f;
+#pragma unroll
+    for (int j = 0; j < 12; j++) {
+      const float2 a = h2f(f2h(v[j].re * inv, v[j].im * inv));
+      v[j] = mk(a.x * m, a.y * m);
+    }
   }
 };
 

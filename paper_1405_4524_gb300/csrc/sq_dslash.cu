@@ -158,7 +158,7 @@ __device__ __forceinline__ void dslash_pass(const KArgs& a, int sb, int slot0, i
     SpinorIO<P>::store(a.out, k, cb, acc);
     if (FIN == FIN_ALPHA) {  // <r1, out>
       cx<R> rv[12];
-      SpinorIO<P>::load(a.r1, k, cb, rv);
+      SpinorIO<ShadowPrec<P>::value>::load(a.r1, k, cb, rv);
       S sr = 0, si = 0;
 #pragma unroll
       for (int j = 0; j < 12; j++) {

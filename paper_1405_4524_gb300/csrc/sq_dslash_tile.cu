@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, 1) k_dslash_tile(const __grid
       S red[NRED];
       if (FIN == FIN_ALPHA) {  // <r1, out>
         cx<float> rv[12];
-        SpinorIO<P>::load(a.r1, k, cb, rv);
+        SpinorIO<ShadowPrec<P>::value>::load(a.r1, k, cb, rv);
         S sr = 0, si = 0;
 #pragma unroll
         for (int j = 0; j < 12; j++) {

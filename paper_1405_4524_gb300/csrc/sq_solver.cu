@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256) k_xr_update(const VArgs a) {
       for (int j = 0; j < 12; j++)
         s[j] = mk(s[j].re - (wr * t[j].re - wi * t[j].im), s[j].im - (wr * t[j].im + wi * t[j].re));
       SpinorIO<P>::store(a.f4, k, cb, s);
-      SpinorIO<P>::load(a.f5, k, cb, rh);
+      SpinorIO<ShadowPrec<P>::value>::load(a.f5, k, cb, rh);
       S n2 = 0, dr = 0, di = 0;
 #pragma unroll
       for (int j = 0; j < 12; j++) {
@@ -217,13 +217,14 @@ __global__ void __launch_bounds__(256) k_rel_r(const VArgs a) {
 #pragma unroll
       for (int j = 0; j < 12; j++) r[j] = mk((R)r64[j].re, (R)r64[j].im);
       SpinorIO<P>::store(a.f1, k, cb, r);
-      if (restart) {
-        SpinorIO<P>::store(a.f2, k, cb, r);
+      if (restart) {  // rhat = r as stored (rounded to its storage precision)
+        SpinorIO<ShadowPrec<P>::value>::store(a.f2, k, cb, r);
         SpinorIO<P>::store(a.f3, k, cb, r);
 #pragma unroll
         for (int j = 0; j < 12; j++) rh[j] = r[j];
+        SpinorIO<ShadowPrec<P>::value>::round_trip(rh);
       } else {
-        SpinorIO<P>::load(a.f2, k, cb, rh);
+        SpinorIO<ShadowPrec<P>::value>::load(a.f2, k, cb, rh);
       }
       S dr = 0, di = 0;
 #pragma unroll
@@ -473,6 +474,7 @@ static sq_status alloc_ws(sq_ctx* c, Workspace& w, int n, int inner) {
   for (int i = 0; i < 7; i++) *f64s[i] = make_field(b + o_f64 + al(f64) * i, Vh, P64, n);
   Field* fins[7] = {&w.r, &w.rh, &w.p, &w.v, &w.s, &w.t, &w.to};
   for (int i = 0; i < 7; i++) *fins[i] = make_field(b + o_fin + al(fin) * i, Vh, inner, n);
+  w.rh = make_field(w.rh.data, Vh, inner == P64 ? P64 : P16, n);  // the shadow residual (ShadowPrec)
   w.xs = make_field(b + o_fx, Vh, px_of(inner), n);
   w.lex = (double*)(b + o_lex);
   w.partial = (double*)(b + o_part);
@@ -804,6 +806,7 @@ struct Cost {
 static Cost class_cost(int kc, int inner, int recon, double Vh, double na, double nu) {
   const double S = inner == P64 ? 192 : inner == P32 ? 96 : 52;  // spinor site
   const double SX = inner == P64 ? 192 : 96;                      // x accumulator
+  const double SH = inner == P64 ? 192 : 52;                      // shadow residual (ShadowPrec)
   // links and clover blocks: FP64 for the FP64 operator, FP32 otherwise
   // (FP16 fields are hopped with the FP32 gauge data)
   const double L = inner == P64 ? 144 : (recon == 12 ? 48 : 72);
@@ -816,13 +819,13 @@ static Cost class_cost(int kc, int inner, int recon, double Vh, double na, doubl
       if (na > 0) r = {Vh * (8 * L + Cl) + na * Vh * 2 * S, na * Vh * (hop + clv)};
       break;
     case KC_DSLASH_XPAY_ALPHA:
-      if (na > 0) r = {Vh * (8 * L + Cl) + na * Vh * 4 * S, na * Vh * (hop + clv + xpay + 48)};
+      if (na > 0) r = {Vh * (8 * L + Cl) + na * Vh * (3 * S + SH), na * Vh * (hop + clv + xpay + 48)};
       break;
     case KC_DSLASH_XPAY_OMEGA:
       if (na > 0) r = {Vh * (8 * L + Cl) + na * Vh * 3 * S, na * Vh * (hop + clv + xpay + 96)};
       break;
     case KC_S_UPDATE: r = {na * Vh * 3 * S, na * Vh * 48}; break;
-    case KC_XR_UPDATE: r = {na * Vh * (2 * SX + 5 * S), na * Vh * 240}; break;
+    case KC_XR_UPDATE: r = {na * Vh * (2 * SX + 4 * S + SH), na * Vh * 240}; break;
     case KC_P_UPDATE: r = {na * Vh * 4 * S, na * Vh * 96}; break;
     case KC_PLAN: break;
     case KC_REL_X: r = {nu * Vh * (4 * 192 + 2 * SX), nu * Vh * 48}; break;
