@@ -288,6 +288,7 @@ void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s) {
     if (d.prec == P64) {
       if (d.fin == FIN_ALPHA) k_finish<double, 2, FIN_ALPHA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
       else if (d.fin == FIN_OMEGA) k_finish<double, 3, FIN_OMEGA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
+      else if (d.fin == FIN_STORE) k_finish<double, 1, FIN_STORE><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
       else k_finish<double, 1, FIN_TRUE><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);
     } else {
       if (d.fin == FIN_ALPHA) k_finish<SumOf<float>::T, 2, FIN_ALPHA><<<d.n, 256, 0, s>>>(a.ra, d.list, d.count, d.n, nparts);

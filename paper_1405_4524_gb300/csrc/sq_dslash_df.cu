@@ -17,7 +17,8 @@
 // from parity 1-p onto p. Modes (out, out2: FP64 fields of parity p):
 //   XFIRST = 0: w = D in; w <- A^-1 w (CLOV); out = x + a w (XPAY) or w
 //   XFIRST = 1: w = x + a D in; out = A^-1 w; out2 = w (OUT2)
-// FIN_TRUE adds ||out||^2 per source (per-warp partials for k_finish).
+// FIN_TRUE and FIN_STORE add ||out||^2 per source (per-warp partials for
+// k_finish: the solver's true residual, or a stored norm).
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(2 * kDfSites, kDfMinBlocks) k_dslash_df(const 
         }
       }
       store_block_df(a.out, k, cb, j, blk);
-      if (FIN == FIN_TRUE) {
+      if (FIN == FIN_TRUE || FIN == FIN_STORE) {
         // ||out||^2 to FP32 accuracy (a residual norm). A residual is the
         // cancellation of nearly equal terms, after which the leading float
         // of a pair need not carry the value: square the rounded h + l.
@@ -256,23 +257,19 @@ __global__ void __launch_bounds__(2 * kDfSites, kDfMinBlocks) k_dslash_df(const 
         red = (double)q2;
       }
     }
-    if (FIN == FIN_TRUE) {  // both threads of a site sit in one warp
+    if (FIN == FIN_TRUE || FIN == FIN_STORE) {  // both threads of a site sit in one warp
       double r1[1] = {red};
       warp_partials<1>(a.ra, r1, k, sb * (2 * kDfSites / 32) + warp);
     }
   }
 }
 
-// out = c1 x + c2 (C in), C = A or A^{-1} (pre-split blocks); x may be
-// absent. The two chirality blocks are independent: a CTA of 128 threads
-// takes 64 sites, warps 0-1 block 0 and warps 2-3 block 1.
-__global__ void __launch_bounds__(128) k_clover_df(int Vh, Field out, Field x, Field in, const float4* C, int parity,
-                                                   df c1, df c2, int n) {
-  const int ch = threadIdx.x >> 6;
-  const int cb = blockIdx.x * 64 + (threadIdx.x & 63);
-  const int k = blockIdx.y;
-  if (cb >= Vh || k >= n) return;
+// one site and chirality block of k_clover_df; returns the block's
+// ||out||^2 to FP32 accuracy
+__device__ __forceinline__ double clover_df_site(int Vh, const Field& out, const Field& x, const Field& in,
+                                                 const float4* C, int parity, df c1, df c2, int k, int cb, int ch) {
   cdf v[6], w[6];
+
   load_block_df(in, k, cb, ch, v);
   herm6_apply_df(C + ((size_t)parity * 36 + 18 * ch) * Vh + cb, Vh, v, w);
   if (x.data) {
@@ -286,6 +283,35 @@ __global__ void __launch_bounds__(128) k_clover_df(int Vh, Field out, Field x, F
     for (int j = 0; j < 6; j++) w[j] = cscale(c2, w[j]);
   }
   store_block_df(out, k, cb, ch, w);
+  typedef SumOf<float>::T S;
+  S q2 = 0;
+#pragma unroll
+  for (int q = 0; q < 6; q++) {
+    const S re = w[q].re.h + w[q].re.l, im = w[q].im.h + w[q].im.l;
+    q2 = fma(re, re, fma(im, im, q2));
+  }
+  return (double)q2;
+}
+
+// out = c1 x + c2 (C in), C = A or A^{-1} (pre-split blocks); x may be
+// absent. The two chirality blocks are independent: a CTA of 128 threads
+// takes 64 sites, warps 0-1 block 0 and warps 2-3 block 1. NORM: per-warp
+// partials of ||out||^2 (FP32-accurate squares, as in k_dslash_df) for a
+// k_finish.
+template <int NORM>
+__global__ void __launch_bounds__(128) k_clover_df(int Vh, Field out, Field x, Field in, const float4* C, int parity,
+                                                   df c1, df c2, int n, RedArgs ra) {
+  const int ch = threadIdx.x >> 6;
+  const int cb = blockIdx.x * 64 + (threadIdx.x & 63);
+  const int k = blockIdx.y;
+  if (NORM) {  // every thread reaches the warp sums
+    double red[1] = {0.0};
+    if (cb < Vh && k < n) red[0] = clover_df_site(Vh, out, x, in, C, parity, c1, c2, k, cb, ch);
+    warp_partials<1>(ra, red, k < n ? k : -1, (int)blockIdx.x * 4 + (int)(threadIdx.x >> 5));
+    return;
+  }
+  if (cb >= Vh || k >= n) return;
+  clover_df_site(Vh, out, x, in, C, parity, c1, c2, k, cb, ch);
 }
 
 // ---------------------------------------------------------------------------
@@ -297,10 +323,18 @@ static df df_host(double v) {
 }
 
 void launch_clover_df(const sq_ctx* c, const CloverSet& cs, Field out, Field x, Field in, int parity, double c1,
-                      double c2, int which, int n, cudaStream_t s) {
+                      double c2, int which, int n, cudaStream_t s, const RedArgs* norm) {
   dim3 grid((c->Vh + 63) / 64, n);
-  k_clover_df<<<grid, 128, 0, s>>>(c->Vh, out, x, in, which ? cs.Ainvdf : cs.Adf, parity, df_host(c1), df_host(c2),
-                                   n);
+  const float4* C = which ? cs.Ainvdf : cs.Adf;
+  if (norm && (int)grid.x * 4 <= norm->nblk_stride) {
+    k_clover_df<1><<<grid, 128, 0, s>>>(c->Vh, out, x, in, C, parity, df_host(c1), df_host(c2), n, *norm);
+    k_finish<double, 1, FIN_STORE><<<n, 256, 0, s>>>(*norm, nullptr, nullptr, n, (int)grid.x * 4);
+  } else {
+    RedArgs none;
+    memset(&none, 0, sizeof(none));
+    k_clover_df<0><<<grid, 128, 0, s>>>(c->Vh, out, x, in, C, parity, df_host(c1), df_host(c2), n, none);
+    if (norm) fprintf(stderr, "libstochq: internal error: clover norm partials do not fit\n");
+  }
 }
 
 template <int CLOV, int XPAY, int XFIRST, int FIN, int OUT2>
@@ -341,6 +375,11 @@ bool launch_dslash_df(const sq_ctx* c, const DslashCall& d, Field out2, int xfir
   if (d.fin == FIN_TRUE) {
     if (m != 3) return false;
     go_df<1, 1, 0, FIN_TRUE, 0>(a, grid, block, s);
+    return true;
+  }
+  if (d.fin == FIN_STORE) {  // the full residual's even half: x + a D in, with its norm
+    if (m != 2) return false;
+    go_df<0, 1, 0, FIN_STORE, 0>(a, grid, block, s);
     return true;
   }
   if (d.fin != FIN_NONE) return false;

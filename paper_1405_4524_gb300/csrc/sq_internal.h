@@ -231,7 +231,8 @@ void launch_dslash(const sq_ctx* c, const DslashCall& d, cudaStream_t s);
 // emulated-FP64 kernels (sq_dslash_df.cu)
 bool launch_dslash_df(const sq_ctx* c, const DslashCall& d, Field out2, int xfirst, cudaStream_t s, int* nparts);
 void launch_clover_df(const sq_ctx* c, const CloverSet& cs, Field out, Field x, Field in, int parity, double c1,
-                      double c2, int which, int n, cudaStream_t s);
+                      double c2, int which, int n, cudaStream_t s,
+                      const RedArgs* norm = nullptr);
 // halo-tiled kernel (sq_dslash_tile.cu): false if d.shape does not apply
 bool launch_dslash_tile(const sq_ctx* c, const DslashCall& d, cudaStream_t s, int* nparts);
 bool tile_shape_ok(const sq_ctx* c, int prec, int recon, const Shape& sh);

@@ -750,18 +750,18 @@ static void launch_update(sq_ctx* c, Workspace& w, const CloverSet& cs, double k
   dim3 bb(kBlasShape.sx, kBlasShape.ry);
   dim3 bg((c->Vh + kBlasShape.sx - 1) / kBlasShape.sx, (n + kBlasShape.ry - 1) / kBlasShape.ry);
   VArgs u = vargs(c, w, true);
-  u.f0 = w.x64; u.f1 = w.xs; u.f2 = w.b64; u.f3 = w.r64;
-  k_rel_x<PX><<<bg, bb, 0, s>>>(u);
-  if (zero_x) {
-    u.f0 = w.r64;
+  if (zero_x) {  // x64 = xs = 0 (set up so): the residual is bhat itself
+    u.f0 = w.b64;
     k_true_norm<<<bg, bb, 0, s>>>(u);
-    u.f0 = w.r64; u.f1 = w.r; u.f2 = w.rh; u.f3 = w.p;
+    u.f0 = w.b64; u.f1 = w.r; u.f2 = w.rh; u.f3 = w.p;
     k_rel_r<P, P64><<<bg, bb, 0, s>>>(u);
     k_finish<typename SumOf<R>::T, 2, FIN_UPDATE><<<n, 256, 0, s>>>(u.ra, w.update_list, &w.ctl->n_update, n, (int)bg.x * (kBlasShape.sx / 32));
     k_control<<<1, 32, 0, s>>>(w.st, w.ctl, w.active_list, n, nullptr, 0, 0);
-    c->launches += 5;
+    c->launches += 4;
     return;
   }
+  u.f0 = w.x64; u.f1 = w.xs; u.f2 = w.b64; u.f3 = w.r64;
+  k_rel_x<PX><<<bg, bb, 0, s>>>(u);
   DslashCall d64;
   memset(&d64, 0, sizeof(d64));
   d64.prec = P64;
@@ -857,13 +857,22 @@ static void launch_full_residual(sq_ctx* c, Workspace& w, const CloverSet& cs, d
   d.shape = kBlasShape;
   d.ra = red_args(w);
   d.emul = emul ? 1 : 0;
-  if (emul) launch_clover_df(c, cs, w.r64, w.eta_e, w.x64, 0, 1.0, -1.0, 0, n, s);
-  else launch_clover64(c, cs, w.r64, w.eta_e, w.x64, 0, 1.0, -1.0, 0, n, s);
+  RedArgs ra = red_args(w);
+  if (emul) {  // the norms come with the last kernel of each half
+    launch_clover_df(c, cs, w.r64, w.eta_e, w.x64, 0, 1.0, -1.0, 0, n, s);
+    d.out = w.r64; d.in = w.x64o; d.x = w.r64; d.p_out = 0; d.xpay = 1; d.a = kappa;
+    d.fin = FIN_STORE;  // ||r_e||^2 -> scal[0..n)
+    launch_dslash(c, d, s);
+    RedArgs ro = ra;
+    ro.out = w.scal + n;  // ||r_o||^2
+    launch_clover_df(c, cs, w.t64o, w.t64o, w.x64o, 1, 1.0, -1.0, 0, n, s, &ro);
+    c->launches += 5;
+    return;
+  }
+  launch_clover64(c, cs, w.r64, w.eta_e, w.x64, 0, 1.0, -1.0, 0, n, s);
   d.out = w.r64; d.in = w.x64o; d.x = w.r64; d.p_out = 0; d.xpay = 1; d.a = kappa;
   launch_dslash(c, d, s);
-  if (emul) launch_clover_df(c, cs, w.t64o, w.t64o, w.x64o, 1, 1.0, -1.0, 0, n, s);
-  else launch_clover64(c, cs, w.t64o, w.t64o, w.x64o, 1, 1.0, -1.0, 0, n, s);
-  RedArgs ra = red_args(w);
+  launch_clover64(c, cs, w.t64o, w.t64o, w.x64o, 1, 1.0, -1.0, 0, n, s);
   launch_norm2(c, w.r64, P64, n, w.scal, ra, s);
   launch_norm2(c, w.t64o, P64, n, w.scal + n, ra, s);
   c->launches += 5;

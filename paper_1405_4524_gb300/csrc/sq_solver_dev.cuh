@@ -365,7 +365,12 @@ __global__ void __launch_bounds__(256) k_finish(const RedArgs ra, const int* lis
     for (int w = 0; w < (int)(blockDim.x >> 5); w++)
 #pragma unroll
       for (int i = 0; i < NRED; i++) tot[i] += sm[w][i];
-    finalize<FIN>(ra, k, tot);
+    if (FIN == FIN_STORE) {
+#pragma unroll
+      for (int i = 0; i < NRED; i++) ra.out[(size_t)k * NRED + i] = tot[i];
+    } else {
+      finalize<FIN>(ra, k, tot);
+    }
   }
 }
 
