@@ -170,7 +170,8 @@ void sq_default_params(sq_solve_params *p);
 sq_status sq_create(sq_ctx **ctx, const int dims[4], int t_bc, void *cuda_stream);
 
 /* Caller-supplied device memory for the context's persistent buffers (gauge
- * copies, clover terms, solver workspaces, contraction and profiling
+ * copies and the staging of host links, clover terms and the clover build's
+ * field-strength scratch, solver workspaces, contraction and profiling
  * scratch), e.g. a framework's caching allocator. alloc returns a device
  * pointer to at least `bytes` bytes, 256-byte aligned, or NULL (reported as
  * SQ_ERR_OOM / SQ_ERR_CUDA by the call that needed it); free releases a
@@ -178,9 +179,10 @@ sq_status sq_create(sq_ctx **ctx, const int dims[4], int t_bc, void *cuda_stream
  * cudaStream_t, on which the buffer is used; the library synchronises that
  * stream before it frees a buffer, so free may reuse the memory at once.
  * `user` is passed through. Both NULL restores cudaMalloc / cudaFree (the
- * default). Per-call staging buffers for host I/O stay on the CUDA
- * stream-ordered pool (cudaMallocAsync on the context's stream), and the
- * context's 4-byte device error word is allocated by sq_create.
+ * default). The other per-call staging buffers for host I/O stay on the
+ * CUDA stream-ordered pool (cudaMallocAsync on the context's stream), and
+ * the context's 16-byte device error word and clover bound are allocated by
+ * sq_create.
  * Errors: SQ_ERR_ARG (only one of alloc/free given), SQ_ERR_STATE (the
  * context already holds persistent buffers: call it before sq_load_gauge). */
 typedef void *(*sq_alloc_fn)(size_t bytes, void *stream, void *user);
@@ -194,7 +196,8 @@ sq_status sq_destroy(sq_ctx *ctx);
  * Kept on the device as FP64 reconstruct-18 and FP32 reconstruct-`recon`
  * (used by the FP32 and the FP16 operator), per-parity site-blocked (the analogue of the
  * array reordering between the paper's host code and its GPU inverter,
- * Sec. "Stochastic propagators"). Drops cached clover terms.
+ * Sec. "Stochastic propagators"). Drops cached clover terms. Host links go
+ * through a staging buffer of the context's size that the context keeps.
  * Errors: SQ_ERR_ARG (recon not 12/18, NULL), SQ_ERR_NONFINITE,
  * SQ_ERR_ARG if recon = 12 and some link is not SU(3) to 1e-6. */
 sq_status sq_load_gauge(sq_ctx *ctx, const double *U, int recon, int where);

@@ -249,7 +249,7 @@ sq_status sq_set_allocator(sq_ctx* c, sq_alloc_fn alloc, sq_free_fn free_fn, voi
   if ((!alloc) != (!free_fn)) return set_error(c, SQ_ERR_ARG, "sq_set_allocator: give both callbacks or neither");
   bool held = c->U64 || c->U32 || c->stoch_part || c->ws.base || c->batch;
   for (auto& cs : c->clover) held = held || cs.A64 || cs.Ainv64 || cs.Ainv32 || cs.Adf || cs.Ainvdf;
-  held = held || c->Udf || c->cloverF;
+  held = held || c->Udf || c->cloverF || c->gstage;
   if (held) return set_error(c, SQ_ERR_STATE, "sq_set_allocator: the context already holds device buffers");
   c->mem.alloc = alloc;
   c->mem.free = free_fn;
@@ -266,6 +266,7 @@ sq_status sq_destroy(sq_ctx* c) {
   dev_free(c->mem, c->Udf, 2 * 4 * 9 * (size_t)c->Vh * sizeof(float4));
   dev_free(c->mem, c->U32, gauge32_bytes(c, c->recon));
   dev_free(c->mem, c->cloverF, clover_scratch_bytes(c));
+  dev_free(c->mem, c->gstage, (size_t)c->V * 4 * 18 * sizeof(double));
   cudaFree(c->d_err);
   dev_free(c->mem, c->stoch_part, c->stoch_cap);
   cudaEventDestroy(c->ev);
@@ -298,15 +299,20 @@ sq_status sq_load_gauge(sq_ctx* c, const double* U, int recon, int where) {
   const size_t nd = (size_t)c->V * 4 * 18;
   const double* dU = U;
   double* stage = nullptr;
-  if (where == SQ_HOST) {
-    e = cudaMallocAsync((void**)&stage, nd * sizeof(double), c->stream);
-    if (e != cudaSuccess) return cuda_check(c, e, "gauge staging");
+  if (where == SQ_HOST) {  // staging buffer kept by the context (no allocation per load)
+    if (!c->gstage) {
+      e = dev_alloc(c->mem, (void**)&c->gstage, nd * sizeof(double));
+      if (e != cudaSuccess) {
+        c->gstage = nullptr;
+        return cuda_check(c, e, "gauge staging");
+      }
+    }
+    stage = c->gstage;
     cudaMemcpyAsync(stage, U, nd * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     dU = stage;
   }
   s = gauge_convert(c, dU);
   c->launches += 1;
-  if (stage) cudaFreeAsync(stage, c->stream);
   int bits = 0;
   if (s == SQ_OK) s = read_error_word(c, &bits);
   if (s != SQ_OK) return s;

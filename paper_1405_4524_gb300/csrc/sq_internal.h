@@ -157,6 +157,7 @@ struct sq_ctx {
   int* d_err = nullptr;
   unsigned long long* d_bound = nullptr;
   double2* cloverF = nullptr;  // [6][9][V] field strengths: the clover build's scratch
+  double* gstage = nullptr;    // [V][4][3][3] complex: staging of host links (sq_load_gauge)
   sq::Workspace ws;
   sq::BatchCache* batch = nullptr;
   unsigned long long uid = 0;  // unique per context (graph cache keys)
