@@ -10,7 +10,7 @@ level up. Both builds solve the same sources in a child process each
 
 * each library reports the precision it was built with (sq_inner_sum_bits);
 * every source converges to 1e-10 in both, with iteration counts that agree
-  to within 2 iterations or 5%;
+  to within 2 iterations or 5% (FP32 inner) / 10% (FP16 inner);
 * the solutions agree with each other to 1e-9 (relative L2) and with the FP64
   oracle: every 4^3x8 source against the oracle's solution, and at 16^3x32
   the oracle's operator residual on two sources and one source against the
@@ -100,7 +100,10 @@ def test_iterations_and_solutions_agree(runs, name, prec):
     for k, (x, y) in enumerate(zip(a, b)):
         assert x["status"] == 0 and y["status"] == 0, (k, x, y)
         assert x["true_residual"] <= 1e-10 and y["true_residual"] <= 1e-10, (k, x, y)
-        assert abs(x["iterations"] - y["iterations"]) <= max(2, 0.05 * y["iterations"]), (k, x, y)
+        # FP16 fields round the recurrence at 2^-11, and a source whose final
+        # check misses 1e-10 is resumed with a tighter target: wider bound
+        frac = 0.05 if prec == 1 else 0.10
+        assert abs(x["iterations"] - y["iterations"]) <= max(2, frac * y["iterations"]), (k, x, y)
         assert rel(s32[key][k], s64[key][k]) <= 1e-9, k
     print(key, "iterations FP32 sums", [x["iterations"] for x in a], "FP64 sums", [y["iterations"] for y in b])
 
