@@ -400,9 +400,11 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         tc_wait_ld();
 #pragma unroll
         for (int q = 0; q < kTcJ; q++) {
-          // exact power of two (subnormal or zero for chunks whose largest
-          // component is near the bottom of the FP64 range)
-          const double w = scalbn(1.0, e[q] - 55 + 11 * (4 - s));
+          // exact power of two 2^E, from its bits in the normal range (E <
+          // 1025 always); subnormal or zero weights, for chunks whose largest
+          // component is near the bottom of the FP64 range, through scalbn
+          const int E = e[q] - 55 + 11 * (4 - s);
+          const double w = E >= -1022 ? __longlong_as_double((long long)(1023 + E) << 52) : scalbn(1.0, E);
           re[q] = fma((double)__uint_as_float(vr[q]), w, re[q]);
           im[q] = fma((double)__uint_as_float(vi[q]), w, im[q]);
         }
