@@ -62,3 +62,31 @@ def test_host_only_calls(lib):
     with pytest.raises(stochq.StochqError) as e:
         stochq.sq_create((4, 4, 4, 8), t_bc=0)
     assert e.value.status == stochq.SQ_ERR_ARG
+
+
+def test_default_params_chunk_and_inner_sums(lib):
+    from paper_1405_4524_gb300 import stochq
+
+    assert stochq.sq_default_params().chunk == 0  # 24 then 4 iterations per graph launch
+    assert stochq.sq_inner_sum_bits() == 32
+
+
+def test_sums64_variant_builds_and_is_selected_by_environment(lib, tmp_path):
+    """The build variant with FP64 inner-iteration sums has its own objects
+    and library, exports the same symbols, and STOCHQ_LIBRARY loads it."""
+    import subprocess
+    import sys
+
+    from paper_1405_4524_gb300 import build
+
+    path = build.build(variant="sums64")
+    assert path == build.library_path("sums64") and path != build.library_path()
+    var = ctypes.CDLL(path)
+    assert not [n for n in declared_functions() if not hasattr(var, n)]
+    code = "from paper_1405_4524_gb300 import stochq as s; print(s.LIBPATH, s.sq_inner_sum_bits())"
+    env = dict(os.environ, STOCHQ_LIBRARY=path)
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                         check=True).stdout.split()
+    assert out == [path, "64"]
+    with pytest.raises(ValueError):
+        build.build(variant="no_such_variant")
