@@ -134,7 +134,8 @@ template <int P>
 __global__ void __launch_bounds__(256) k_norm2(int Vh, Field f, int n, RedArgs ra) {
   typedef typename Real<P>::T R;
   const int cb = blockIdx.x * blockDim.x + threadIdx.x;
-  const int k = blockIdx.y * blockDim.y + threadIdx.y < n ? blockIdx.y * blockDim.y + threadIdx.y : -1;
+  const int ky = (int)(blockIdx.y * blockDim.y + threadIdx.y);
+  const int k = ky < n ? ky : -1;
   double v[1] = {0.0};
   if (k >= 0 && cb < Vh) {
     cx<R> a[12];
